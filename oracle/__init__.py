@@ -1,0 +1,185 @@
+"""Plain FP64 CPU oracle for the pivoted skew-symmetric LTL^T factorization.
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's CPU
+baseline are the only callers.  The GPU product path never imports this package, and
+this package imports nothing from the GPU package.
+
+The arithmetic lives in ``skew_oracle.c`` (plain C, compiled here with gcc and
+``-ffp-contract=off``); this module only builds it and marshals numpy arrays.
+Paper: "Performant Tridiagonal Factorization of Skew-Symmetric Matrices"
+(arXiv 2411.09859); each C function cites the passage it follows.
+
+Every function takes and returns numpy float64 arrays indexed ``A[i, j]``.  Only the
+strictly lower triangle of a skew input is read.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SOURCE = os.path.join(HERE, "skew_oracle.c")
+_LIB_PATH = os.path.join(HERE, "_liboracle.so")
+_lock = threading.Lock()
+_default = None
+
+ERR_NONFINITE = -100
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC"]
+
+
+def compile_source(src: str, out: str) -> str:
+    """Compile one C source of the oracle into a shared library ``out``."""
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", *CFLAGS, "-o", tmp, src, "-lm"], check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile ``skew_oracle.c`` into ``_liboracle.so`` beside it (gcc, OpenMP)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(SOURCE)):
+        return _LIB_PATH
+    return compile_source(SOURCE, _LIB_PATH)
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _fortran_copy(A: np.ndarray) -> np.ndarray:
+    return np.array(A, dtype=np.float64, order="F", copy=True)
+
+
+class OracleLib:
+    """ctypes view of one compiled oracle library (the default one, or a test build)."""
+
+    def __init__(self, path: str):
+        lib = ctypes.CDLL(path)
+        i64, dbl, p = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+        lib.oracle_ltlt_steps.argtypes = [i64, p, i64, p, i64, p, p, i64]
+        lib.oracle_ltlt_steps.restype = ctypes.c_int
+        lib.oracle_pfaffian.argtypes = [i64, p, p, p, p]
+        lib.oracle_pfaffian.restype = None
+        lib.oracle_skew_rank2k.argtypes = [i64, i64, dbl, p, i64, p, i64, dbl, p, i64]
+        lib.oracle_skew_rank2k.restype = None
+        lib.oracle_skew_tridiag_rankk.argtypes = [i64, i64, dbl, p, i64, p, dbl, p, i64]
+        lib.oracle_skew_tridiag_rankk.restype = None
+        lib.oracle_threads.argtypes = []
+        lib.oracle_threads.restype = ctypes.c_int
+        self.lib = lib
+        self.path = path
+
+    def threads(self) -> int:
+        """Host threads the update loop uses (OpenMP; OMP_NUM_THREADS)."""
+        return int(self.lib.oracle_threads())
+
+    def ltlt(self, A: np.ndarray, nsteps: int | None = None, overwrite: bool = False):
+        """Unblocked right-looking pivoted LTL^T of the skew matrix ``A``.
+
+        Returns ``(L, t, piv, info)``: L n x n unit lower (Fortran order), t length
+        n-1, piv int32 length n (absolute, piv[0] = 0), info as returned by the C
+        routine (0, 1 + first zero pivot, or a negative error).  ``nsteps`` stops
+        after that many elimination steps (bounded timing samples only).  With
+        ``overwrite`` and a Fortran-ordered float64 ``A``, ``A`` is the workspace.
+        """
+        n = int(A.shape[0])
+        if A.shape != (n, n):
+            raise ValueError("A must be square")
+        if overwrite and A.dtype == np.float64 and A.flags.f_contiguous:
+            X = A
+        else:
+            X = _fortran_copy(A)
+        L = np.zeros((n, n), dtype=np.float64, order="F")
+        t = np.zeros(max(n - 1, 1), dtype=np.float64)
+        piv = np.zeros(max(n, 1), dtype=np.int32)
+        steps = n if nsteps is None else int(nsteps)
+        ld = max(n, 1)
+        if n == 0:
+            X = np.zeros((1, 1), order="F")
+            L = np.zeros((1, 1), order="F")
+        info = self.lib.oracle_ltlt_steps(n, _ptr(X), ld, _ptr(L), ld, _ptr(t),
+                                          _ptr(piv), steps)
+        if n == 0:
+            return (np.zeros((0, 0), order="F"), np.zeros(0), np.zeros(0, np.int32),
+                    int(info))
+        return L, t[: n - 1], piv, int(info)
+
+    def pfaffian_from_factors(self, n: int, t: np.ndarray, piv: np.ndarray):
+        """``(log|Pf|, sign)`` read off T and P (sign in {-1, 0, 1})."""
+        tt = np.zeros(max(len(t), 1))
+        tt[: len(t)] = t
+        pp = np.zeros(max(len(piv), 1), dtype=np.int32)
+        pp[: len(piv)] = piv
+        logabs = np.zeros(1, dtype=np.float64)
+        sign = np.zeros(1, dtype=np.int32)
+        self.lib.oracle_pfaffian(int(n), _ptr(tt), _ptr(pp), _ptr(logabs), _ptr(sign))
+        return float(logabs[0]), int(sign[0])
+
+    def pfaffian(self, A: np.ndarray):
+        """``(log|Pf(A)|, sign)`` via :meth:`ltlt` then :meth:`pfaffian_from_factors`."""
+        L, t, piv, info = self.ltlt(A)
+        if info < 0:
+            raise ValueError(f"oracle_ltlt failed with {info}")
+        return self.pfaffian_from_factors(A.shape[0], t, piv)
+
+    def skew_rank2k(self, alpha, A, B, beta, C):
+        """Copy of C with its strictly lower part := beta C + alpha (A B^T - B A^T)."""
+        m, k = A.shape
+        Af, Bf, Cf = _fortran_copy(A), _fortran_copy(B), _fortran_copy(C)
+        ld = max(m, 1)
+        self.lib.oracle_skew_rank2k(m, k, float(alpha), _ptr(Af), ld, _ptr(Bf), ld,
+                                    float(beta), _ptr(Cf), ld)
+        return Cf
+
+    def skew_tridiag_rankk(self, alpha, A, t, beta, C):
+        """Copy of C with its strictly lower part := beta C + alpha A T A^T."""
+        m, b = A.shape
+        Af, Cf = _fortran_copy(A), _fortran_copy(C)
+        tt = np.zeros(max(b - 1, 1))
+        tt[: max(b - 1, 0)] = np.asarray(t, dtype=np.float64)[: max(b - 1, 0)]
+        ld = max(m, 1)
+        self.lib.oracle_skew_tridiag_rankk(m, b, float(alpha), _ptr(Af), ld, _ptr(tt),
+                                           float(beta), _ptr(Cf), ld)
+        return Cf
+
+
+def default() -> OracleLib:
+    """The oracle built from ``skew_oracle.c`` (compiled on first use)."""
+    global _default
+    with _lock:
+        if _default is None:
+            try:
+                _default = OracleLib(build())
+            except OSError:
+                # a library left by a build on another architecture: rebuild here
+                _default = OracleLib(build(force=True))
+        return _default
+
+
+def threads() -> int:
+    return default().threads()
+
+
+def ltlt(A, nsteps=None, overwrite=False):
+    return default().ltlt(A, nsteps=nsteps, overwrite=overwrite)
+
+
+def pfaffian_from_factors(n, t, piv):
+    return default().pfaffian_from_factors(n, t, piv)
+
+
+def pfaffian(A):
+    return default().pfaffian(A)
+
+
+def skew_rank2k(alpha, A, B, beta, C):
+    return default().skew_rank2k(alpha, A, B, beta, C)
+
+
+def skew_tridiag_rankk(alpha, A, t, beta, C):
+    return default().skew_tridiag_rankk(alpha, A, t, beta, C)

@@ -1,0 +1,241 @@
+"""Checks used by the tests: the Pfaffian by its definition, the factor properties,
+and a numpy restatement of the pivoted blocked right-looking algorithm.
+
+Nothing here calls the GPU library.  Section and equation numbers refer to
+"Performant Tridiagonal Factorization of Skew-Symmetric Matrices" (arXiv 2411.09859).
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+EPS = 2.0 ** -52
+
+
+# ----------------------------------------------------------------------------------
+# the Pfaffian from its definition (Section 1)
+# ----------------------------------------------------------------------------------
+def _perm_sign(p) -> int:
+    p = list(p)
+    s = 1
+    for i in range(len(p)):
+        while p[i] != i:
+            j = p[i]
+            p[i], p[j] = p[j], p[i]
+            s = -s
+    return s
+
+
+def pfaffian_by_definition(X: np.ndarray) -> float:
+    """Pf(X) = 1/(2^m m!) sum over all permutations sigma of the 2m indices of
+    sgn(sigma) prod_{i=1..m} x[sigma(2i-1), sigma(2i)]  (Section 1), summed literally.
+    Feasible for n <= 8 (40320 permutations).  Odd n gives 0; n = 0 gives 1."""
+    n = X.shape[0]
+    if n % 2:
+        return 0.0
+    if n == 0:
+        return 1.0
+    m = n // 2
+    total = 0.0
+    for sigma in itertools.permutations(range(n)):
+        prod = 1.0
+        for i in range(m):
+            prod *= X[sigma[2 * i], sigma[2 * i + 1]]
+        total += _perm_sign(sigma) * prod
+    return total / (2 ** m * math.factorial(m))
+
+
+def pfaffian_by_matchings(X: np.ndarray) -> float:
+    """The same sum grouped by perfect matchings (each matching appears 2^m m! times
+    with one sign): expansion along the first index, recursively.  n <= 14."""
+    n = X.shape[0]
+    if n % 2:
+        return 0.0
+
+    def rec(idx):
+        if not idx:
+            return 1.0
+        a = idx[0]
+        total = 0.0
+        for pos in range(1, len(idx)):
+            b = idx[pos]
+            rest = idx[1:pos] + idx[pos + 1:]
+            total += (-1) ** (pos - 1) * X[a, b] * rec(rest)
+        return total
+
+    return rec(list(range(n)))
+
+
+def pf4_closed_form(X: np.ndarray) -> float:
+    """Pf of a 4x4 skew matrix: x01 x23 - x02 x13 + x03 x12."""
+    return X[0, 1] * X[2, 3] - X[0, 2] * X[1, 3] + X[0, 3] * X[1, 2]
+
+
+# ----------------------------------------------------------------------------------
+# factor properties
+# ----------------------------------------------------------------------------------
+def perm_from_piv(piv) -> np.ndarray:
+    """perm with (P A P^T)[a, b] = A[perm[a], perm[b]] for P = P(p) of Section 5.1
+    (the row exchanges i <-> piv[i] applied in order i = 0, 1, ...)."""
+    n = len(piv)
+    perm = np.arange(n)
+    for i in range(n):
+        r = int(piv[i])
+        perm[i], perm[r] = perm[r], perm[i]
+    return perm
+
+
+def tridiag_from_t(t, n: int) -> np.ndarray:
+    """T with T[i+1, i] = t[i] and T[i, i+1] = -t[i] (Eq. (T))."""
+    T = np.zeros((n, n))
+    for i in range(n - 1):
+        T[i + 1, i] = t[i]
+        T[i, i + 1] = -t[i]
+    return T
+
+
+def full_skew_from_lower(X: np.ndarray) -> np.ndarray:
+    """Full skew matrix from the strictly lower triangle of X."""
+    Lw = np.tril(X, -1)
+    return Lw - Lw.T
+
+
+def backward_error(A: np.ndarray, L: np.ndarray, t, piv) -> float:
+    """||P A P^T - L T L^T||_F / (n eps ||A||_F) with eps = 2^-52."""
+    n = A.shape[0]
+    if n <= 1:
+        return 0.0
+    Af = full_skew_from_lower(A)
+    perm = perm_from_piv(piv)
+    PAPt = Af[np.ix_(perm, perm)]
+    T = tridiag_from_t(t, n)
+    R = PAPt - L @ T @ L.T
+    nrm = np.linalg.norm(Af)
+    if nrm == 0:
+        return float(np.linalg.norm(R))
+    return float(np.linalg.norm(R) / (n * EPS * nrm))
+
+
+def check_structure(L: np.ndarray, t, piv, n: int):
+    """Invariants of the pivoted factorization: L unit lower triangular, L e_0 = e_0,
+    |L_ij| <= 1 (the pivot is the entry of largest magnitude), piv[0] = 0 and
+    piv[i] >= i."""
+    assert L.shape == (n, n)
+    if n == 0:
+        return
+    assert np.all(np.diag(L) == 1.0)
+    assert np.all(np.triu(L, 1) == 0.0)
+    e0 = np.zeros(n)
+    e0[0] = 1.0
+    assert np.array_equal(L[:, 0], e0)
+    assert np.all(np.abs(L) <= 1.0)
+    assert piv[0] == 0
+    assert all(int(piv[i]) >= i and int(piv[i]) < n for i in range(n))
+    assert len(t) == n - 1
+
+
+def pfaffian_from_t_piv(t, piv, n):
+    """Independent restatement of the read-off: Pf = det(P) prod_i T[2i, 2i+1]."""
+    if n % 2:
+        return 0.0
+    swaps = sum(1 for i in range(n) if int(piv[i]) != i)
+    val = 1.0
+    for i in range(n // 2):
+        val *= -t[2 * i]
+    return (-1) ** swaps * val
+
+
+# ----------------------------------------------------------------------------------
+# the pivoted blocked right-looking algorithm (Section 4.2 Variant 1 with the
+# pivoted panel of Section 5.2), restated in numpy on FULL storage
+# ----------------------------------------------------------------------------------
+def ltlt_blocked(A: np.ndarray, nb: int, fused_w: bool = False):
+    """Blocked right-looking pivoted LTL^T.
+
+    Each panel of nb columns k0 .. k0+nb-1 is factored with the left-looking
+    (modified Aasen) algorithm: the column to eliminate is formed on the fly as
+    v = X[k+1:, k] - L[k+1:, k0+1:k+1] h with h = T L[k, :]^T restricted to the
+    panel (skew_tridiag_gemv); the pivot exchanges rows and columns of the whole
+    unfactored matrix and rows of the panel's L columns; L columns left of the panel
+    get the panel's exchanges afterwards (pivot_rows).  The trailing matrix then
+    receives X[s:, s:] -= A T_p A^T with A = L[s:, k0+1:s+1] (s = k0+nb) and T_p the
+    panel's skew tridiagonal block, followed by the last Gauss transform as a skew
+    rank-2 update X[s+1:, s+1:] += l x^T - x l^T.
+
+    With ``fused_w`` the trailing update is instead done the way the GPU path does
+    it: W = A S (Theorem on T = S - S^T), the updated column x = X[s+1:, s] is
+    formed first by the same left-looking formula, and one skew rank-2(k+1) update
+    C += X' Y'^T - Y' X'^T with X' = [odd columns of A, l], Y' = [odd columns of W, x]
+    covers both parts.
+    """
+    n = A.shape[0]
+    X = full_skew_from_lower(np.asarray(A, dtype=np.float64))
+    L = np.eye(n)
+    t = np.zeros(max(n - 1, 0))
+    piv = np.arange(n)
+
+    def h_vector(k, k0):
+        # h_q for q = k0+1 .. k, with L[k, k] = 1
+        h = np.zeros(k - k0)
+        for q in range(k0 + 1, k + 1):
+            val = 0.0
+            if q - 1 >= k0 + 1:
+                val += t[q - 1] * L[k, q - 1]
+            if q + 1 <= k:
+                val -= t[q] * L[k, q + 1]
+            h[q - k0 - 1] = val
+        return h
+
+    k0 = 0
+    while k0 < n - 1:
+        kend = min(k0 + nb, n - 1)
+        for k in range(k0, kend):
+            h = h_vector(k, k0)
+            v = X[k + 1:, k] - L[k + 1:, k0 + 1:k + 1] @ h
+            r = k + 1 + int(np.argmax(np.abs(v)))       # first index of the maximum
+            piv[k + 1] = r
+            if r != k + 1:
+                v[[0, r - k - 1]] = v[[r - k - 1, 0]]
+                X[[k + 1, r], :] = X[[r, k + 1], :]
+                X[:, [k + 1, r]] = X[:, [r, k + 1]]
+                L[[k + 1, r], k0 + 1:k + 1] = L[[r, k + 1], k0 + 1:k + 1]
+            t[k] = v[0]
+            L[k + 2:, k + 1] = v[1:] / t[k] if t[k] != 0.0 else 0.0
+        for k in range(k0, kend):                         # pivot_rows
+            r = piv[k + 1]
+            if r != k + 1:
+                L[[k + 1, r], 1:k0 + 1] = L[[r, k + 1], 1:k0 + 1]
+        s = kend
+        if s < n - 1:
+            Ap = L[s:, k0 + 1:s + 1]
+            b = Ap.shape[1]
+            if not fused_w:
+                Tp = tridiag_from_t(t[k0 + 1:s], b)
+                X[s:, s:] -= Ap @ Tp @ Ap.T
+                l = L[s + 1:, s]
+                x = X[s + 1:, s].copy()
+                X[s + 1:, s + 1:] += np.outer(l, x) - np.outer(x, l)
+            else:
+                # updated column s by the left-looking formula (step k = s)
+                h = h_vector(s, k0)
+                x = X[s + 1:, s] - L[s + 1:, k0 + 1:s + 1] @ h
+                X[s + 1:, s] = x
+                X[s, s + 1:] = -x
+                tp = t[k0 + 1:s]                          # T_p sub-diagonal, b-1 values
+                a = L[s + 1:, k0 + 1:s + 1]               # rows s+1.. of A
+                cols_x, cols_y = [], []
+                for j in range(1, b, 2):                   # odd columns of W = A S
+                    w = -tp[j - 1] * a[:, j - 1]
+                    if j + 1 < b:
+                        w = w + tp[j] * a[:, j + 1]
+                    cols_x.append(a[:, j])
+                    cols_y.append(w)
+                cols_x.append(L[s + 1:, s])
+                cols_y.append(x)
+                Xp = np.stack(cols_x, axis=1)
+                Yp = np.stack(cols_y, axis=1)
+                X[s + 1:, s + 1:] += Xp @ Yp.T - Yp @ Xp.T
+        k0 = kend
+    return L, t, piv
