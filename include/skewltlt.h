@@ -1,0 +1,194 @@
+/*
+ * skewltlt.h -- C ABI of the GB300 (sm_103a) skew-symmetric LTL^T library.
+ *
+ * Operation (arXiv 2411.09859, Section 1 and Section 5): for a real skew-symmetric
+ * n x n matrix X (X = -X^T), compute the pivoted triangular tridiagonalization
+ *
+ *     P X P^T = L T L^T,
+ *
+ * with P a permutation, L unit lower triangular with L e_0 = e_0 (Section 4.1), and T
+ * skew-symmetric tridiagonal with sub-diagonal tau_{i+1,i} (Eq. (T)); and the
+ * Pfaffian Pf(X) = det(P) Pf(T) read off the factors.  The method is the pivoted
+ * blocked right-looking algorithm (Section 4.2 "Blocked algorithms", Variant 1, with
+ * the pivoted left-looking panel of Section 5.2), whose trailing update is a
+ * skew-symmetric rank-2k update obtained from A T A^T through W = A S (Theorem on
+ * T = S - S^T, Section 2.2).
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are FP64, column-major: element (i, j) of M is M[i + j * ldm].
+ *   - Only the strictly lower triangle of a skew input is read; its upper triangle
+ *     and diagonal are never referenced (Section 4.1: the skew structure is implicit).
+ *   - Indices are 0-based.  t[j] = tau_{j+1,j}, j = 0 .. n-2.
+ *   - piv[i] (i = 0 .. n-1) is the absolute row exchanged with row i just before
+ *     column i of L is formed; piv[0] = 0 and piv[i] >= i.  The relative pivot
+ *     pi_i of Section 5.1 is piv[i] - i, and P = P(p) of Section 5.1.
+ *   - Pivot search: the entry of largest magnitude; among equal magnitudes the
+ *     lowest row index (the paper leaves ties open).
+ *   - Pointers named "device" must point to memory of the current CUDA device.  The
+ *     caller owns every buffer it passes.  The library owns only the workspace it
+ *     allocates itself (stream-ordered, freed before the call's work completes).
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device work is
+ *     enqueued on it and the call returns without waiting; outputs are valid once
+ *     the stream has reached the call's end.
+ *   - Return value: SKEW_OK, or a negative status.  A value -i with 1 <= i <= 99
+ *     means argument i (1-based) is invalid; nothing is enqueued then.
+ *   - `info` (device int32, may be NULL) receives, in stream order: 0 on success;
+ *     1 + the first j with t[j] == 0 (a zero pivot column: the factorization is
+ *     still complete and valid, its Gauss transform is the identity); or a negative
+ *     status detected on the device (SKEW_ERR_NONFINITE, SKEW_ERR_TIMEOUT), in which
+ *     case the outputs are unspecified.
+ */
+#ifndef SKEWLTLT_H
+#define SKEWLTLT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SKEW_OK = 0,
+    SKEW_ERR_NONFINITE = -100,  /* a NaN or infinity in the strictly lower input */
+    SKEW_ERR_NOMEM = -101,      /* device workspace could not be allocated */
+    SKEW_ERR_CUDA = -102,       /* a CUDA runtime call failed (see skew_last_error) */
+    SKEW_ERR_TIMEOUT = -103,    /* a bounded device-side wait gave up */
+    SKEW_ERR_NODEVICE = -104    /* no usable sm_103 device is current */
+} skew_status;
+
+/* Library version as 10000*major + 100*minor + patch. */
+int skew_version(void);
+
+/* Text of the last CUDA error seen by this thread's calls ("" if none).  The
+ * returned string is owned by the library and valid until the next call. */
+const char *skew_last_error(void);
+
+/* Number of device kernels this process has launched through the library so far
+ * (every entry point counts its own launches; never reset). */
+uint64_t skew_kernel_launches(void);
+
+/* Return the device memory that the library keeps in its private stream-ordered
+ * pool (freed blocks stay reserved for reuse by later calls) to the system.  Call
+ * only when no library work is in flight on the current device. */
+int skew_trim_memory(void);
+
+/* Panel width used when `nb` is 0 for a matrix of order n. */
+int skew_default_nb(int64_t n);
+
+/*
+ * Device workspace, in bytes, that skew_ltlt / skew_pfaffian need for order n and
+ * panel width nb (0 = default).  `with_L` = 0 gives the figure for skew_pfaffian,
+ * which keeps only the current panel of L.  Pass a buffer of at least this size to
+ * avoid the library's own stream-ordered allocation.
+ */
+size_t skew_workspace_bytes(int64_t n, int nb, int with_L);
+
+/*
+ * skew_ltlt -- pivoted blocked right-looking P A P^T = L T L^T
+ * (Section 4.2, Variant 1; Section 5.2 pivoted blocked right-looking algorithm).
+ *
+ *   1  n          order, n >= 0
+ *   2  A          device, lda x n; strictly lower triangle = the skew input.
+ *                 DESTROYED: used as the trailing-matrix workspace.
+ *   3  lda        >= max(1, n)
+ *   4  L          device, ldl x n output, fully written: unit lower triangular,
+ *                 zero above the diagonal, L[:, 0] = e_0
+ *   5  ldl        >= max(1, n)
+ *   6  t          device, n-1 outputs t[j] = tau_{j+1,j} (may be NULL when n <= 1)
+ *   7  piv        device, n int32 outputs (absolute pivots, piv[0] = 0)
+ *   8  info       device int32 or NULL (see above)
+ *   9  nb         panel width 1 .. 256, or 0 for skew_default_nb(n)
+ *  10  workspace  device buffer or NULL (library allocates on `stream`)
+ *  11  workspace_bytes  size of `workspace` (ignored when it is NULL)
+ *  12  stream     cudaStream_t
+ * A, L, t, piv must not overlap.
+ */
+int skew_ltlt(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
+              int32_t *piv, int32_t *info, int nb, void *workspace,
+              size_t workspace_bytes, void *stream);
+
+/*
+ * skew_pfaffian -- Pf(A) through the same factorization, keeping only the current
+ * panel of L (Pf(X) = det(P) Pf(T) = det(P) prod_i T[2i, 2i+1], Section 1 with
+ * Pf(B X B^T) = det(B) Pf(X)).
+ *
+ *   1  n        order, n >= 0
+ *   2  A        device, lda x n, strictly lower triangle read; DESTROYED
+ *   3  lda      >= max(1, n)
+ *   4  logabs   device double: log |Pf(A)| (-inf when Pf = 0; 0 for n = 0)
+ *   5  sign     device int32: sign of Pf(A) in {-1, 0, +1} (0 for odd n or a zero
+ *               t[2i]; +1 for n = 0)
+ *   6  t        device, n-1 outputs, or NULL (then kept in the workspace)
+ *   7  piv      device, n outputs, or NULL (then kept in the workspace)
+ *   8  info     device int32 or NULL
+ *   9  nb, 10 workspace, 11 workspace_bytes, 12 stream: as for skew_ltlt
+ */
+int skew_pfaffian(int64_t n, double *A, int64_t lda, double *logabs, int32_t *sign,
+                  double *t, int32_t *piv, int32_t *info, int nb, void *workspace,
+                  size_t workspace_bytes, void *stream);
+
+/*
+ * skew_pfaffian_from_factors -- the read-off alone: log|Pf| and sign from t and piv
+ * of an order-n factorization (all device pointers; t has n-1 entries).
+ *   1 n, 2 t, 3 piv, 4 logabs, 5 sign, 6 stream
+ * The sum of logarithms uses a fixed (deterministic) reduction order.
+ */
+int skew_pfaffian_from_factors(int64_t n, const double *t, const int32_t *piv,
+                               double *logabs, int32_t *sign, void *stream);
+
+/*
+ * skew_rank2k -- C := beta C + alpha (X Y^T - Y X^T) on the strictly lower
+ * triangle of the m x m skew matrix C (operation skew_rank2k of the table of
+ * BLAS-like operations in Section 4.2).  FP64 tensor-core (DMMA) tiles.
+ *   1 m, 2 k, 3 alpha, 4 X (device, ldx x k), 5 ldx, 6 Y (device, ldy x k), 7 ldy,
+ *   8 beta, 9 C (device, ldc x m), 10 ldc, 11 stream
+ * The upper triangle and diagonal of C are not touched.
+ */
+int skew_rank2k(int64_t m, int64_t k, double alpha, const double *X, int64_t ldx,
+                const double *Y, int64_t ldy, double beta, double *C, int64_t ldc,
+                void *stream);
+
+/*
+ * skew_tridiag_rankk -- C := beta C + alpha A T A^T on the strictly lower triangle
+ * of the m x m skew matrix C, where A is m x b and T is the b x b skew tridiagonal
+ * matrix with sub-diagonal t[0 .. b-2] (operation skew_tridiag_rankk, Section 4.2).
+ * Evaluated as the rank-2*floor(b/2) update W A^T - A W^T with W = A S, where
+ * T = S - S^T and only the odd columns of W are nonzero (Section 2.2); W is formed
+ * while the operand tiles are staged, never stored.
+ *   1 m, 2 b, 3 alpha, 4 A (device, lda x b), 5 lda, 6 t (device, b-1 values),
+ *   7 beta, 8 C (device, ldc x m), 9 ldc, 10 stream
+ */
+int skew_tridiag_rankk(int64_t m, int64_t b, double alpha, const double *A,
+                       int64_t lda, const double *t, double beta, double *C,
+                       int64_t ldc, void *stream);
+
+/*
+ * skew_ltlt_host -- convenience form of skew_ltlt + skew_pfaffian_from_factors on
+ * HOST buffers, for callers without device memory of their own.  Copies A to the
+ * device, factors it on the current device, copies the results back and returns
+ * when they are in host memory (synchronous).  Device buffers are allocated and
+ * freed by the call.  A is not modified.
+ *   1  n
+ *   2  A_host    lda x n host input (strictly lower triangle read)
+ *   3  lda
+ *   4  L_host    ldl x n host output, or NULL (then L is not formed on the device:
+ *                the Pfaffian-only path)
+ *   5  ldl
+ *   6  t_host    n-1 host outputs or NULL
+ *   7  piv_host  n host outputs or NULL
+ *   8  logabs    host double or NULL
+ *   9  sign      host int32 or NULL
+ *  10  info      host int32 or NULL
+ *  11  nb
+ * Host buffers may be pageable or page-locked (page-locked copies are faster).
+ */
+int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
+                   int64_t ldl, double *t_host, int32_t *piv_host, double *logabs,
+                   int32_t *sign, int32_t *info, int nb);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SKEWLTLT_H */

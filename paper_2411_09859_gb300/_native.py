@@ -1,0 +1,231 @@
+"""ctypes declarations of libskewltlt.so and torch-tensor marshalling."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libskewltlt.so")
+
+STATUS = {
+    0: "SKEW_OK",
+    -100: "SKEW_ERR_NONFINITE",
+    -101: "SKEW_ERR_NOMEM",
+    -102: "SKEW_ERR_CUDA",
+    -103: "SKEW_ERR_TIMEOUT",
+    -104: "SKEW_ERR_NODEVICE",
+}
+
+_lock = threading.Lock()
+_lib = None
+
+_i64, _i32, _dbl, _vp, _sz = (ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                              ctypes.c_void_p, ctypes.c_size_t)
+
+SIGNATURES = {
+    "skew_version": ([], _i32),
+    "skew_last_error": ([], ctypes.c_char_p),
+    "skew_kernel_launches": ([], ctypes.c_uint64),
+    "skew_trim_memory": ([], _i32),
+    "skew_default_nb": ([_i64], _i32),
+    "skew_workspace_bytes": ([_i64, _i32, _i32], _sz),
+    "skew_ltlt": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
+    "skew_pfaffian": ([_i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
+    "skew_pfaffian_from_factors": ([_i64, _vp, _vp, _vp, _vp, _vp], _i32),
+    "skew_rank2k": ([_i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _vp], _i32),
+    "skew_tridiag_rankk": ([_i64, _i64, _dbl, _vp, _i64, _vp, _dbl, _vp, _i64, _vp], _i32),
+    "skew_ltlt_host": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32], _i32),
+}
+
+
+class SkewError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        if status < 0 and -status < 100:
+            what = f"argument {-status} is invalid"
+        else:
+            what = STATUS.get(status, str(status))
+        detail = ""
+        if status == -102 and _lib is not None:
+            detail = ": " + _lib.skew_last_error().decode()
+        super().__init__(f"{fn} failed with {status} ({what}){detail}")
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with "
+                    "`python -m paper_2411_09859_gb300.build`")
+            try:
+                import torch  # noqa: F401  (loads the CUDA runtime torch uses first)
+            except ImportError:
+                pass
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+        return _lib
+
+
+def _check(fn: str, status: int):
+    if status != 0:
+        raise SkewError(fn, status)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def fortran_empty(rows: int, cols: int, device=None, dtype=None):
+    """Uninitialised column-major (rows x cols) CUDA tensor (stride(0) == 1)."""
+    import torch
+    dtype = dtype or torch.float64
+    device = device or "cuda"
+    return torch.empty((cols, rows), dtype=dtype, device=device).t()
+
+
+def _colmajor(name: str, M, rows: int):
+    import torch
+    if not M.is_cuda or M.dtype != torch.float64:
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if M.dim() != 2 or M.shape[0] != rows:
+        raise ValueError(f"{name} must have {rows} rows")
+    if M.shape[1] > 1 and M.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1)")
+    return max(M.stride(1) if M.shape[1] > 1 else rows, 1)
+
+
+def kernel_launches() -> int:
+    return int(lib().skew_kernel_launches())
+
+
+def default_nb(n: int) -> int:
+    return int(lib().skew_default_nb(n))
+
+
+def workspace_bytes(n: int, nb: int = 0, with_L: bool = True) -> int:
+    return int(lib().skew_workspace_bytes(n, nb, 1 if with_L else 0))
+
+
+def trim_memory():
+    _check("skew_trim_memory", lib().skew_trim_memory())
+
+
+def ltlt(A, nb: int = 0, stream=None, L=None, t=None, piv=None, info=None, workspace=None):
+    """P A P^T = L T L^T of the column-major float64 CUDA tensor ``A`` (destroyed).
+
+    Returns ``(L, t, piv, info)`` as CUDA tensors (L column-major n x n, t (n-1,),
+    piv int32 (n,), info int32 (1,)).  Asynchronous on ``stream``.
+    """
+    import torch
+    n = A.shape[0]
+    lda = _colmajor("A", A, n)
+    L = fortran_empty(n, n, A.device) if L is None else L
+    ldl = _colmajor("L", L, n)
+    t = torch.empty(max(n - 1, 0), dtype=torch.float64, device=A.device) if t is None else t
+    piv = torch.empty(n, dtype=torch.int32, device=A.device) if piv is None else piv
+    info = torch.empty(1, dtype=torch.int32, device=A.device) if info is None else info
+    ws, wsb = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
+    st = lib().skew_ltlt(n, _ptr(A), lda, _ptr(L), ldl, _ptr(t) if n > 1 else None,
+                         _ptr(piv), _ptr(info), nb, ws, wsb, _stream_handle(stream))
+    _check("skew_ltlt", st)
+    return L, t, piv, info
+
+
+def pfaffian(A, nb: int = 0, stream=None, t=None, piv=None, info=None, workspace=None):
+    """log|Pf(A)| and sign through the factorization (A destroyed).
+
+    Returns ``(logabs, sign, t, piv, info)`` CUDA tensors (logabs float64 (1,),
+    sign int32 (1,)).
+    """
+    import torch
+    n = A.shape[0]
+    lda = _colmajor("A", A, n)
+    dev = A.device
+    logabs = torch.empty(1, dtype=torch.float64, device=dev)
+    sign = torch.empty(1, dtype=torch.int32, device=dev)
+    t = torch.empty(max(n - 1, 0), dtype=torch.float64, device=dev) if t is None else t
+    piv = torch.empty(n, dtype=torch.int32, device=dev) if piv is None else piv
+    info = torch.empty(1, dtype=torch.int32, device=dev) if info is None else info
+    ws, wsb = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
+    st = lib().skew_pfaffian(n, _ptr(A), lda, _ptr(logabs), _ptr(sign),
+                             _ptr(t) if n > 1 else None, _ptr(piv) if n > 0 else None,
+                             _ptr(info), nb, ws, wsb, _stream_handle(stream))
+    _check("skew_pfaffian", st)
+    return logabs, sign, t, piv, info
+
+
+def pfaffian_from_factors(t, piv, n: int, stream=None):
+    import torch
+    dev = piv.device
+    logabs = torch.empty(1, dtype=torch.float64, device=dev)
+    sign = torch.empty(1, dtype=torch.int32, device=dev)
+    st = lib().skew_pfaffian_from_factors(n, _ptr(t) if n > 1 else None,
+                                          _ptr(piv) if n > 0 else None, _ptr(logabs),
+                                          _ptr(sign), _stream_handle(stream))
+    _check("skew_pfaffian_from_factors", st)
+    return logabs, sign
+
+
+def rank2k(alpha: float, X, Y, beta: float, C, stream=None):
+    """C := beta C + alpha (X Y^T - Y X^T) on the strictly lower triangle (in place)."""
+    m = C.shape[0]
+    k = X.shape[1]
+    ldx = _colmajor("X", X, m)
+    ldy = _colmajor("Y", Y, m)
+    ldc = _colmajor("C", C, m)
+    st = lib().skew_rank2k(m, k, float(alpha), _ptr(X), ldx, _ptr(Y), ldy, float(beta),
+                           _ptr(C), ldc, _stream_handle(stream))
+    _check("skew_rank2k", st)
+    return C
+
+
+def tridiag_rankk(alpha: float, A, t, beta: float, C, stream=None):
+    """C := beta C + alpha A T A^T on the strictly lower triangle (in place)."""
+    m = C.shape[0]
+    b = A.shape[1]
+    lda = _colmajor("A", A, m)
+    ldc = _colmajor("C", C, m)
+    st = lib().skew_tridiag_rankk(m, b, float(alpha), _ptr(A), lda,
+                                  _ptr(t) if b > 1 else None, float(beta), _ptr(C), ldc,
+                                  _stream_handle(stream))
+    _check("skew_tridiag_rankk", st)
+    return C
+
+
+def ltlt_host(A: np.ndarray, want_L: bool = True, nb: int = 0):
+    """Host-buffer convenience call: returns numpy (L or None, t, piv, logabs, sign, info).
+
+    ``A`` is a float64 numpy array (any order; its strictly lower triangle is read).
+    """
+    n = A.shape[0]
+    Af = np.asfortranarray(A, dtype=np.float64)
+    L = np.zeros((n, n), dtype=np.float64, order="F") if want_L else None
+    t = np.zeros(max(n - 1, 1), dtype=np.float64)
+    piv = np.zeros(max(n, 1), dtype=np.int32)
+    logabs = ctypes.c_double(0.0)
+    sign = ctypes.c_int32(0)
+    info = ctypes.c_int32(0)
+    ld = max(n, 1)
+    st = lib().skew_ltlt_host(n, ctypes.c_void_p(Af.ctypes.data), ld,
+                              None if L is None else ctypes.c_void_p(L.ctypes.data), ld,
+                              ctypes.c_void_p(t.ctypes.data), ctypes.c_void_p(piv.ctypes.data),
+                              ctypes.byref(logabs), ctypes.byref(sign), ctypes.byref(info), nb)
+    _check("skew_ltlt_host", st)
+    return L, t[: max(n - 1, 0)], piv[:n], logabs.value, sign.value, info.value

@@ -1,0 +1,461 @@
+// api.cu -- the C ABI (include/skewltlt.h): argument checks, workspace, and the
+// panel loop of the pivoted blocked right-looking factorization.
+//
+// Per panel k0 .. kend-1 (Section 4.2 Variant 1 with the pivoted panel of
+// Section 5.2), all enqueued on the caller's stream with no host synchronisation:
+//   1. panel kernel (cooperative): the nb pivoted left-looking steps, then the
+//      updated column x = X[kend+1:, kend] for the fused trailing update;
+//   2. pivot_rows on the L columns left of the panel (skipped when L is not kept);
+//   3. skew rank-2k trailing update of X[kend+1:, kend+1:] (Fused pairs).
+// Then one kernel reads off log|Pf|, its sign and the info word.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace skew {
+
+static std::atomic<uint64_t> g_launches{0};
+static thread_local char g_last_error[256] = "";
+
+void note_launches(uint64_t count) { g_launches.fetch_add(count); }
+
+void set_last_error(cudaError_t e) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", cudaGetErrorName(e),
+             cudaGetErrorString(e));
+}
+
+int check_launch() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_last_error(e);
+        return SKEW_ERR_CUDA;
+    }
+    return SKEW_OK;
+}
+
+// ------------------------------------------------------------------ per-device state
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_dev_mutex;
+DeviceInfo g_dev[kMaxDevices];
+bool g_dev_ready[kMaxDevices];
+cudaMemPool_t g_pool[kMaxDevices];
+bool g_pool_ready[kMaxDevices];
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Library-private stream-ordered pool: freed blocks stay reserved for reuse (release
+// threshold = max), so repeated calls do not map and unmap device memory.
+int device_pool(int dev, cudaMemPool_t *out) {
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    if (!g_pool_ready[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        SKEW_TRY(cudaMemPoolCreate(&g_pool[dev], &props));
+        uint64_t thr = UINT64_MAX;
+        SKEW_TRY(cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &thr));
+        g_pool_ready[dev] = true;
+    }
+    *out = g_pool[dev];
+    return SKEW_OK;
+}
+
+int pool_alloc(void **p, size_t bytes, cudaStream_t st) {
+    int dev;
+    SKEW_TRY(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    SKEW_TRY_STATUS(device_pool(dev, &pool));
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes ? bytes : 256, pool, st);
+    if (e != cudaSuccess) {
+        set_last_error(e);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? SKEW_ERR_NOMEM : SKEW_ERR_CUDA;
+    }
+    return SKEW_OK;
+}
+}  // namespace
+
+int current_device_info(DeviceInfo *out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return SKEW_ERR_NODEVICE;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_dev_mutex);
+        if (g_dev_ready[dev]) {
+            *out = g_dev[dev];
+            return SKEW_OK;
+        }
+    }
+    int major = 0, minor = 0, sms = 0;
+    SKEW_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+    SKEW_TRY(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+    SKEW_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (major != 10 || minor != 3) return SKEW_ERR_NODEVICE;
+    int bps = 0;
+    SKEW_TRY_STATUS(panel_max_blocks_per_sm(&bps));
+    if (bps < 1) return SKEW_ERR_CUDA;
+    DeviceInfo di;
+    di.device = dev;
+    di.sms = sms;
+    di.panel_grid_max = sms;                       // one panel CTA per SM
+    if (di.panel_grid_max > kMaxPanelGrid) di.panel_grid_max = kMaxPanelGrid;
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    g_dev[dev] = di;
+    g_dev_ready[dev] = true;
+    *out = di;
+    return SKEW_OK;
+}
+
+WsLayout workspace_layout(int64_t n, int nb, bool with_L) {
+    WsLayout w;
+    size_t off = 0;
+    w.ctrl = off;
+    off += align256(sizeof(Ctrl));
+    w.partials = off;
+    off += align256(sizeof(ArgmaxPartial) * kMaxPanelGrid);
+    w.tbuf = off;
+    off += align256(sizeof(double) * (size_t)(n > 1 ? n : 1));
+    w.pivbuf = off;
+    off += align256(sizeof(int32_t) * (size_t)(n > 1 ? n : 1));
+    w.lbuf = off;
+    if (!with_L) off += align256(sizeof(double) * (size_t)(n > 1 ? n : 1) * (size_t)nb);
+    w.total = off;
+    return w;
+}
+
+// ------------------------------------------------------------------ the factorization
+namespace {
+
+int panel_grid_for(const DeviceInfo &di, int64_t n) {
+    int64_t g = (n + 127) / 128;
+    if (g < 1) g = 1;
+    if (g > di.panel_grid_max) g = di.panel_grid_max;
+    return (int)g;
+}
+
+int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
+           int32_t *piv, int32_t *info, double *logabs, int32_t *sign, int nb,
+           void *workspace, size_t workspace_bytes, cudaStream_t st, bool with_L) {
+    DeviceInfo di;
+    SKEW_TRY_STATUS(current_device_info(&di));
+    if (nb == 0) nb = skew_default_nb(n);
+    const WsLayout lay = workspace_layout(n, nb, with_L);
+    char *base = static_cast<char *>(workspace);
+    bool own = false;
+    if (base == nullptr) {
+        SKEW_TRY_STATUS(pool_alloc(reinterpret_cast<void **>(&base), lay.total, st));
+        own = true;
+    } else if (workspace_bytes < lay.total) {
+        return -11;
+    }
+    int status = SKEW_OK;
+    Ctrl *ctrl = reinterpret_cast<Ctrl *>(base + lay.ctrl);
+    ArgmaxPartial *part = reinterpret_cast<ArgmaxPartial *>(base + lay.partials);
+    if (t == nullptr) t = reinterpret_cast<double *>(base + lay.tbuf);
+    if (piv == nullptr) piv = reinterpret_cast<int32_t *>(base + lay.pivbuf);
+    double *Lbuf = with_L ? nullptr : reinterpret_cast<double *>(base + lay.lbuf);
+
+    do {
+        cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
+        if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+        status = launch_prologue(n, A, lda, with_L ? L : nullptr, ldl, piv, ctrl, st);
+        if (status != SKEW_OK) break;
+        const int G = panel_grid_for(di, n);
+        for (int64_t k0 = 0; k0 < n - 1 && status == SKEW_OK;) {
+            const int64_t kend = (k0 + nb < n - 1) ? k0 + nb : n - 1;
+            const int64_t s = kend;
+            const bool with_x = s < n - 1;
+            PanelArgs pa;
+            pa.X = A;
+            pa.ldx = lda;
+            if (with_L) {
+                pa.Lp = L + (k0 + 1) * ldl;
+                pa.ldl = ldl;
+            } else {
+                pa.Lp = Lbuf;
+                pa.ldl = n;
+            }
+            pa.t = t;
+            pa.piv = piv;
+            pa.ctrl = ctrl;
+            pa.part = part;
+            pa.n = (int)n;
+            pa.k0 = (int)k0;
+            pa.kend = (int)kend;
+            pa.with_x = with_x ? 1 : 0;
+            status = launch_panel(pa, G, st);
+            if (status != SKEW_OK) break;
+            if (with_L && k0 >= 1) {
+                status = launch_pivot_rows(n, L, ldl, piv, (int)k0, (int)kend, st);
+                if (status != SKEW_OK) break;
+            }
+            if (with_x) {
+                Skr2kArgs sa;
+                sa.m = n - s - 1;
+                sa.C = A + (s + 1) + (s + 1) * lda;
+                sa.ldc = lda;
+                sa.alpha = 1.0;
+                sa.beta = 1.0;
+                sa.P = pa.Lp + (s + 1);
+                sa.ldp = pa.ldl;
+                sa.Q = nullptr;
+                sa.ldq = 0;
+                sa.tt = t + k0 + 1;
+                sa.x = A + (s + 1) + s * lda;
+                sa.b = kend - k0;
+                status = launch_skr2k(PairKind::Fused, sa, st);
+            }
+            k0 = kend;
+        }
+        if (status != SKEW_OK) break;
+        status = launch_finish(n, t, piv, ctrl, logabs, sign, info, st);
+    } while (0);
+
+    if (own) {
+        cudaError_t e = cudaFreeAsync(base, st);
+        if (e != cudaSuccess && status == SKEW_OK) {
+            set_last_error(e);
+            status = SKEW_ERR_CUDA;
+        }
+    }
+    return status;
+}
+
+}  // namespace
+}  // namespace skew
+
+using namespace skew;
+
+extern "C" {
+
+int skew_version(void) { return 100; }   // 0.1.0
+
+const char *skew_last_error(void) { return g_last_error; }
+
+uint64_t skew_kernel_launches(void) { return g_launches.load(); }
+
+int skew_default_nb(int64_t n) {
+    if (n <= 256) return 16;
+    if (n <= 2048) return 32;
+    return 64;
+}
+
+size_t skew_workspace_bytes(int64_t n, int nb, int with_L) {
+    if (n < 0) return 0;
+    if (nb <= 0) nb = skew_default_nb(n);
+    if (nb > kMaxNb) nb = kMaxNb;
+    return workspace_layout(n, nb, with_L != 0).total;
+}
+
+int skew_trim_memory(void) {
+    int dev;
+    SKEW_TRY(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    SKEW_TRY_STATUS(device_pool(dev, &pool));
+    SKEW_TRY(cudaMemPoolTrimTo(pool, 0));
+    return SKEW_OK;
+}
+
+int skew_ltlt(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
+              int32_t *piv, int32_t *info, int nb, void *workspace,
+              size_t workspace_bytes, void *stream) {
+    if (n < 0 || n > kMaxOrder) return -1;
+    const int64_t ld_min = n > 1 ? n : 1;
+    if (A == nullptr && n > 0) return -2;
+    if (lda < ld_min) return -3;
+    if (L == nullptr && n > 0) return -4;
+    if (ldl < ld_min) return -5;
+    if (t == nullptr && n >= 2) return -6;
+    if (piv == nullptr && n >= 1) return -7;
+    if (nb < 0 || nb > kMaxNb) return -9;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n == 0) {
+        if (info) SKEW_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
+        return SKEW_OK;
+    }
+    return factor(n, A, lda, L, ldl, t, piv, info, nullptr, nullptr, nb, workspace,
+                  workspace_bytes, st, true);
+}
+
+int skew_pfaffian(int64_t n, double *A, int64_t lda, double *logabs, int32_t *sign,
+                  double *t, int32_t *piv, int32_t *info, int nb, void *workspace,
+                  size_t workspace_bytes, void *stream) {
+    if (n < 0 || n > kMaxOrder) return -1;
+    const int64_t ld_min = n > 1 ? n : 1;
+    if (A == nullptr && n > 0) return -2;
+    if (lda < ld_min) return -3;
+    if (logabs == nullptr) return -4;
+    if (sign == nullptr) return -5;
+    if (nb < 0 || nb > kMaxNb) return -9;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n == 0) {
+        // Pf of the empty matrix is 1
+        DeviceInfo di;
+        SKEW_TRY_STATUS(current_device_info(&di));
+        SKEW_TRY_STATUS(launch_finish(0, nullptr, nullptr, nullptr, logabs, sign, info, st));
+        return SKEW_OK;
+    }
+    return factor(n, A, lda, nullptr, 0, t, piv, info, logabs, sign, nb, workspace,
+                  workspace_bytes, st, false);
+}
+
+int skew_pfaffian_from_factors(int64_t n, const double *t, const int32_t *piv,
+                               double *logabs, int32_t *sign, void *stream) {
+    if (n < 0 || n > kMaxOrder) return -1;
+    if (t == nullptr && n >= 2) return -2;
+    if (piv == nullptr && n >= 1) return -3;
+    if (logabs == nullptr) return -4;
+    if (sign == nullptr) return -5;
+    DeviceInfo di;
+    SKEW_TRY_STATUS(current_device_info(&di));
+    return launch_finish(n, t, piv, nullptr, logabs, sign, nullptr,
+                         static_cast<cudaStream_t>(stream));
+}
+
+int skew_rank2k(int64_t m, int64_t k, double alpha, const double *X, int64_t ldx,
+                const double *Y, int64_t ldy, double beta, double *C, int64_t ldc,
+                void *stream) {
+    if (m < 0 || m > kMaxOrder) return -1;
+    if (k < 0) return -2;
+    const int64_t ld_min = m > 1 ? m : 1;
+    const bool need_ops = m > 1 && k > 0;
+    if (X == nullptr && need_ops) return -4;
+    if (ldx < ld_min) return -5;
+    if (Y == nullptr && need_ops) return -6;
+    if (ldy < ld_min) return -7;
+    if (C == nullptr && m > 1) return -9;
+    if (ldc < ld_min) return -10;
+    if (m <= 1) return SKEW_OK;
+    DeviceInfo di;
+    SKEW_TRY_STATUS(current_device_info(&di));
+    Skr2kArgs sa;
+    sa.m = m;
+    sa.C = C;
+    sa.ldc = ldc;
+    sa.alpha = alpha;
+    sa.beta = beta;
+    sa.P = X;
+    sa.ldp = ldx;
+    sa.Q = Y;
+    sa.ldq = ldy;
+    sa.tt = nullptr;
+    sa.x = nullptr;
+    sa.b = k;
+    return launch_skr2k(PairKind::Rank2k, sa, static_cast<cudaStream_t>(stream));
+}
+
+int skew_tridiag_rankk(int64_t m, int64_t b, double alpha, const double *A,
+                       int64_t lda, const double *t, double beta, double *C,
+                       int64_t ldc, void *stream) {
+    if (m < 0 || m > kMaxOrder) return -1;
+    if (b < 0) return -2;
+    const int64_t ld_min = m > 1 ? m : 1;
+    const bool need_ops = m > 1 && b > 1;
+    if (A == nullptr && need_ops) return -4;
+    if (lda < ld_min) return -5;
+    if (t == nullptr && need_ops) return -6;
+    if (C == nullptr && m > 1) return -8;
+    if (ldc < ld_min) return -9;
+    if (m <= 1) return SKEW_OK;
+    DeviceInfo di;
+    SKEW_TRY_STATUS(current_device_info(&di));
+    Skr2kArgs sa;
+    sa.m = m;
+    sa.C = C;
+    sa.ldc = ldc;
+    sa.alpha = -alpha;            // A T A^T = -sum_j (a_j w_j^T - w_j a_j^T)
+    sa.beta = beta;
+    sa.P = A;
+    sa.ldp = lda;
+    sa.Q = nullptr;
+    sa.ldq = 0;
+    sa.tt = t;
+    sa.x = nullptr;
+    sa.b = b;
+    return launch_skr2k(PairKind::Tridiag, sa, static_cast<cudaStream_t>(stream));
+}
+
+int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
+                   int64_t ldl, double *t_host, int32_t *piv_host, double *logabs,
+                   int32_t *sign, int32_t *info, int nb) {
+    if (n < 0 || n > kMaxOrder) return -1;
+    const int64_t ld_min = n > 1 ? n : 1;
+    if (A_host == nullptr && n > 0) return -2;
+    if (lda < ld_min) return -3;
+    if (L_host != nullptr && ldl < ld_min) return -5;
+    if (nb < 0 || nb > kMaxNb) return -11;
+    DeviceInfo di;
+    SKEW_TRY_STATUS(current_device_info(&di));
+    cudaStream_t st;
+    SKEW_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    double *dA = nullptr, *dL = nullptr, *dt = nullptr, *dlog = nullptr;
+    int32_t *dpiv = nullptr, *dsign = nullptr, *dinfo = nullptr;
+    int status = SKEW_OK;
+    double h_log = 0.0;
+    int32_t h_sign = 0, h_info = 0;
+    do {
+        if ((status = pool_alloc((void **)&dA, nn * nn * sizeof(double), st))) break;
+        if (L_host && (status = pool_alloc((void **)&dL, nn * nn * sizeof(double), st))) break;
+        if ((status = pool_alloc((void **)&dt, nn * sizeof(double), st))) break;
+        if ((status = pool_alloc((void **)&dpiv, nn * sizeof(int32_t), st))) break;
+        if ((status = pool_alloc((void **)&dlog, sizeof(double), st))) break;
+        if ((status = pool_alloc((void **)&dsign, sizeof(int32_t), st))) break;
+        if ((status = pool_alloc((void **)&dinfo, sizeof(int32_t), st))) break;
+        cudaError_t e = cudaSuccess;
+        if (n > 0)
+            e = cudaMemcpy2DAsync(dA, n * sizeof(double), A_host, lda * sizeof(double),
+                                  n * sizeof(double), n, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+        if (L_host) {
+            status = skew_ltlt(n, dA, ld_min, dL, ld_min, dt, dpiv, dinfo, nb, nullptr, 0, st);
+            if (status == SKEW_OK) status = skew_pfaffian_from_factors(n, dt, dpiv, dlog, dsign, st);
+        } else {
+            status = skew_pfaffian(n, dA, ld_min, dlog, dsign, dt, dpiv, dinfo, nb, nullptr, 0, st);
+        }
+        if (status != SKEW_OK) break;
+        if (L_host && n > 0)
+            e = cudaMemcpy2DAsync(L_host, ldl * sizeof(double), dL, n * sizeof(double),
+                                  n * sizeof(double), n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && t_host && n > 1)
+            e = cudaMemcpyAsync(t_host, dt, (n - 1) * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && piv_host && n > 0)
+            e = cudaMemcpyAsync(piv_host, dpiv, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&h_log, dlog, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&h_sign, dsign, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&h_info, dinfo, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+    } while (0);
+    void *bufs[] = {dA, dL, dt, dlog, dpiv, dsign, dinfo};
+    for (void *b : bufs)
+        if (b) cudaFreeAsync(b, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess && status == SKEW_OK) {
+        set_last_error(e);
+        status = SKEW_ERR_CUDA;
+    }
+    cudaStreamDestroy(st);
+    if (status == SKEW_OK) {
+        if (n == 0) {   // empty factorization: Pf = 1
+            h_info = 0;
+        }
+        if (logabs) *logabs = h_log;
+        if (sign) *sign = h_sign;
+        if (info) *info = h_info;
+    }
+    return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,188 @@
+// common.cuh -- internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "skewltlt.h"
+
+namespace skew {
+
+// ------------------------------------------------------------------ host bookkeeping
+void note_launches(uint64_t count);           // adds to skew_kernel_launches()
+void set_last_error(cudaError_t e);           // records for skew_last_error()
+int check_launch();                           // cudaGetLastError -> SKEW_OK / ERR_CUDA
+
+#define SKEW_TRY(call)                                     \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) {                           \
+            ::skew::set_last_error(e_);                    \
+            return SKEW_ERR_CUDA;                          \
+        }                                                  \
+    } while (0)
+
+#define SKEW_TRY_STATUS(expr)                              \
+    do {                                                   \
+        int s_ = (expr);                                   \
+        if (s_ != SKEW_OK) return s_;                      \
+    } while (0)
+
+struct DeviceInfo {
+    int device;
+    int sms;              // multiprocessors
+    int panel_grid_max;   // co-resident CTAs of the panel kernel (cooperative limit)
+};
+// Properties of the current device; SKEW_ERR_NODEVICE unless it is an sm_103 part.
+int current_device_info(DeviceInfo *out);
+
+// ------------------------------------------------------------------ device control block
+// Lives at the start of every workspace.  Zeroed (cudaMemsetAsync) at the start of
+// each factorization.
+struct Ctrl {
+    unsigned int bar_count;   // grid barrier: CTAs arrived in the current round
+    unsigned int bar_gen;     // grid barrier: completed rounds
+    int err;                  // first device-detected error status (0 = none)
+    int pad0;
+    double vtop;              // panel: v[k+1] of the current step, before the exchange
+    double pad1[5];
+};
+
+struct ArgmaxPartial {       // one per panel CTA
+    double val;               // signed v at the CTA's best row
+    int idx;                  // that row (INT32_MAX if none)
+    int pad;
+};
+
+constexpr int kPanelThreads = 256;
+constexpr int kMaxPanelGrid = 1024;
+constexpr int kMaxNb = 256;
+constexpr int64_t kMaxOrder = int64_t(1) << 22;   // keeps every tile count below 2^31
+
+// Workspace layout (byte offsets), see workspace_layout().
+struct WsLayout {
+    size_t ctrl, partials, tbuf, pivbuf, lbuf, total;
+};
+WsLayout workspace_layout(int64_t n, int nb, bool with_L);
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int *p) {
+    return *reinterpret_cast<const volatile int *>(p);
+}
+
+// Record the first device-side error (later ones are dropped).
+__device__ __forceinline__ void raise_error(Ctrl *c, int status) {
+    atomicCAS(&c->err, 0, status);
+}
+
+// Grid-wide barrier for a cooperative launch of `nblocks` CTAs.  `gen` is the
+// caller's copy of the barrier generation (read once at kernel entry).  Every wait
+// is bounded: after kBarrierTimeoutNs the CTA records SKEW_ERR_TIMEOUT and returns
+// false; a CTA also returns false as soon as any error has been recorded, so all
+// CTAs leave promptly.  Returns true when the barrier completed normally.
+constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned int nblocks,
+                                             unsigned int &gen) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned int target = gen + 1;
+        __threadfence();
+        unsigned int arrived = atomicAdd(&c->bar_count, 1u) + 1u;
+        if (arrived == nblocks) {
+            atomicExch(&c->bar_count, 0u);
+            __threadfence();
+            st_release_u32(&c->bar_gen, target);
+        } else {
+            uint64_t t0 = 0;
+            unsigned int polls = 0;
+            while (ld_acquire_u32(&c->bar_gen) != target) {
+                if (ld_volatile_i32(&c->err) != 0) { ok = 0; break; }
+                if ((++polls & 255u) == 0u) {
+                    uint64_t now = global_ns();
+                    if (t0 == 0) t0 = now;
+                    else if (now - t0 > kBarrierTimeoutNs) {
+                        raise_error(c, SKEW_ERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        gen = target;
+        if (ld_volatile_i32(&c->err) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ------------------------------------------------------------------ kernel launchers
+// (each returns SKEW_OK or a negative status; they count their own launches)
+
+// Sets L := identity (when L != nullptr), piv := 0..n-1, and flags a non-finite
+// strictly-lower entry of A in ctrl->err.
+int launch_prologue(int64_t n, const double *A, int64_t lda, double *L, int64_t ldl,
+                    int32_t *piv, Ctrl *ctrl, cudaStream_t stream);
+
+// One pivoted left-looking panel: steps k = k0 .. kend-1; with `with_x`, also forms
+// the updated column X[kend+1:, kend].  Lp points at L column k0+1 (stride ldl).
+struct PanelArgs {
+    double *X;
+    int64_t ldx;
+    double *Lp;
+    int64_t ldl;
+    double *t;
+    int32_t *piv;
+    Ctrl *ctrl;
+    ArgmaxPartial *part;
+    int n, k0, kend, with_x;
+};
+int launch_panel(const PanelArgs &a, int grid, cudaStream_t stream);
+int panel_max_blocks_per_sm(int *out);
+
+// Row exchanges piv[k+1] <-> k+1, k = k0 .. kend-1 in order, on L columns 1 .. k0.
+int launch_pivot_rows(int64_t n, double *L, int64_t ldl, const int32_t *piv, int k0,
+                      int kend, cudaStream_t stream);
+
+// Trailing update kinds of the skew rank-2k tile kernel.
+enum class PairKind { Rank2k = 0, Tridiag = 1, Fused = 2 };
+struct Skr2kArgs {
+    int64_t m;             // order of the updated skew block C
+    double *C;
+    int64_t ldc;
+    double alpha, beta;    // C := beta C + alpha * sum_p (a_p w_p^T - w_p a_p^T)
+    const double *P;       // Rank2k: the a columns; Tridiag/Fused: the A columns
+    int64_t ldp;
+    const double *Q;       // Rank2k: the w columns
+    int64_t ldq;
+    const double *tt;      // Tridiag/Fused: sub-diagonal of T (b-1 values)
+    const double *x;       // Fused: the updated column x (m values)
+    int64_t b;             // Rank2k: k; Tridiag/Fused: number of A columns
+};
+int launch_skr2k(PairKind kind, const Skr2kArgs &a, cudaStream_t stream);
+
+// log|Pf|, sign (either may be null), and the final info word (may be null).
+int launch_finish(int64_t n, const double *t, const int32_t *piv, const Ctrl *ctrl,
+                  double *logabs, int32_t *sign, int32_t *info, cudaStream_t stream);
+
+}  // namespace skew

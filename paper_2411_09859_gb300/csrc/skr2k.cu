@@ -1,0 +1,194 @@
+// skr2k.cu -- skew-symmetric rank-2k update of a strictly lower triangle on FP64
+// tensor cores (DMMA, mma.sync.m8n8k4.f64).
+//
+//     C := beta C + alpha * sum_p (a_p w_p^T - w_p a_p^T),   strictly lower part only
+//
+// evaluated as the GEMM  C += U V^T  with U = [a_1 .. a_K, -w_1 .. -w_K] and
+// V = [w_1 .. w_K, a_1 .. a_K] restricted to lower tiles (skew_rank2k, table of
+// BLAS-like operations, Section 4.2).  The pairs (a_p, w_p) come from:
+//
+//   Rank2k  : a_p = X[:, p], w_p = Y[:, p].
+//   Tridiag : A T A^T with T = S - S^T (Section 2.2 theorem): W = A S has only odd
+//             columns, w_j = t[j] a_{j+1} - t[j-1] a_{j-1} (j odd, a_b := 0), and
+//             A T A^T = W A^T - A W^T = -sum_{j odd} (a_j w_j^T - w_j a_j^T); so the
+//             pairs are (a_j, w_j) with the sign folded into alpha.  This is the
+//             "form W after the panel" two-step route of Section 4.2.
+//   Fused   : the trailing update of one panel of the blocked right-looking
+//             algorithm (Section 4.2 Variant 1): X44 -= A T_p A^T followed by the
+//             last Gauss transform X44 += l x^T - x l^T, where l is A's last column
+//             and x the already updated column.  Both are one update: the pairs of
+//             Tridiag with x added to w_{b-1} when b is even (l = a_{b-1} is then
+//             already a pair), or the extra pair (a_{b-1}, x) when b is odd.
+//
+// W is never stored: each CTA forms the pair columns of its row block while it
+// stages them into shared memory (the GPU counterpart of forming T A^T while
+// packing, Section 4.3).  FP64 throughput on this part is what bounds the kernel
+// (about 1 TFLOP/s for the whole GPU), so the tile loop is kept simple: 64 x 64
+// CTA tiles, four warps of 32 x 32, 16 pairs (32 K-columns) staged per round.
+#include <climits>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace skew {
+namespace {
+
+constexpr int BM = 64;            // CTA tile (rows and columns)
+constexpr int PC = 16;            // pairs per staging round
+constexpr int KC = 2 * PC;        // K columns per staging round
+constexpr int LDS = KC + 4;       // padded smem row (doubles): conflict-free fragments
+constexpr int kThreads = 128;     // four warps
+
+template <PairKind KIND>
+struct PairSource {
+    const double *P;
+    int64_t ldp;
+    const double *Q;
+    int64_t ldq;
+    const double *tt;
+    const double *x;
+    int64_t b;
+
+    __device__ __forceinline__ int64_t npairs() const {
+        if (KIND == PairKind::Rank2k) return b;
+        if (KIND == PairKind::Tridiag) return b / 2;
+        return b / 2 + (b & 1);
+    }
+    // (a_p, w_p) at row i (0 <= i < m)
+    __device__ __forceinline__ void get(int64_t p, int64_t i, double &av, double &wv) const {
+        if (KIND == PairKind::Rank2k) {
+            av = P[i + p * ldp];
+            wv = Q[i + p * ldq];
+            return;
+        }
+        const int64_t j = 2 * p + 1;
+        if (j < b) {
+            av = P[i + j * ldp];
+            double w = -tt[j - 1] * P[i + (j - 1) * ldp];
+            if (j + 1 < b) w += tt[j] * P[i + (j + 1) * ldp];
+            if (KIND == PairKind::Fused && j == b - 1) w += x[i];
+            wv = w;
+        } else {                                    // Fused, b odd: (a_{b-1}, x)
+            av = P[i + (b - 1) * ldp];
+            wv = x[i];
+        }
+    }
+};
+
+__device__ __forceinline__ void dmma_8x8x4(double &c0, double &c1, double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                 : "+d"(c0), "+d"(c1)
+                 : "d"(a), "d"(b));
+}
+
+// Lower-triangular tile index -> (bi, bj), bi >= bj, idx = bi (bi + 1) / 2 + bj.
+__device__ __forceinline__ void tri_tile(int64_t idx, int64_t &bi, int64_t &bj) {
+    int64_t r = (int64_t)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
+    while (r * (r + 1) / 2 > idx) --r;
+    while ((r + 1) * (r + 2) / 2 <= idx) ++r;
+    bi = r;
+    bj = idx - r * (r + 1) / 2;
+}
+
+template <PairKind KIND>
+__global__ void __launch_bounds__(kThreads, 2)
+skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
+             PairSource<KIND> src) {
+    __shared__ double Us[BM][LDS];
+    __shared__ double Vs[BM][LDS];
+
+    int64_t bi, bj;
+    tri_tile(blockIdx.x, bi, bj);
+    const int64_t I0 = bi * BM, J0 = bj * BM;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 1, wn = warp >> 1;       // warp quadrant
+    const int g = lane >> 2, tg = lane & 3;        // fragment coordinates
+
+    double acc[4][4][2];
+#pragma unroll
+    for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
+
+    const int64_t np = src.npairs();
+    for (int64_t p0 = 0; p0 < np; p0 += PC) {
+        const int nv = (int)((np - p0) < PC ? (np - p0) : PC);
+        // ---- stage U rows I0.. and V rows J0.. for pairs p0 .. p0+PC-1
+        for (int it = tid; it < BM * PC; it += kThreads) {
+            const int r = it % BM, pp = it / BM;
+            double ai = 0.0, wi = 0.0, aj = 0.0, wj = 0.0;
+            if (pp < nv) {
+                if (I0 + r < m) src.get(p0 + pp, I0 + r, ai, wi);
+                if (J0 + r < m) src.get(p0 + pp, J0 + r, aj, wj);
+            }
+            Us[r][pp] = ai;
+            Us[r][PC + pp] = -wi;
+            Vs[r][pp] = wj;
+            Vs[r][PC + pp] = aj;
+        }
+        __syncthreads();
+        // ---- DMMA over the valid K columns of this round: [a | -w] x [w | a]^T
+        const int ksteps = (nv + 3) / 4;
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+#pragma unroll 1
+            for (int ks = 0; ks < ksteps; ++ks) {
+                const int kc = half * PC + ks * 4 + tg;
+                double af[4], bf[4];
+#pragma unroll
+                for (int mi = 0; mi < 4; ++mi) af[mi] = Us[wm * 32 + mi * 8 + g][kc];
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) bf[ni] = Vs[wn * 32 + ni * 8 + g][kc];
+#pragma unroll
+                for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+                    for (int ni = 0; ni < 4; ++ni)
+                        dmma_8x8x4(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- epilogue: strictly lower entries inside the block
+#pragma unroll
+    for (int mi = 0; mi < 4; ++mi) {
+        const int64_t gi = I0 + wm * 32 + mi * 8 + g;
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int64_t gj = J0 + wn * 32 + ni * 8 + 2 * tg + c;
+                if (gi < m && gj < m && gi > gj) {
+                    double *dst = C + gi + gj * ldc;
+                    const double upd = alpha * acc[mi][ni][c];
+                    *dst = (beta == 0.0) ? upd : ((beta == 1.0) ? *dst + upd : beta * *dst + upd);
+                }
+            }
+        }
+    }
+}
+
+template <PairKind KIND>
+int launch_kind(const Skr2kArgs &a, cudaStream_t stream) {
+    if (a.m <= 1) return SKEW_OK;
+    const int64_t nt = (a.m + BM - 1) / BM;
+    const int64_t tiles = nt * (nt + 1) / 2;
+    if (tiles > INT_MAX) return SKEW_ERR_CUDA;      // unreachable: orders are capped
+    PairSource<KIND> src{a.P, a.ldp, a.Q, a.ldq, a.tt, a.x, a.b};
+    skr2k_kernel<KIND><<<(unsigned)tiles, kThreads, 0, stream>>>(a.m, a.C, a.ldc, a.alpha,
+                                                                  a.beta, src);
+    note_launches(1);
+    return check_launch();
+}
+
+}  // namespace
+
+int launch_skr2k(PairKind kind, const Skr2kArgs &a, cudaStream_t stream) {
+    switch (kind) {
+        case PairKind::Rank2k: return launch_kind<PairKind::Rank2k>(a, stream);
+        case PairKind::Tridiag: return launch_kind<PairKind::Tridiag>(a, stream);
+        default: return launch_kind<PairKind::Fused>(a, stream);
+    }
+}
+
+}  // namespace skew

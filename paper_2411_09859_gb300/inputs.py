@@ -3,8 +3,8 @@
 This module only draws random numbers and lays them out; it holds none of the
 factorization's arithmetic.  Matrices are returned as float64 numpy arrays in
 Fortran (column-major) order holding BOTH triangles of the skew matrix, so a
-caller can hand the same memory to the column-major GPU library and to the CPU
-oracle, and can also form dense products for checks.
+caller can hand the same memory to the column-major GPU library and to a CPU
+implementation, and can also form dense products for checks.
 
 Recipe for the iid Gaussian skew matrices (the paper's experiments use
 "skew-symmetric matrices" of a stated order without a value distribution):
