@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the pivoted skew-symmetric LTL^T factorization (FP64) on GB300.
+
+One step = one whole factorization P A P^T = L T L^T (panel, pivot_rows, skew
+rank-2k update, Pfaffian read-off) of an n = 16384 skew matrix with iid N(0, 1)
+strictly lower entries (seed 3), counted as n^3 / 3 flops.  Inputs are resident in
+HBM before the timed region: one fresh copy per step (2.1 GB each, larger than the
+129 MB L2, so no flush is needed).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank factors its own copy of the matrix (independent
+replicas, no collective on the data path); the barrier and the max over ranks of
+the timed region give the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "skew LTLt FP64 TFLOP/s at n=16384 (% peak); batched Pfaffians/s, p99 latency"
+UNIT = "TFLOP/s"
+FP64_NOMINAL_TFLOPS = 1.25       # GB300 dense FP64 (nominal)
+BF16_NOMINAL_TFLOPS = 2250.0     # GB300 dense bf16 (nominal)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--nb", type=int, default=0)
+    ap.add_argument("--cpu-sample-steps", type=int, default=384,
+                    help="elimination steps of the oracle timed per CPU sample")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def factorization_flops(n: int) -> float:
+    return n ** 3 / 3.0
+
+
+def workload_config(n: int, nb: int, seed: int) -> dict:
+    return {"workload": f"plain pivoted LTL^T, n={n}, iid N(0,1) skew, seed {seed}",
+            "n": n, "nb": nb, "seed": seed, "flops_per_step": "n^3/3",
+            "l2": (f"inputs larger than L2: a fresh {n * n * 8 / 1e9:.2f} GB HBM-resident "
+                   "copy per step"),
+            "parallelism": "independent replicas (one matrix per GPU)"}
+
+
+# ----------------------------------------------------------------------------- peaks
+def fp64_peak():
+    """FP64 tensor peak per the measured bf16 figure x the nominal FP64:bf16 ratio."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    ratio = FP64_NOMINAL_TFLOPS / BF16_NOMINAL_TFLOPS
+    try:
+        with open(path) as f:
+            mp = json.load(f)
+        bf16 = float(mp["bf16_tflops_sustained"])
+        return bf16 * ratio, (f"of measured: bf16_tflops_sustained {bf16} x FP64:bf16 "
+                              f"nominal {FP64_NOMINAL_TFLOPS}/{BF16_NOMINAL_TFLOPS}")
+    except (OSError, KeyError, ValueError):
+        return 1700.0 * ratio, "of fallback: 1.7 PFLOP/s bf16 sustained x 1.25/2250"
+
+
+def recorded_traffic():
+    """DRAM bytes per algorithmic byte of the skr2k kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "skr2k_fused_n4096.md")
+    src = os.path.join(ROOT, "paper_2411_09859_gb300", "csrc", "skr2k.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    m_ratio = re.search(r"dram_bytes_per_algorithmic_byte:\s*([0-9.eE+-]+)", text)
+    if not m_sha or not m_ratio or m_sha.group(1) != sha:
+        return None
+    return float(m_ratio.group(1))
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "note": "nvidia-smi unavailable"}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle
+def oracle_sample(A_host: np.ndarray, sample_steps: int) -> dict:
+    """Time the CPU oracle (as it stands) on the first `sample_steps` elimination
+    steps of this factorization and extrapolate to the whole one by the share of
+    its rank-2 update work (entries updated per step: (n-k-2)(n-k-3)/2)."""
+    import oracle
+    n = A_host.shape[0]
+    X = np.array(A_host, order="F", copy=True)
+    t0 = time.perf_counter()
+    oracle.ltlt(X, nsteps=0, overwrite=True)
+    t_init = time.perf_counter() - t0
+    X = np.array(A_host, order="F", copy=True)
+    t0 = time.perf_counter()
+    oracle.ltlt(X, nsteps=sample_steps, overwrite=True)
+    t_s = time.perf_counter() - t0
+    k = np.arange(n - 1, dtype=np.float64)
+    work = (n - k - 2) * (n - k - 3) / 2.0
+    frac = float(np.sum(work[:sample_steps]) / np.sum(work))
+    t_full = t_init + max(t_s - t_init, 0.0) / frac
+    return {"value": factorization_flops(n) / t_full / 1e12, "unit": UNIT,
+            "cores": oracle.threads(), "kind": "oracle",
+            "sample": (f"first {sample_steps} of {n - 1} elimination steps of the n={n} "
+                       f"factorization ({100 * frac:.1f}% of its update work, "
+                       f"{t_s:.1f} s) plus its O(n^2) set-up ({t_init:.1f} s), "
+                       f"extrapolated to the whole factorization: {t_full:.1f} s"),
+            "seconds_full_estimate": t_full}
+
+
+# ----------------------------------------------------------------------------- dist
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return 0
+    from paper_2411_09859_gb300 import inputs
+    n = args.n
+    seed = inputs.SEED_SCALE.get(n, 3)
+    A_host = inputs.skew_gaussian(n, seed)
+    sample = max(1, min(args.cpu_sample_steps, n - 1))
+    est = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(A_host, sample)
+        if i >= args.warmup:
+            est.append(r["seconds_full_estimate"])
+            last = r
+    t_full = statistics.mean(est)
+    value = factorization_flops(n) / t_full / 1e12
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_full * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(n, args.nb, seed),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"],
+                             "kind": "oracle", "sample": last["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2411_09859_gb300 as skew
+    from paper_2411_09859_gb300 import build as skew_build
+    from paper_2411_09859_gb300 import inputs
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    skew_build.build()
+    dev = torch.device("cuda", local)
+
+    n = args.n
+    seed = inputs.SEED_SCALE.get(n, 3)
+    nb = args.nb if args.nb > 0 else skew.default_nb(n)
+    A_host = inputs.skew_gaussian(n, seed)
+    W, K = args.warmup, args.steps
+    stream = torch.cuda.Stream(device=dev)
+
+    # one fresh HBM-resident copy of A per step, made before the timed region
+    pristine = torch.from_numpy(A_host).to(dev)
+    copies = []
+    for _ in range(W + K):
+        c = skew.fortran_empty(n, n, dev)
+        c.copy_(pristine)
+        copies.append(c)
+    del pristine
+    L = skew.fortran_empty(n, n, dev)
+    t = torch.empty(n - 1, dtype=torch.float64, device=dev)
+    piv = torch.empty(n, dtype=torch.int32, device=dev)
+    info = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(skew.workspace_bytes(n, nb, True), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    def step(A):
+        skew.ltlt(A, nb=nb, stream=stream, L=L, t=t, piv=piv, info=info, workspace=ws)
+
+    for i in range(W):
+        step(copies[i])
+    torch.cuda.synchronize()
+    if int(info.item()) != 0:
+        raise RuntimeError(f"warm-up factorization reported info={int(info.item())}")
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    skew.profile_read()
+    skew.profile_enable(True)
+    launches0 = skew.kernel_launches()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(K):
+        step(copies[W + i])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = skew.kernel_launches() - launches0
+    prof = skew.profile_read()
+    skew.profile_enable(False)
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        tm = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms = float(tm.item())
+    if int(info.item()) != 0:
+        raise RuntimeError(f"timed factorization reported info={int(info.item())}")
+    del copies
+    torch.cuda.empty_cache()
+
+    value = world * K * factorization_flops(n) / (ms / 1e3) / 1e12
+    peak, peak_note = fp64_peak()
+    sk = prof["skr2k"]
+    achieved = sk["flops"] / (sk["ms"] / 1e3) / 1e12 if sk["ms"] > 0 else None
+    ratio = recorded_traffic()
+    traffic = (ratio * sk["bytes"] / sk["launches"]) if (ratio and sk["launches"]) else None
+    kernels = {k: {"ms_per_step": v["ms"] / K, "launches_per_step": v["launches"] / K,
+                   "share": v["ms"] / ms if ms > 0 else None}
+               for k, v in prof.items()}
+    panel = prof["panel"]
+    kernels["panel"]["achieved_gbs"] = (panel["bytes"] / (panel["ms"] / 1e3) / 1e9
+                                        if panel["ms"] > 0 else None)
+
+    # ---- end to end through the host-buffer C-ABI call (pinned host buffers)
+    e2e = None
+    if not args.skip_e2e:
+        A_pin = torch.empty((n, n), dtype=torch.float64).pin_memory().t()
+        A_pin.copy_(torch.from_numpy(A_host))
+        L_pin = torch.empty((n, n), dtype=torch.float64).pin_memory().t()
+        t_pin = torch.empty(n - 1, dtype=torch.float64).pin_memory()
+        p_pin = torch.empty(n, dtype=torch.int32).pin_memory()
+        A_np, L_np, t_np, p_np = A_pin.numpy(), L_pin.numpy(), t_pin.numpy(), p_pin.numpy()
+        skew.ltlt_host(A_np, True, nb, L_out=L_np, t_out=t_np, piv_out=p_np)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            res = skew.ltlt_host(A_np, True, nb, L_out=L_np, t_out=t_np, piv_out=p_np)
+            if res[5] != 0:
+                raise RuntimeError(f"host-buffer factorization reported info={res[5]}")
+        el = time.perf_counter() - t0
+        if world > 1:
+            tm = torch.tensor([el], dtype=torch.float64, device=dev)
+            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+            el = float(tm.item())
+        e2e = {"value": world * K * factorization_flops(n) / el / 1e12, "unit": UNIT,
+               "h2d_bytes_per_step": n * n * 8,
+               "d2h_bytes_per_step": n * n * 8 + (n - 1) * 8 + n * 4 + 8 + 4 + 4,
+               "ms_per_step": el / K * 1e3,
+               "api": "skew_ltlt_host (page-locked host A in, L, t, piv, log|Pf|, sign out)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu_baseline:
+        r = oracle_sample(A_host, max(1, min(args.cpu_sample_steps, n - 1)))
+        cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(n, nb, seed),
+            "pct_of_fp64_peak": 100.0 * (value / world) / peak,
+            "roofline": {"kernel": "skr2k (fused skew rank-2k trailing update, DMMA)",
+                         "bound": "tensor", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s",
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": traffic, "peak_source": peak_note,
+                         "algorithmic_bytes_per_launch": sk["bytes"] / max(sk["launches"], 1),
+                         "algorithmic_flops_per_launch": sk["flops"] / max(sk["launches"], 1)},
+            "kernels": kernels,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

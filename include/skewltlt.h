@@ -73,6 +73,31 @@ uint64_t skew_kernel_launches(void);
  * only when no library work is in flight on the current device. */
 int skew_trim_memory(void);
 
+/*
+ * Per-kernel timing.  While enabled, every kernel launch made by skew_ltlt,
+ * skew_pfaffian, skew_rank2k and skew_tridiag_rankk is bracketed by two CUDA events
+ * recorded on the launch's stream, tagged with the launch's algorithmic work.
+ * skew_profile_read waits for the recorded events, adds up the elapsed times per
+ * kernel kind, and clears the record.  Kinds: 0 prologue, 1 panel, 2 pivot_rows,
+ * 3 skr2k (the skew rank-2k update), 4 finish.
+ *   flops: skr2k counts 4 * (number of pairs) per strictly lower entry of C, i.e.
+ *          2 * npairs * m * (m - 1); panel counts 2 * rows * (columns already formed)
+ *          per step for its skew_tridiag_gemv.
+ *   bytes: skr2k counts reading and writing the strictly lower triangle of C once;
+ *          panel counts, per step, the column read, the L column written and the
+ *          exchanged entries read and written.
+ */
+typedef struct {
+    double ms;          /* summed event time of this kind's launches */
+    double flops;       /* summed algorithmic flops */
+    double bytes;       /* summed algorithmic DRAM bytes */
+    uint64_t launches;  /* number of launches */
+} skew_kernel_stat;
+
+#define SKEW_KIND_COUNT 5
+int skew_profile_enable(int on);
+int skew_profile_read(skew_kernel_stat *stats /* SKEW_KIND_COUNT entries */);
+
 /* Panel width used when `nb` is 0 for a matrix of order n. */
 int skew_default_nb(int64_t n);
 

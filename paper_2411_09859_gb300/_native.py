@@ -30,6 +30,8 @@ SIGNATURES = {
     "skew_last_error": ([], ctypes.c_char_p),
     "skew_kernel_launches": ([], ctypes.c_uint64),
     "skew_trim_memory": ([], _i32),
+    "skew_profile_enable": ([_i32], _i32),
+    "skew_profile_read": ([_vp], _i32),
     "skew_default_nb": ([_i64], _i32),
     "skew_workspace_bytes": ([_i64, _i32, _i32], _sz),
     "skew_ltlt": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
@@ -109,6 +111,28 @@ def _colmajor(name: str, M, rows: int):
     if M.shape[1] > 1 and M.stride(0) != 1:
         raise ValueError(f"{name} must be column-major (stride(0) == 1)")
     return max(M.stride(1) if M.shape[1] > 1 else rows, 1)
+
+
+KIND_NAMES = ["prologue", "panel", "pivot_rows", "skr2k", "finish"]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("launches", ctypes.c_uint64)]
+
+
+def profile_enable(on: bool = True):
+    """Bracket every library kernel launch with CUDA events (see profile_read)."""
+    _check("skew_profile_enable", lib().skew_profile_enable(1 if on else 0))
+
+
+def profile_read() -> dict:
+    """Per kernel kind: summed event ms, algorithmic flops and bytes, launch count
+    since the last read (waits for the recorded events)."""
+    stats = (KernelStat * len(KIND_NAMES))()
+    _check("skew_profile_read", lib().skew_profile_read(ctypes.cast(stats, ctypes.c_void_p)))
+    return {name: {"ms": s.ms, "flops": s.flops, "bytes": s.bytes, "launches": int(s.launches)}
+            for name, s in zip(KIND_NAMES, stats)}
 
 
 def kernel_launches() -> int:
@@ -209,16 +233,24 @@ def tridiag_rankk(alpha: float, A, t, beta: float, C, stream=None):
     return C
 
 
-def ltlt_host(A: np.ndarray, want_L: bool = True, nb: int = 0):
+def ltlt_host(A: np.ndarray, want_L: bool = True, nb: int = 0, L_out=None, t_out=None,
+              piv_out=None):
     """Host-buffer convenience call: returns numpy (L or None, t, piv, logabs, sign, info).
 
     ``A`` is a float64 numpy array (any order; its strictly lower triangle is read).
+    ``L_out`` (n x n Fortran-ordered float64), ``t_out`` (n-1 float64) and
+    ``piv_out`` (n int32) may be given to receive the results (e.g. page-locked).
     """
     n = A.shape[0]
     Af = np.asfortranarray(A, dtype=np.float64)
-    L = np.zeros((n, n), dtype=np.float64, order="F") if want_L else None
-    t = np.zeros(max(n - 1, 1), dtype=np.float64)
-    piv = np.zeros(max(n, 1), dtype=np.int32)
+    if want_L:
+        L = np.zeros((n, n), dtype=np.float64, order="F") if L_out is None else L_out
+        if not (L.flags.f_contiguous and L.dtype == np.float64 and L.shape == (n, n)):
+            raise ValueError("L_out must be an n x n Fortran-ordered float64 array")
+    else:
+        L = None
+    t = np.zeros(max(n - 1, 1), dtype=np.float64) if t_out is None else t_out
+    piv = np.zeros(max(n, 1), dtype=np.int32) if piv_out is None else piv_out
     logabs = ctypes.c_double(0.0)
     sign = ctypes.c_int32(0)
     info = ctypes.c_int32(0)

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -35,6 +36,68 @@ int check_launch() {
     }
     return SKEW_OK;
 }
+
+// ------------------------------------------------------------------ per-kernel timing
+namespace {
+enum ProfKind { kProfPrologue = 0, kProfPanel = 1, kProfPivotRows = 2, kProfSkr2k = 3,
+                kProfFinish = 4 };
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+    double flops, bytes;
+};
+std::mutex g_prof_mutex;
+std::atomic<bool> g_prof_on{false};
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t take_event() {
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Brackets one launch with events on `st` while profiling is enabled.
+struct ProfScope {
+    bool on;
+    ProfRec r;
+    cudaStream_t st;
+    ProfScope(int kind, cudaStream_t stream, double flops, double bytes)
+        : on(g_prof_on.load()), st(stream) {
+        if (!on) return;
+        r.kind = kind;
+        r.flops = flops;
+        r.bytes = bytes;
+        r.a = take_event();
+        r.b = take_event();
+        if (!r.a || !r.b || cudaEventRecord(r.a, st) != cudaSuccess) {
+            cudaGetLastError();
+            on = false;
+        }
+    }
+    ~ProfScope() {
+        if (!on) return;
+        if (cudaEventRecord(r.b, st) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        std::lock_guard<std::mutex> lock(g_prof_mutex);
+        g_prof.push_back(r);
+    }
+};
+
+double skr2k_flops(int64_t m, int64_t npairs) { return 2.0 * (double)npairs * (double)m * (double)(m - 1); }
+double skr2k_bytes(int64_t m) { return 2.0 * 8.0 * (double)m * (double)(m - 1) / 2.0; }
+}  // namespace
 
 // ------------------------------------------------------------------ per-device state
 namespace {
@@ -167,7 +230,12 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
     do {
         cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
         if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
-        status = launch_prologue(n, A, lda, with_L ? L : nullptr, ldl, piv, ctrl, st);
+        {
+            ProfScope ps(kProfPrologue, st, 0.0,
+                         8.0 * (double)n * (double)(n - 1) / 2.0 +
+                             (with_L ? 8.0 * (double)n * (double)n : 0.0));
+            status = launch_prologue(n, A, lda, with_L ? L : nullptr, ldl, piv, ctrl, st);
+        }
         if (status != SKEW_OK) break;
         const int G = panel_grid_for(di, n);
         for (int64_t k0 = 0; k0 < n - 1 && status == SKEW_OK;) {
@@ -192,9 +260,23 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
             pa.k0 = (int)k0;
             pa.kend = (int)kend;
             pa.with_x = with_x ? 1 : 0;
-            status = launch_panel(pa, G, st);
+            {
+                double pf = 0.0, pb = 0.0;
+                for (int64_t k = k0; k < kend; ++k) {
+                    const double rows = (double)(n - k - 1);
+                    pf += 2.0 * rows * (double)(k - k0);
+                    pb += 8.0 * rows * 6.0;
+                }
+                if (with_x) {
+                    pf += 2.0 * (double)(n - s - 1) * (double)(s - k0);
+                    pb += 8.0 * (double)(n - s - 1) * 2.0;
+                }
+                ProfScope ps(kProfPanel, st, pf, pb);
+                status = launch_panel(pa, G, st);
+            }
             if (status != SKEW_OK) break;
             if (with_L && k0 >= 1) {
+                ProfScope ps(kProfPivotRows, st, 0.0, 4.0 * 8.0 * (double)k0 * (double)(kend - k0));
                 status = launch_pivot_rows(n, L, ldl, piv, (int)k0, (int)kend, st);
                 if (status != SKEW_OK) break;
             }
@@ -212,11 +294,14 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
                 sa.tt = t + k0 + 1;
                 sa.x = A + (s + 1) + s * lda;
                 sa.b = kend - k0;
+                ProfScope ps(kProfSkr2k, st, skr2k_flops(sa.m, sa.b / 2 + (sa.b & 1)),
+                             skr2k_bytes(sa.m));
                 status = launch_skr2k(PairKind::Fused, sa, st);
             }
             k0 = kend;
         }
         if (status != SKEW_OK) break;
+        ProfScope ps(kProfFinish, st, 0.0, 12.0 * (double)n);
         status = launch_finish(n, t, piv, ctrl, logabs, sign, info, st);
     } while (0);
 
@@ -254,6 +339,42 @@ size_t skew_workspace_bytes(int64_t n, int nb, int with_L) {
     if (nb <= 0) nb = skew_default_nb(n);
     if (nb > kMaxNb) nb = kMaxNb;
     return workspace_layout(n, nb, with_L != 0).total;
+}
+
+int skew_profile_enable(int on) {
+    g_prof_on.store(on != 0);
+    return SKEW_OK;
+}
+
+int skew_profile_read(skew_kernel_stat *stats) {
+    if (stats == nullptr) return -1;
+    for (int k = 0; k < SKEW_KIND_COUNT; ++k) stats[k] = skew_kernel_stat{0.0, 0.0, 0.0, 0};
+    std::vector<ProfRec> recs;
+    {
+        std::lock_guard<std::mutex> lock(g_prof_mutex);
+        recs.swap(g_prof);
+    }
+    int status = SKEW_OK;
+    for (const ProfRec &r : recs) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) {
+            set_last_error(e);
+            status = SKEW_ERR_CUDA;
+        } else if (r.kind >= 0 && r.kind < SKEW_KIND_COUNT) {
+            stats[r.kind].ms += ms;
+            stats[r.kind].flops += r.flops;
+            stats[r.kind].bytes += r.bytes;
+            stats[r.kind].launches += 1;
+        }
+    }
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
+    for (const ProfRec &r : recs) {
+        g_event_pool.push_back(r.a);
+        g_event_pool.push_back(r.b);
+    }
+    return status;
 }
 
 int skew_trim_memory(void) {
@@ -350,6 +471,7 @@ int skew_rank2k(int64_t m, int64_t k, double alpha, const double *X, int64_t ldx
     sa.tt = nullptr;
     sa.x = nullptr;
     sa.b = k;
+    ProfScope ps(kProfSkr2k, static_cast<cudaStream_t>(stream), skr2k_flops(m, k), skr2k_bytes(m));
     return launch_skr2k(PairKind::Rank2k, sa, static_cast<cudaStream_t>(stream));
 }
 
@@ -381,6 +503,7 @@ int skew_tridiag_rankk(int64_t m, int64_t b, double alpha, const double *A,
     sa.tt = t;
     sa.x = nullptr;
     sa.b = b;
+    ProfScope ps(kProfSkr2k, static_cast<cudaStream_t>(stream), skr2k_flops(m, b / 2), skr2k_bytes(m));
     return launch_skr2k(PairKind::Tridiag, sa, static_cast<cudaStream_t>(stream));
 }
 
