@@ -54,7 +54,9 @@ typedef enum {
     SKEW_ERR_NOMEM = -101,      /* device workspace could not be allocated */
     SKEW_ERR_CUDA = -102,       /* a CUDA runtime call failed (see skew_last_error) */
     SKEW_ERR_TIMEOUT = -103,    /* a bounded device-side wait gave up */
-    SKEW_ERR_NODEVICE = -104    /* no usable sm_103 device is current */
+    SKEW_ERR_NODEVICE = -104,   /* no usable sm_103 device is current */
+    SKEW_ERR_SCRATCH_LIMIT = -105 /* skew_pfaffian_noalloc: the problem needs more
+                                     than its fixed scratch (see there) */
 } skew_status;
 
 /* Library version as 10000*major + 100*minor + patch. */
@@ -161,6 +163,35 @@ int skew_pfaffian(int64_t n, double *A, int64_t lda, double *logabs, int32_t *si
  */
 int skew_pfaffian_from_factors(int64_t n, const double *t, const int32_t *piv,
                                double *logabs, int32_t *sign, void *stream);
+
+/*
+ * skew_pfaffian_noalloc -- skew_pfaffian for callers that must not have the library
+ * allocate device memory.  The paper has no counterpart: this is a deployment
+ * variant.  It serves programs whose device memory belongs to another allocator (for
+ * example a framework that reserves nearly all of HBM for its own caching pool, so a
+ * library allocation would fail or fragment that pool) and latency-bound loops that
+ * cannot take an allocation on their critical path, when they cannot pass a
+ * workspace to skew_pfaffian either.
+ *
+ * The workspace is a fixed 16 MiB device array inside the library, present on every
+ * device that loads the library until the process exits.  The call itself allocates
+ * nothing (no cudaMalloc, cudaFree, pool or library allocation).  Problems whose
+ * workspace, skew_workspace_bytes(n, nb, 0), exceeds 16 MiB are rejected with
+ * SKEW_ERR_SCRATCH_LIMIT before any device work (at nb = 64 this admits n up to about
+ * 32000; a smaller nb admits larger n).
+ *
+ * The first call on a device looks up the array's device address (with that device
+ * current); make that first call before any stream capture begins.  All calls share
+ * the one array, which keeps the previous call's contents; the call clears, in
+ * stream order, what must start at zero.  Calls whose device work overlaps (on
+ * different streams, or from different threads) race on the array: serialise them.
+ *
+ *   1 n, 2 A (device, DESTROYED), 3 lda, 4 logabs (device), 5 sign (device),
+ *   6 info (device or NULL), 7 nb (0 = default), 8 stream -- as for skew_pfaffian;
+ *   t and piv are kept in the fixed array.
+ */
+int skew_pfaffian_noalloc(int64_t n, double *A, int64_t lda, double *logabs,
+                          int32_t *sign, int32_t *info, int nb, void *stream);
 
 /*
  * skew_rank2k -- C := beta C + alpha (X Y^T - Y X^T) on the strictly lower

@@ -17,6 +17,7 @@ STATUS = {
     -102: "SKEW_ERR_CUDA",
     -103: "SKEW_ERR_TIMEOUT",
     -104: "SKEW_ERR_NODEVICE",
+    -105: "SKEW_ERR_SCRATCH_LIMIT",
 }
 
 _lock = threading.Lock()
@@ -37,6 +38,7 @@ SIGNATURES = {
     "skew_ltlt": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
     "skew_pfaffian": ([_i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
     "skew_pfaffian_from_factors": ([_i64, _vp, _vp, _vp, _vp, _vp], _i32),
+    "skew_pfaffian_noalloc": ([_i64, _vp, _i64, _vp, _vp, _vp, _i32, _vp], _i32),
     "skew_rank2k": ([_i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _vp], _i32),
     "skew_tridiag_rankk": ([_i64, _i64, _dbl, _vp, _i64, _vp, _dbl, _vp, _i64, _vp], _i32),
     "skew_ltlt_host": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32], _i32),
