@@ -84,7 +84,7 @@ def fp64_peak():
 def recorded_traffic():
     """DRAM bytes per algorithmic byte of the skr2k kernel from the committed ncu
     summary, if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "skr2k_fused_n4096.md")
+    path = os.path.join(ROOT, "profiles", "skr2k_fused_n8192.md")
     src = os.path.join(ROOT, "paper_2411_09859_gb300", "csrc", "skr2k.cu")
     try:
         text = open(path).read()
