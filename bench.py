@@ -91,7 +91,7 @@ def recorded_traffic():
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
         return None
-    m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    m_sha = re.search(r"source_sha256[^:\n]*:\s*([0-9a-f]{64})", text)
     m_ratio = re.search(r"dram_bytes_per_algorithmic_byte:\s*([0-9.eE+-]+)", text)
     if not m_sha or not m_ratio or m_sha.group(1) != sha:
         return None

@@ -178,7 +178,7 @@ int skew_pfaffian_from_factors(int64_t n, const double *t, const int32_t *piv,
  * nothing (no cudaMalloc, cudaFree, pool or library allocation).  Problems whose
  * workspace, skew_workspace_bytes(n, nb, 0), exceeds 16 MiB are rejected with
  * SKEW_ERR_SCRATCH_LIMIT before any device work (at nb = 64 this admits n up to about
- * 32000; a smaller nb admits larger n).
+ * 29990; a smaller nb admits larger n).
  *
  * The first call on a device looks up the array's device address (with that device
  * current); make that first call before any stream capture begins.  All calls share

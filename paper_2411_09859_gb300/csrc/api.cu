@@ -110,6 +110,35 @@ bool g_pool_ready[kMaxDevices];
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// A side stream with fork/join events: pivot_rows runs on it, overlapping the next
+// trailing update (it touches only L columns left of the current panel).  Pooled
+// per device; a pooled stream may still hold earlier work, which only orders it.
+struct SideStream {
+    cudaStream_t stream;
+    cudaEvent_t fork, join;
+};
+std::vector<SideStream> g_side_pool[kMaxDevices];
+
+int side_acquire(int dev, SideStream *out) {
+    {
+        std::lock_guard<std::mutex> lock(g_dev_mutex);
+        if (!g_side_pool[dev].empty()) {
+            *out = g_side_pool[dev].back();
+            g_side_pool[dev].pop_back();
+            return SKEW_OK;
+        }
+    }
+    SKEW_TRY(cudaStreamCreateWithFlags(&out->stream, cudaStreamNonBlocking));
+    SKEW_TRY(cudaEventCreateWithFlags(&out->fork, cudaEventDisableTiming));
+    SKEW_TRY(cudaEventCreateWithFlags(&out->join, cudaEventDisableTiming));
+    return SKEW_OK;
+}
+
+void side_release(int dev, const SideStream &s) {
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    g_side_pool[dev].push_back(s);
+}
+
 // Library-private stream-ordered pool: freed blocks stay reserved for reuse (release
 // threshold = max), so repeated calls do not map and unmap device memory.
 int device_pool(int dev, cudaMemPool_t *out) {
@@ -184,7 +213,7 @@ WsLayout workspace_layout(int64_t n, int nb, bool with_L) {
     w.ctrl = off;
     off += align256(sizeof(Ctrl));
     w.partials = off;
-    off += align256(sizeof(ArgmaxPartial) * kMaxPanelGrid);
+    off += align256(sizeof(ArgmaxPartial) * 2 * kMaxPanelGrid);
     w.tbuf = off;
     off += align256(sizeof(double) * (size_t)(n > 1 ? n : 1));
     w.pivbuf = off;
@@ -197,13 +226,6 @@ WsLayout workspace_layout(int64_t n, int nb, bool with_L) {
 
 // ------------------------------------------------------------------ the factorization
 namespace {
-
-int panel_grid_for(const DeviceInfo &di, int64_t n) {
-    int64_t g = (n + 127) / 128;
-    if (g < 1) g = 1;
-    if (g > di.panel_grid_max) g = di.panel_grid_max;
-    return (int)g;
-}
 
 int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
            int32_t *piv, int32_t *info, double *logabs, int32_t *sign, int nb,
@@ -227,8 +249,23 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
     if (piv == nullptr) piv = reinterpret_cast<int32_t *>(base + lay.pivbuf);
     double *Lbuf = with_L ? nullptr : reinterpret_cast<double *>(base + lay.lbuf);
 
+    SideStream side{};
+    bool have_side = false;
+    if (with_L && n > nb + 1) {
+        status = side_acquire(di.device, &side);
+        if (status != SKEW_OK) {
+            if (own) cudaFreeAsync(base, st);
+            return status;
+        }
+        have_side = true;
+    }
+    bool side_used = false;
+
     do {
+        // control block and the step tags of the argmax partials start at zero
         cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(part, 0, sizeof(ArgmaxPartial) * 2 * kMaxPanelGrid, st);
         if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
         {
             ProfScope ps(kProfPrologue, st, 0.0,
@@ -237,7 +274,6 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
             status = launch_prologue(n, A, lda, with_L ? L : nullptr, ldl, piv, ctrl, st);
         }
         if (status != SKEW_OK) break;
-        const int G = panel_grid_for(di, n);
         for (int64_t k0 = 0; k0 < n - 1 && status == SKEW_OK;) {
             const int64_t kend = (k0 + nb < n - 1) ? k0 + nb : n - 1;
             const int64_t s = kend;
@@ -272,12 +308,22 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
                     pb += 8.0 * (double)(n - s - 1) * 2.0;
                 }
                 ProfScope ps(kProfPanel, st, pf, pb);
-                status = launch_panel(pa, G, st);
+                status = launch_panel(pa, di.panel_grid_max, st);
             }
             if (status != SKEW_OK) break;
             if (with_L && k0 >= 1) {
-                ProfScope ps(kProfPivotRows, st, 0.0, 4.0 * 8.0 * (double)k0 * (double)(kend - k0));
-                status = launch_pivot_rows(n, L, ldl, piv, (int)k0, (int)kend, st);
+                // fork: pivot_rows after this panel, beside the next trailing update
+                cudaStream_t ps_stream = st;
+                if (have_side) {
+                    e = cudaEventRecord(side.fork, st);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(side.stream, side.fork, 0);
+                    if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+                    ps_stream = side.stream;
+                    side_used = true;
+                }
+                ProfScope ps(kProfPivotRows, ps_stream, 0.0,
+                             4.0 * 8.0 * (double)k0 * (double)(kend - k0));
+                status = launch_pivot_rows(n, L, ldl, piv, (int)k0, (int)kend, ps_stream);
                 if (status != SKEW_OK) break;
             }
             if (with_x) {
@@ -304,6 +350,17 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
         ProfScope ps(kProfFinish, st, 0.0, 12.0 * (double)n);
         status = launch_finish(n, t, piv, ctrl, logabs, sign, info, st);
     } while (0);
+
+    if (side_used) {
+        // join: the caller's stream waits for the last pivot_rows
+        cudaError_t e = cudaEventRecord(side.join, side.stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, side.join, 0);
+        if (e != cudaSuccess && status == SKEW_OK) {
+            set_last_error(e);
+            status = SKEW_ERR_CUDA;
+        }
+    }
+    if (have_side) side_release(di.device, side);
 
     if (own) {
         cudaError_t e = cudaFreeAsync(base, st);

@@ -39,24 +39,28 @@ int current_device_info(DeviceInfo *out);
 // ------------------------------------------------------------------ device control block
 // Lives at the start of every workspace.  Zeroed (cudaMemsetAsync) at the start of
 // each factorization.
+constexpr int kPanelThreads = 256;
+constexpr int kMaxPanelGrid = 256;      // >= SMs of the part (152 on GB300)
+constexpr int kMaxNb = 256;
+
 struct Ctrl {
     unsigned int bar_count;   // grid barrier: CTAs arrived in the current round
     unsigned int bar_gen;     // grid barrier: completed rounds
     int err;                  // first device-detected error status (0 = none)
     int pad0;
-    double vtop;              // panel: v[k+1] of the current step, before the exchange
-    double pad1[5];
+    double vtop[2];           // panel: v[k+1] of step k (slot k & 1), before the exchange
+    double pad1[4];
+    double rowp[2][kMaxNb];   // panel: L[k+1, k0+1..k] of step k (slot k & 1)
 };
 
-struct ArgmaxPartial {       // one per panel CTA
+// One per panel CTA and step parity: the CTA's best candidate row of the step and
+// that row's L values in the panel columns formed so far.
+struct ArgmaxPartial {
     double val;               // signed v at the CTA's best row
     int idx;                  // that row (INT32_MAX if none)
-    int pad;
+    unsigned int tag;         // shared-memory panel: step tag released after the rest
+    double row[kMaxNb];       // L[idx, k0+1 .. k]
 };
-
-constexpr int kPanelThreads = 256;
-constexpr int kMaxPanelGrid = 1024;
-constexpr int kMaxNb = 256;
 constexpr int64_t kMaxOrder = int64_t(1) << 22;   // keeps every tile count below 2^31
 
 // Workspace layout (byte offsets), see workspace_layout().
@@ -76,6 +80,16 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
     unsigned int v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
 __device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v) {
@@ -157,7 +171,9 @@ struct PanelArgs {
     ArgmaxPartial *part;
     int n, k0, kend, with_x;
 };
-int launch_panel(const PanelArgs &a, int grid, cudaStream_t stream);
+// Picks the shared-memory panel kernel when every panel row gets its own thread on
+// `sms` CTAs and the panel is at most 96 columns wide, else the global-memory one.
+int launch_panel(const PanelArgs &a, int sms, cudaStream_t stream);
 int panel_max_blocks_per_sm(int *out);
 
 // Row exchanges piv[k+1] <-> k+1, k = k0 .. kend-1 in order, on L columns 1 .. k0.

@@ -15,12 +15,16 @@
 // L columns, then sets t[k] = v[k+1] and L[k+2:, k+1] = v[k+2:] / t[k].
 // Columns of L left of the panel are exchanged later (pivot_rows).
 //
-// GPU organisation: one CTA per SM (cooperative launch), rows of each column step
-// spread over all threads (consecutive threads -> consecutive rows, so column reads
-// of X and L are coalesced).  Each step has two grid barriers: after the gemv and the
-// per-CTA argmax, and after the exchange and the scaling.  The unscaled v lives in L's
-// column k+1 between the two phases; data written by other CTAs inside this launch
-// is read with ld.global.cg (L2, never a stale L1 line).
+// GPU organisation: one CTA per SM (cooperative launch).  Row i is owned by thread
+// i mod (#threads) for the whole panel, so everything a step does to row i -- its
+// exchange, its scaled L entry, and the next step's v_i -- is done by one thread
+// without synchronisation.  What crosses rows is published before the one grid
+// barrier of each step: every CTA writes its best candidate (|v|, index) together
+// with that row's L values in the panel columns, and the owner of row k+1 writes
+// v[k+1] and its L row.  After the barrier every CTA knows the pivot r, t[k], the
+// new row k+1 of L (old row r) and so the next h, and goes straight on.  The
+// published data are double-buffered by step parity: a CTA can be at most one step
+// ahead of another.  Data written inside this launch are read with ld.global.cg.
 #include <cfloat>
 #include <climits>
 
@@ -29,53 +33,88 @@
 namespace skew {
 namespace {
 
-__device__ __forceinline__ bool better(double va, int ia, double vb, int ib) {
-    // (|va|, ia) beats (|vb|, ib): larger magnitude, then lower index.  A NaN
-    // magnitude never wins (its comparisons are false).
-    double a = fabs(va), b = fabs(vb);
-    return (a > b) || (a == b && ia < ib);
+// Pivot candidates are compared on the bits of |v| as unsigned integers (for
+// non-negative IEEE doubles the order of the bit patterns is the order of the
+// values), then on the row index: larger magnitude wins, the lower index wins a tie.
+// FP64 instructions are avoided because they are slow on this part.  A NaN is never
+// a candidate.  (0, INT_MAX) is the "no candidate" value: any real entry beats it,
+// since |v| > 0 is larger and |v| == 0 wins on the index.
+constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
+constexpr unsigned long long kExpMask = 0x7ff0000000000000ull;
+
+__device__ __forceinline__ bool finite_bits(unsigned long long raw) {
+    return (raw & kExpMask) != kExpMask;
 }
 
 struct Best {
-    double v;
-    int i;
+    unsigned long long raw;   // bits of the signed v
+    int i;                    // row
+    int c;                    // CTA that published it
 };
+
+__device__ __forceinline__ bool better(unsigned long long ra, int ia, unsigned long long rb,
+                                       int ib) {
+    const unsigned long long a = ra & kAbsMask, b = rb & kAbsMask;
+    return (a > b) || (a == b && ia < ib);
+}
+
+__device__ __forceinline__ Best no_candidate() {
+    Best b;
+    b.raw = 0ull;
+    b.i = INT_MAX;
+    b.c = 0;
+    return b;
+}
+
+// Offer row i with value v; NaN is skipped.
+__device__ __forceinline__ void offer(Best &b, double v, int i) {
+    const unsigned long long raw = (unsigned long long)__double_as_longlong(v);
+    if ((raw & kAbsMask) > kExpMask) return;          // NaN
+    if (better(raw, i, b.raw, b.i)) { b.raw = raw; b.i = i; }
+}
 
 __device__ __forceinline__ Best warp_best(Best x) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        double ov = __shfl_down_sync(0xffffffffu, x.v, off);
-        int oi = __shfl_down_sync(0xffffffffu, x.i, off);
-        if (better(ov, oi, x.v, x.i)) { x.v = ov; x.i = oi; }
+        const unsigned long long orw = __shfl_down_sync(0xffffffffu, x.raw, off);
+        const int oi = __shfl_down_sync(0xffffffffu, x.i, off);
+        const int oc = __shfl_down_sync(0xffffffffu, x.c, off);
+        if (better(orw, oi, x.raw, x.i)) { x.raw = orw; x.i = oi; x.c = oc; }
     }
     return x;
 }
 
-// Reduce one Best per thread to thread 0 of the CTA.
+// Reduce one Best per thread; the result is valid in every thread on return.
 __device__ Best block_best(Best x) {
-    __shared__ double s_v[kPanelThreads / 32];
+    __shared__ unsigned long long s_raw[kPanelThreads / 32];
     __shared__ int s_i[kPanelThreads / 32];
+    __shared__ Best s_res;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     x = warp_best(x);
-    if (lane == 0) { s_v[w] = x.v; s_i[w] = x.i; }
+    if (lane == 0) { s_raw[w] = x.raw; s_i[w] = x.i; }
     __syncthreads();
     if (w == 0) {
-        Best y;
-        // (0, INT_MAX) is the "no candidate" value: any real entry beats it, because a
-        // finite |v| > 0 is larger and |v| == 0 wins on the index
-        y.v = (lane < kPanelThreads / 32) ? s_v[lane] : 0.0;
-        y.i = (lane < kPanelThreads / 32) ? s_i[lane] : INT_MAX;
-        x = warp_best(y);
+        Best y = no_candidate();
+        if (lane < kPanelThreads / 32) { y.raw = s_raw[lane]; y.i = s_i[lane]; }
+        y = warp_best(y);
+        if (lane == 0) s_res = y;
     }
     __syncthreads();
-    return x;
+    return s_res;
+}
+
+__device__ __forceinline__ double as_double(unsigned long long raw) {
+    return __longlong_as_double((long long)raw);
 }
 
 __global__ void __launch_bounds__(kPanelThreads)
-panel_kernel(PanelArgs a) {
-    __shared__ double s_h[kMaxNb + 1];
+panel_global_kernel(PanelArgs a) {
+    __shared__ double s_h[kMaxNb + 1];   // h of the next step, index q - k0 - 1
+    __shared__ double s_t[kMaxNb + 1];   // t[k] of this panel, index k - k0
+    __shared__ double s_w[kMaxNb + 1];   // new L row k+1 (old row r), index c - k0 - 1
+    __shared__ double s_rp[kMaxNb + 1];  // new L row r (old row k+1), index c - k0 - 1
     __shared__ double s_tau, s_vtop;
-    __shared__ int s_r;
+    __shared__ int s_r, s_win;
 
     Ctrl *ctrl = a.ctrl;
     const int n = a.n, k0 = a.k0, kend = a.kend;
@@ -86,138 +125,492 @@ panel_kernel(PanelArgs a) {
     if (threadIdx.x == 0) gen = ld_acquire_u32(&ctrl->bar_gen);
     if (ld_volatile_i32(&ctrl->err) != 0) return;
 
-    // L(i, q) for panel columns q in [k0+1, kend]
-    auto Lcol = [&](int q) -> double * { return a.Lp + (int64_t)(q - k0 - 1) * a.ldl; };
     double *X = a.X;
-    const int64_t ldx = a.ldx;
-
-    // h = T L[k, :]^T restricted to the panel, into s_h[q - k0 - 1]
-    auto form_h = [&](int k) {
-        for (int q = k0 + 1 + threadIdx.x; q <= k; q += blockDim.x) {
-            double hq = 0.0;
-            if (q - 1 >= k0 + 1) hq = __ldcg(a.t + (q - 1)) * __ldcg(Lcol(q - 1) + k);
-            if (q + 1 <= k) hq -= __ldcg(a.t + q) * __ldcg(Lcol(q + 1) + k);
-            s_h[q - k0 - 1] = hq;
-        }
-        __syncthreads();
+    const int64_t ldx = a.ldx, ldl = a.ldl;
+    // panel column q (k0+1 <= q <= kend) of L
+    auto Lcol = [&](int q) -> double * { return a.Lp + (int64_t)(q - k0 - 1) * ldl; };
+    // first row >= lo owned by this thread (rows i with i mod nthreads == gtid)
+    auto first_row = [&](int64_t lo) -> int64_t {
+        int64_t rem = (gtid - lo) % nthreads;
+        if (rem < 0) rem += nthreads;
+        return lo + rem;
     };
-
-    for (int k = k0; k < kend; ++k) {
-        // ---------------- phase A: v = X[k+1:, k] - L[k+1:, k0+1..k] h; local argmax
-        form_h(k);
-        const int nq = k - k0;                   // panel columns already formed
-        double *vcol = Lcol(k + 1);              // v is parked in L's column k+1
-        const double *xk = X + (int64_t)k * ldx;
-        Best best;
-        best.v = 0.0;
-        best.i = INT_MAX;
-        bool nonfinite = false;
-        for (int64_t i = k + 1 + gtid; i < n; i += nthreads) {
-            double v = __ldcg(xk + i);
-            for (int q = 0; q < nq; ++q) v -= __ldcg(a.Lp + (int64_t)q * a.ldl + i) * s_h[q];
-            vcol[i] = v;
-            if (i == k + 1) ctrl->vtop = v;
-            if (!isfinite(v)) nonfinite = true;
-            if (better(v, (int)i, best.v, best.i)) { best.v = v; best.i = (int)i; }
-        }
+    auto slot = [&](int k, unsigned int cta) -> ArgmaxPartial * {
+        return a.part + (k & 1) * kMaxPanelGrid + cta;
+    };
+    // Publish this CTA's best candidate of step k and its L row (columns k0+1..k);
+    // the CTA owning row k+1 also publishes that row.  The rows are copied by all
+    // threads of the CTA in parallel.
+    auto publish = [&](int k, Best best, bool nonfinite) {
         if (nonfinite) raise_error(ctrl, SKEW_ERR_NONFINITE);
         best = block_best(best);
+        ArgmaxPartial *sp = slot(k, blockIdx.x);
         if (threadIdx.x == 0) {
-            a.part[blockIdx.x].val = best.v;
-            a.part[blockIdx.x].idx = best.i;
+            sp->val = as_double(best.raw);
+            sp->idx = best.i;
         }
+        if (best.i != INT_MAX)
+            for (int q = threadIdx.x; q < k - k0; q += blockDim.x)
+                sp->row[q] = __ldcg(Lcol(k0 + 1 + q) + best.i);
+        const int64_t pn = k + 1;
+        if (pn < n && (pn % nthreads) / blockDim.x == blockIdx.x)
+            for (int q = threadIdx.x; q < k - k0; q += blockDim.x)
+                ctrl->rowp[k & 1][q] = __ldcg(Lcol(k0 + 1 + q) + pn);
+    };
+
+    // ---------------- step k0: v = X[k0+1:, k0] (no panel column formed yet)
+    {
+        const int k = k0;
+        double *vcol = Lcol(k + 1);
+        const double *xk = X + (int64_t)k * ldx;
+        Best best = no_candidate();
+        bool nonfinite = false;
+        for (int64_t i = first_row(k + 1); i < n; i += nthreads) {
+            const double v = __ldcg(xk + i);
+            vcol[i] = v;
+            if (i == k + 1) ctrl->vtop[k & 1] = v;
+            if (!isfinite(v)) nonfinite = true;
+            offer(best, v, (int)i);
+        }
+        best.c = blockIdx.x;
+        publish(k, best, nonfinite);
+    }
+
+    for (int k = k0; k < kend; ++k) {
         if (!grid_barrier(ctrl, G, gen)) return;
 
-        // ---------------- phase B: global argmax, exchange k+1 <-> r, scale
+        // ---------------- pivot of step k: global argmax over the published partials
         if (threadIdx.x < 32) {
-            Best b;
-            b.v = 0.0;
-            b.i = INT_MAX;
+            Best b = no_candidate();
             for (unsigned int c = threadIdx.x; c < G; c += 32) {
-                double pv = __ldcg(&a.part[c].val);
-                int pi = __ldcg(&a.part[c].idx);
-                if (better(pv, pi, b.v, b.i)) { b.v = pv; b.i = pi; }
+                const ArgmaxPartial *sp = slot(k, c);
+                const unsigned long long pr = (unsigned long long)__double_as_longlong(__ldcg(&sp->val));
+                const int pi = __ldcg(&sp->idx);
+                if (better(pr, pi, b.raw, b.i)) { b.raw = pr; b.i = pi; b.c = (int)c; }
             }
             b = warp_best(b);
             if (threadIdx.x == 0) {
-                int r = (b.i == INT_MAX) ? k + 1 : b.i;   // all NaN: keep the diagonal
-                s_r = r;
-                s_vtop = __ldcg(&ctrl->vtop);
-                s_tau = (b.i == INT_MAX) ? s_vtop : b.v;
+                const double vt = __ldcg(&ctrl->vtop[k & 1]);
+                s_vtop = vt;
+                s_r = (b.i == INT_MAX) ? k + 1 : b.i;    // all NaN: keep the diagonal
+                s_tau = (b.i == INT_MAX) ? vt : as_double(b.raw);
+                s_win = (b.i == INT_MAX) ? -1 : b.c;
             }
         }
         __syncthreads();
-        const int r = s_r, p = k + 1;
+        const int r = s_r, p = k + 1, nq = k - k0;
         const double tau = s_tau, vtop = s_vtop;
+        // exchanged rows of L in the formed panel columns: new row p = old row r (the
+        // winner's published row), new row r = old row p (published by its owner)
+        if (s_win >= 0)
+            for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+                s_w[q] = __ldcg(&slot(k, s_win)->row[q]);
+                s_rp[q] = __ldcg(&ctrl->rowp[k & 1][q]);
+            }
+        if (threadIdx.x == 0) s_t[k - k0] = tau;
         if (gtid == 0) {
             a.t[k] = tau;
             a.piv[p] = r;
         }
-        for (int64_t i = p + gtid; i < n; i += nthreads) {
-            // L column k+1: 1 on the diagonal, v / tau below it (v[p] and v[r] exchanged)
+        __syncthreads();
+
+        const bool next = (k + 1 < kend);          // another step of this panel follows
+        const bool form_x = (!next && a.with_x);   // last step: form column kend instead
+        const int nqn = nq + 1;                     // panel columns k0+1 .. k+1
+        if (next || form_x) {
+            // h for step k+1 from the new row k+1 of L: L[k+1, c] = s_w[c-k0-1] for
+            // c <= k and L[k+1, k+1] = 1
+            for (int q = k0 + 1 + threadIdx.x; q <= k + 1; q += blockDim.x) {
+                double hq = 0.0;
+                if (q - 1 >= k0 + 1) hq = s_t[q - 1 - k0] * s_w[q - 2 - k0];
+                if (q + 1 <= k + 1) {
+                    const double lq1 = (q + 1 == k + 1) ? 1.0 : s_w[q - k0];
+                    hq -= s_t[q - k0] * lq1;
+                }
+                s_h[q - k0 - 1] = hq;
+            }
+        }
+        __syncthreads();
+
+        double *vcol = Lcol(k + 1);                 // v of step k, parked in L column k+1
+        double *vnext = next ? Lcol(k + 2) : nullptr;
+        double *colp = X + (int64_t)p * ldx;
+        Best best = no_candidate();
+        bool nonfinite = false;
+        for (int64_t i = first_row(p); i < n; i += nthreads) {
+            // ---- finish step k for row i
             if (i == p) {
                 vcol[i] = 1.0;
+                if (r != p)
+                    for (int q = 0; q < nq; ++q) Lcol(k0 + 1 + q)[i] = s_w[q];
             } else {
-                double v = (i == r) ? vtop : vcol[i];
+                const double v = (i == r) ? vtop : __ldcg(vcol + i);
                 vcol[i] = (tau != 0.0) ? v / tau : 0.0;
+                if (i == r)
+                    for (int q = 0; q < nq; ++q) Lcol(k0 + 1 + q)[i] = s_rp[q];
             }
             if (r != p && i > p) {
                 // symmetric exchange of indices p and r in the strictly lower storage
-                double *colp = X + (int64_t)p * ldx;
                 if (i < r) {
-                    double *xri = X + (int64_t)i * ldx + r;    // X[r, i]
-                    double tmp = __ldcg(colp + i);
+                    double *xri = X + i * ldx + r;          // X[r, i]
+                    const double tmp = __ldcg(colp + i);
                     colp[i] = -__ldcg(xri);
                     *xri = -tmp;
                 } else if (i == r) {
                     colp[i] = -__ldcg(colp + i);
                 } else {
                     double *colr = X + (int64_t)r * ldx;
-                    double tmp = __ldcg(colp + i);
+                    const double tmp = __ldcg(colp + i);
                     colp[i] = __ldcg(colr + i);
                     colr[i] = tmp;
                 }
             }
-        }
-        // rows p and r of the panel's L columns k0+1 .. k
-        if (r != p && blockIdx.x == 0) {
-            for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-                double *col = a.Lp + (int64_t)q * a.ldl;
-                double tmp = __ldcg(col + p);
-                col[p] = __ldcg(col + r);
-                col[r] = tmp;
+            // ---- step k+1 for row i (or the updated column kend at the last step)
+            if ((next || form_x) && i > p) {
+                double acc0 = 0.0, acc1 = 0.0;
+                int q = 0;
+#pragma unroll 4
+                for (; q + 1 < nqn; q += 2) {
+                    acc0 += __ldcg(a.Lp + (int64_t)q * ldl + i) * s_h[q];
+                    acc1 += __ldcg(a.Lp + (int64_t)(q + 1) * ldl + i) * s_h[q + 1];
+                }
+                if (q < nqn) acc0 += __ldcg(a.Lp + (int64_t)q * ldl + i) * s_h[q];
+                const double v = __ldcg(colp + i) - (acc0 + acc1);
+                if (!isfinite(v)) nonfinite = true;
+                if (form_x) {
+                    colp[i] = v;
+                } else {
+                    vnext[i] = v;
+                    if (i == p + 1) ctrl->vtop[(k + 1) & 1] = v;
+                    offer(best, v, (int)i);
+                }
             }
         }
-        const bool last = (k + 1 == kend);
-        if (!last || a.with_x) {
-            if (!grid_barrier(ctrl, G, gen)) return;
+        if (next) {
+            best.c = blockIdx.x;
+            publish(k + 1, best, nonfinite);
+        } else if (nonfinite) {
+            raise_error(ctrl, SKEW_ERR_NONFINITE);
         }
+    }
+}
+
+
+// ------------------------------------------------------------------------------------
+// Shared-memory panel: used when every row of the panel has its own thread
+// (n - k0 - 1 <= #CTAs x 256) and the panel is at most kSmemMaxNb wide.  Each thread
+// keeps its row of the panel's L columns in shared memory, so the per-step
+// skew_tridiag_gemv reads no global memory, and the v of its row in a register.
+// There is no separate grid barrier: each CTA publishes its step-k partial with a
+// release store of a step tag, and every CTA's warp 0 acquires all G tags -- the
+// gather of the argmax candidates is the barrier.  Rows are dealt to CTAs in chunks
+// of 32 (one warp) round-robin, so the rows of a step are spread over all SMs and
+// each warp's accesses to a column are coalesced.
+// ------------------------------------------------------------------------------------
+constexpr int kSmemMaxNb = 96;
+
+__device__ __forceinline__ void st_release_u32_gpu(unsigned int *p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(kPanelThreads)
+panel_smem_kernel(PanelArgs a) {
+    extern __shared__ double s_L[];          // [q][threadIdx.x], q < kend - k0
+    __shared__ double s_h[kSmemMaxNb + 1];   // h of the next step, index q - k0 - 1
+    __shared__ double s_t[kSmemMaxNb + 1];   // t[k] of this panel, index k - k0
+    __shared__ double s_w[kSmemMaxNb + 1];   // new L row k+1 (old row r), index c - k0 - 1
+    __shared__ double s_rp[kSmemMaxNb + 1];  // new L row r (old row k+1)
+    __shared__ double s_tau, s_vtop;
+    __shared__ int s_r, s_win, s_fail;
+    __shared__ unsigned int s_base;
+
+    Ctrl *ctrl = a.ctrl;
+    const int n = a.n, k0 = a.k0, kend = a.kend;
+    const int G = (int)gridDim.x;
+    const int tid = threadIdx.x;
+    double *X = a.X;
+    const int64_t ldx = a.ldx, ldl = a.ldl;
+    auto Lcol = [&](int q) -> double * { return a.Lp + (int64_t)(q - k0 - 1) * ldl; };
+    auto slot = [&](int k, int cta) -> ArgmaxPartial * {
+        return a.part + (k & 1) * kMaxPanelGrid + cta;
+    };
+    auto sL = [&](int q) -> double & { return s_L[q * kPanelThreads + tid]; };
+
+    // this thread's row: chunk (tid / 32) * G + cta, lane tid % 32
+    const int64_t i = (int64_t)k0 + 1 + ((int64_t)((tid >> 5) * G + (int)blockIdx.x) << 5) + (tid & 31);
+    const bool own = i < n;
+
+    if (tid == 0) {
+        s_base = ld_acquire_u32(&ctrl->bar_gen);
+        s_fail = ld_volatile_i32(&ctrl->err) != 0;
+    }
+    __syncthreads();
+    if (s_fail) return;
+    const unsigned int base = s_base;
+
+    // CTA and thread that own row `row` (k0 < row < n; 32-bit index arithmetic)
+    auto owner_cta = [&](int row) -> int { return ((row - k0 - 1) >> 5) % G; };
+    auto owner_tid = [&](int row) -> int {
+        const int j = row - k0 - 1;
+        return (((j >> 5) / G) << 5) + (j & 31);
+    };
+
+    // Publish this CTA's step-k candidate (and its L row), the row k+1 of L and
+    // v[k+1] if this CTA owns row k+1, then release the step tag.  Rows are copied
+    // from shared memory by all threads of the CTA.
+    auto publish = [&](int k, Best best, bool nonfinite) {
+        if (nonfinite) raise_error(ctrl, SKEW_ERR_NONFINITE);
+        best = block_best(best);
+        ArgmaxPartial *sp = slot(k, blockIdx.x);
+        const int nq = k - k0;
+        if (best.i != INT_MAX) {
+            const int ot = owner_tid(best.i);
+            for (int q = tid; q < nq; q += blockDim.x)
+                sp->row[q] = s_L[q * kPanelThreads + ot];
+        }
+        if (k + 1 < n && owner_cta(k + 1) == (int)blockIdx.x) {
+            const int ot = owner_tid(k + 1);
+            for (int q = tid; q < nq; q += blockDim.x)
+                ctrl->rowp[k & 1][q] = s_L[q * kPanelThreads + ot];
+        }
+        if (tid == 0) {
+            sp->val = as_double(best.raw);
+            sp->idx = best.i;
+        }
+        __syncthreads();
+        // release: the CTA's writes above (ordered before by the barrier) become
+        // visible to any CTA that acquires the tag
+        if (tid == 0) st_release_u32_gpu(&sp->tag, base + (unsigned int)(k - k0) + 1u);
+    };
+
+    // ---------------- step k0: v = X[k0+1:, k0]
+    double v = 0.0;
+    {
+        const int k = k0;
+        Best best = no_candidate();
+        bool nonfinite = false;
+        if (own) {
+            v = __ldcg(X + (int64_t)k * ldx + i);
+            if (i == k + 1) ctrl->vtop[k & 1] = v;
+            if (!finite_bits((unsigned long long)__double_as_longlong(v))) nonfinite = true;
+            offer(best, v, (int)i);
+        }
+        best.c = blockIdx.x;
+        publish(k, best, nonfinite);
     }
 
-    // ---------------- the updated column s = kend (for the fused trailing update)
-    if (a.with_x) {
-        const int s = kend;
-        form_h(s);
-        const int nq = s - k0;
-        double *xs = X + (int64_t)s * ldx;
-        bool nonfinite = false;
-        for (int64_t i = s + 1 + gtid; i < n; i += nthreads) {
-            double v = __ldcg(xs + i);
-            for (int q = 0; q < nq; ++q) v -= __ldcg(a.Lp + (int64_t)q * a.ldl + i) * s_h[q];
-            xs[i] = v;
-            if (!isfinite(v)) nonfinite = true;
+    for (int k = k0; k < kend; ++k) {
+        // ---------------- gather the step-k candidates of all CTAs (the barrier).
+        // Lane l of warp 0 watches slots l, l+32, ...: all its tags are polled in one
+        // pass of independent acquire loads, then all values are loaded at once.
+        if (tid < 32) {
+            constexpr int kPer = kMaxPanelGrid / 32;
+            const unsigned int want = base + (unsigned int)(k - k0) + 1u;
+            unsigned int pending = 0;
+#pragma unroll
+            for (int j = 0; j < kPer; ++j)
+                if (tid + 32 * j < G) pending |= 1u << j;
+            int fail = 0;
+            uint64_t t0 = 0;
+            unsigned int polls = 0;
+            // relaxed loads, all in flight at once (acquire loads would serialise);
+            // the fence after the loop turns the observed tags into an acquire
+            while (pending != 0u) {
+#pragma unroll
+                for (int j = 0; j < kPer; ++j)
+                    if ((pending >> j) & 1u)
+                        if (ld_relaxed_u32(&slot(k, tid + 32 * j)->tag) == want)
+                            pending &= ~(1u << j);
+                if (pending == 0u) break;
+                // the error word and the clock are looked at every 16th pass only, so
+                // that a pass is one round of loads
+                if ((++polls & 15u) == 0u) {
+                    if (ld_volatile_i32(&ctrl->err) != 0) { fail = 1; break; }
+                    const uint64_t now = global_ns();
+                    if (t0 == 0) t0 = now;
+                    else if (now - t0 > kBarrierTimeoutNs) {
+                        raise_error(ctrl, SKEW_ERR_TIMEOUT);
+                        fail = 1;
+                        break;
+                    }
+                }
+            }
+            fence_acq_rel_gpu();
+            Best b = no_candidate();
+            if (!fail) {
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) {
+                    const int c = tid + 32 * j;
+                    if (c < G) {
+                        const ArgmaxPartial *sp = slot(k, c);
+                        const unsigned long long pr =
+                            (unsigned long long)__double_as_longlong(__ldcg(&sp->val));
+                        const int pi = __ldcg(&sp->idx);
+                        if (better(pr, pi, b.raw, b.i)) { b.raw = pr; b.i = pi; b.c = c; }
+                    }
+                }
+            }
+            fail = __any_sync(0xffffffffu, fail);
+            b = warp_best(b);
+            if (tid == 0) {
+                s_fail = fail;
+                s_r = (b.i == INT_MAX) ? k + 1 : b.i;    // all NaN: keep the diagonal
+                s_tau = as_double(b.raw);
+                s_win = (b.i == INT_MAX) ? -1 : b.c;
+            }
         }
-        if (nonfinite) raise_error(ctrl, SKEW_ERR_NONFINITE);
+        __syncthreads();
+        if (s_fail) return;
+        const int r = s_r, p = k + 1, nq = k - k0;
+
+        // ---------------- one round of loads: exchanged L rows, v[k+1], own X entries
+        if (s_win >= 0)
+            for (int q = tid; q < nq; q += blockDim.x) {
+                s_w[q] = __ldcg(&slot(k, s_win)->row[q]);
+                s_rp[q] = __ldcg(&ctrl->rowp[k & 1][q]);
+            }
+        if (tid == 0) {
+            const double vt = __ldcg(&ctrl->vtop[k & 1]);
+            s_vtop = vt;
+            if (s_win < 0) s_tau = vt;
+        }
+        double *colp = X + (int64_t)p * ldx;
+        double x_old = 0.0, xe = 0.0;
+        if (own && i > p) {
+            x_old = __ldcg(colp + i);
+            if (r != p) {
+                if (i < r) xe = __ldcg(X + i * ldx + r);                 // X[r, i]
+                else if (i > r) xe = __ldcg(X + (int64_t)r * ldx + i);   // X[i, r]
+            }
+        }
+        __syncthreads();
+        const double tau = s_tau, vtop = s_vtop;
+        if (tid == 0) s_t[k - k0] = tau;
+        if (blockIdx.x == 0 && tid == 0) {
+            a.t[k] = tau;
+            a.piv[p] = r;
+        }
+        __syncthreads();
+
+        // exchanged rows of the panel's L columns k0+1..k: new row p = old row r (s_w)
+        // in the CTA owning p, new row r = old row p (s_rp) in the CTA owning r
+        if (r != p && s_win >= 0) {
+            if (owner_cta(p) == (int)blockIdx.x) {
+                const int ot = owner_tid(p);
+                for (int q = tid; q < nq; q += blockDim.x) {
+                    s_L[q * kPanelThreads + ot] = s_w[q];
+                    Lcol(k0 + 1 + q)[p] = s_w[q];
+                }
+            }
+            if (owner_cta(r) == (int)blockIdx.x) {
+                const int ot = owner_tid(r);
+                for (int q = tid; q < nq; q += blockDim.x) {
+                    s_L[q * kPanelThreads + ot] = s_rp[q];
+                    Lcol(k0 + 1 + q)[r] = s_rp[q];
+                }
+            }
+        }
+        const bool next = (k + 1 < kend);
+        const bool form_x = (!next && a.with_x);
+        if (next || form_x) {
+            for (int q = k0 + 1 + tid; q <= k + 1; q += blockDim.x) {
+                double hq = 0.0;
+                if (q - 1 >= k0 + 1) hq = s_t[q - 1 - k0] * s_w[q - 2 - k0];
+                if (q + 1 <= k + 1) {
+                    const double lq1 = (q + 1 == k + 1) ? 1.0 : s_w[q - k0];
+                    hq -= s_t[q - k0] * lq1;
+                }
+                s_h[q - k0 - 1] = hq;
+            }
+        }
+        __syncthreads();
+
+        Best best = no_candidate();
+        bool nonfinite = false;
+        if (own && i >= p) {
+            // ---- finish step k for this row: L column k+1 and the exchanged rows
+            double *lk1 = Lcol(k + 1) + i;
+            if (i == p) {
+                sL(nq) = 1.0;
+                *lk1 = 1.0;
+            } else {
+                const double val = (i == r) ? vtop : v;
+                const double l = (tau != 0.0) ? val / tau : 0.0;
+                sL(nq) = l;
+                *lk1 = l;
+            }
+            if (i > p) {
+                // ---- symmetric exchange of p and r in the strictly lower storage
+                double xn = x_old;                        // new X[i, p]
+                if (r != p) {
+                    if (i < r) {
+                        xn = -xe;
+                        X[i * ldx + r] = -x_old;          // X[r, i]
+                    } else if (i == r) {
+                        xn = -x_old;
+                    } else {
+                        xn = xe;
+                        X[(int64_t)r * ldx + i] = x_old;  // X[i, r]
+                    }
+                    colp[i] = xn;
+                }
+                // ---- step k+1 for this row (or the updated column kend)
+                if (next || form_x) {
+                    double acc0 = 0.0, acc1 = 0.0;
+                    int q = 0;
+#pragma unroll 4
+                    for (; q + 1 <= nq; q += 2) {
+                        acc0 += sL(q) * s_h[q];
+                        acc1 += sL(q + 1) * s_h[q + 1];
+                    }
+                    if (q <= nq) acc0 += sL(q) * s_h[q];
+                    const double vn = xn - (acc0 + acc1);
+                    if (!finite_bits((unsigned long long)__double_as_longlong(vn))) nonfinite = true;
+                    if (form_x) {
+                        colp[i] = vn;
+                    } else {
+                        v = vn;
+                        if (i == p + 1) ctrl->vtop[(k + 1) & 1] = vn;
+                        offer(best, vn, (int)i);
+                    }
+                }
+            }
+        }
+        if (next) {
+            best.c = blockIdx.x;
+            publish(k + 1, best, nonfinite);
+        } else if (nonfinite) {
+            raise_error(ctrl, SKEW_ERR_NONFINITE);
+        }
     }
+    // tags of this launch were base+1 .. base+(kend-k0); the next launch starts above
+    if (blockIdx.x == 0 && tid == 0) st_release_u32_gpu(&ctrl->bar_gen, base + (unsigned int)(kend - k0) + 1u);
 }
 
 }  // namespace
 
-int launch_panel(const PanelArgs &a, int grid, cudaStream_t stream) {
+int launch_panel(const PanelArgs &a, int sms, cudaStream_t stream) {
     PanelArgs args = a;
     void *params[] = {&args};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)panel_kernel, dim3(grid),
-                                                dim3(kPanelThreads), params, 0, stream);
+    const int64_t rows = (int64_t)a.n - a.k0 - 1;
+    const int width = a.kend - a.k0;
+    cudaError_t e;
+    if (width <= kSmemMaxNb && rows <= (int64_t)sms * kPanelThreads) {
+        int64_t g = (rows + 31) / 32;
+        if (g > sms) g = sms;
+        if (g < 1) g = 1;
+        // (the dynamic shared-memory limit was raised when the device was first used,
+        // in panel_max_blocks_per_sm)
+        const size_t smem = (size_t)width * kPanelThreads * sizeof(double);
+        e = cudaLaunchCooperativeKernel((const void *)panel_smem_kernel, dim3((unsigned)g),
+                                        dim3(kPanelThreads), params, smem, stream);
+    } else {
+        int64_t g = (a.n + 127) / 128;
+        if (g > sms) g = sms;
+        if (g < 1) g = 1;
+        e = cudaLaunchCooperativeKernel((const void *)panel_global_kernel, dim3((unsigned)g),
+                                        dim3(kPanelThreads), params, 0, stream);
+    }
     if (e != cudaSuccess) {
         set_last_error(e);
         return SKEW_ERR_CUDA;
@@ -227,12 +620,21 @@ int launch_panel(const PanelArgs &a, int grid, cudaStream_t stream) {
 }
 
 int panel_max_blocks_per_sm(int *out) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, panel_kernel,
-                                                                  kPanelThreads, 0);
+    int a = 0, b = 0;
+    cudaError_t e = cudaFuncSetAttribute((const void *)panel_smem_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kSmemMaxNb * kPanelThreads * sizeof(double)));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, panel_global_kernel,
+                                                          kPanelThreads, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &b, panel_smem_kernel, kPanelThreads, kSmemMaxNb * kPanelThreads * sizeof(double));
     if (e != cudaSuccess) {
         set_last_error(e);
         return SKEW_ERR_CUDA;
     }
+    *out = a < b ? a : b;
     return SKEW_OK;
 }
 
