@@ -81,7 +81,7 @@ int skew_trim_memory(void);
  * recorded on the launch's stream, tagged with the launch's algorithmic work.
  * skew_profile_read waits for the recorded events, adds up the elapsed times per
  * kernel kind, and clears the record.  Kinds: 0 prologue, 1 panel, 2 pivot_rows,
- * 3 skr2k (the skew rank-2k update), 4 finish.
+ * 3 skr2k (the skew rank-2k update), 4 finish, 5 batched (the whole batched call).
  *   flops: skr2k counts 4 * (number of pairs) per strictly lower entry of C, i.e.
  *          2 * npairs * m * (m - 1); panel counts 2 * rows * (columns already formed)
  *          per step for its skew_tridiag_gemv.
@@ -96,7 +96,7 @@ typedef struct {
     uint64_t launches;  /* number of launches */
 } skew_kernel_stat;
 
-#define SKEW_KIND_COUNT 5
+#define SKEW_KIND_COUNT 6
 int skew_profile_enable(int on);
 int skew_profile_read(skew_kernel_stat *stats /* SKEW_KIND_COUNT entries */);
 
@@ -218,6 +218,53 @@ int skew_rank2k(int64_t m, int64_t k, double alpha, const double *X, int64_t ldx
 int skew_tridiag_rankk(int64_t m, int64_t b, double alpha, const double *A,
                        int64_t lda, const double *t, double beta, double *C,
                        int64_t ldc, void *stream);
+
+/*
+ * One problem of a batched call: an order-n skew matrix and where its factors go.
+ * All pointers are device pointers; the array of descriptors itself is in device
+ * memory too.  A is DESTROYED.  L may be NULL: the factorization is then computed
+ * without storing L (Pfaffian-only use).  t has n-1 entries, piv n.
+ */
+typedef struct {
+    int64_t n;
+    double *A;
+    int64_t lda;
+    double *L;
+    int64_t ldl;
+    double *t;
+    int32_t *piv;
+} skew_problem;
+
+/* Largest order skew_ltlt_batched accepts. */
+#define SKEW_BATCH_MAX_N 8192
+
+/* Device workspace of skew_ltlt_batched for `count` problems of order <= max_n. */
+size_t skew_batched_workspace_bytes(int count, int max_n);
+
+/*
+ * skew_ltlt_batched -- `count` independent pivoted factorizations P A P^T = L T L^T
+ * and their Pfaffians in one persistent launch: each CTA factors whole matrices
+ * (the unblocked right-looking algorithm of Section 4.1, Eq. (1), with the pivoting
+ * of Section 5.2), taking them largest first from a device queue.  Meant for many
+ * small and medium matrices (a few hundred); results are the same as skew_ltlt's up
+ * to rounding, with identical pivots.
+ *
+ *   1 count      number of problems, >= 0
+ *   2 problems   device array of `count` descriptors
+ *   3 logabs     device array [count] or NULL: log|Pf| per problem
+ *   4 sign       device array [count] or NULL: sign of Pf per problem
+ *   5 info       device array [count] or NULL: per problem as for skew_ltlt, or -2
+ *                when its descriptor is invalid (negative or too large n, NULL
+ *                pointers, short leading dimensions); that problem is skipped
+ *   6 max_n      an upper bound of every n, 0 <= max_n <= SKEW_BATCH_MAX_N
+ *   7 workspace  device buffer of skew_batched_workspace_bytes(count, max_n) bytes,
+ *                or NULL (allocated stream-ordered by the library)
+ *   8 workspace_bytes
+ *   9 stream
+ */
+int skew_ltlt_batched(int count, const skew_problem *problems, double *logabs,
+                      int32_t *sign, int32_t *info, int max_n, void *workspace,
+                      size_t workspace_bytes, void *stream);
 
 /*
  * skew_ltlt_host -- convenience form of skew_ltlt + skew_pfaffian_from_factors on

@@ -42,6 +42,8 @@ SIGNATURES = {
     "skew_rank2k": ([_i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _vp], _i32),
     "skew_tridiag_rankk": ([_i64, _i64, _dbl, _vp, _i64, _vp, _dbl, _vp, _i64, _vp], _i32),
     "skew_ltlt_host": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32], _i32),
+    "skew_batched_workspace_bytes": ([_i32, _i32], _sz),
+    "skew_ltlt_batched": ([_i32, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
 }
 
 
@@ -115,7 +117,7 @@ def _colmajor(name: str, M, rows: int):
     return max(M.stride(1) if M.shape[1] > 1 else rows, 1)
 
 
-KIND_NAMES = ["prologue", "panel", "pivot_rows", "skr2k", "finish"]
+KIND_NAMES = ["prologue", "panel", "pivot_rows", "skr2k", "finish", "batched"]
 
 
 class KernelStat(ctypes.Structure):
@@ -263,3 +265,50 @@ def ltlt_host(A: np.ndarray, want_L: bool = True, nb: int = 0, L_out=None, t_out
                               ctypes.byref(logabs), ctypes.byref(sign), ctypes.byref(info), nb)
     _check("skew_ltlt_host", st)
     return L, t[: max(n - 1, 0)], piv[:n], logabs.value, sign.value, info.value
+
+
+BATCH_MAX_N = 8192
+
+
+def problem_table(As, Ls, ts, pivs, device):
+    """Device array of skew_problem descriptors (n, A, lda, L, ldl, t, piv)."""
+    import torch
+    rows = []
+    for A, L, t, piv in zip(As, Ls, ts, pivs):
+        n = A.shape[0]
+        lda = max(A.stride(1) if n > 1 else 1, 1)
+        ldl = 0 if L is None else max(L.stride(1) if n > 1 else 1, 1)
+        rows.append([n, A.data_ptr() if n > 0 else 0, lda,
+                     0 if L is None else L.data_ptr(), ldl,
+                     t.data_ptr() if n > 1 else 0, piv.data_ptr() if n > 0 else 0])
+    host = torch.tensor(rows, dtype=torch.int64).reshape(-1, 7)
+    return host.to(device)
+
+
+def ltlt_batched(As, want_L: bool = False, stream=None, max_n: int | None = None,
+                 table=None, outs=None):
+    """Factor every column-major float64 CUDA tensor of the list ``As`` (destroyed) in
+    one batched launch.  Returns ``(logabs, sign, info, ts, pivs, Ls)``: per-problem
+    CUDA tensors (logabs float64 (count,), sign/info int32 (count,)) and lists of the
+    factors (``Ls`` entries are None unless ``want_L``)."""
+    import torch
+    count = len(As)
+    dev = As[0].device if count else torch.device("cuda")
+    if outs is None:
+        ts = [torch.empty(max(A.shape[0] - 1, 0), dtype=torch.float64, device=dev) for A in As]
+        pivs = [torch.empty(A.shape[0], dtype=torch.int32, device=dev) for A in As]
+        Ls = [fortran_empty(A.shape[0], A.shape[0], dev) if want_L else None for A in As]
+    else:
+        ts, pivs, Ls = outs
+    for A in As:
+        _colmajor("A", A, A.shape[0])
+    if table is None:
+        table = problem_table(As, Ls, ts, pivs, dev)
+    logabs = torch.empty(count, dtype=torch.float64, device=dev)
+    sign = torch.empty(count, dtype=torch.int32, device=dev)
+    info = torch.empty(count, dtype=torch.int32, device=dev)
+    mx = max((A.shape[0] for A in As), default=0) if max_n is None else max_n
+    st = lib().skew_ltlt_batched(count, _ptr(table) if count else None, _ptr(logabs),
+                                 _ptr(sign), _ptr(info), mx, None, 0, _stream_handle(stream))
+    _check("skew_ltlt_batched", st)
+    return logabs, sign, info, ts, pivs, Ls

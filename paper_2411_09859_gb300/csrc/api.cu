@@ -40,7 +40,7 @@ int check_launch() {
 // ------------------------------------------------------------------ per-kernel timing
 namespace {
 enum ProfKind { kProfPrologue = 0, kProfPanel = 1, kProfPivotRows = 2, kProfSkr2k = 3,
-                kProfFinish = 4 };
+                kProfFinish = 4, kProfBatched = 5 };
 struct ProfRec {
     int kind;
     cudaEvent_t a, b;
@@ -562,6 +562,44 @@ int skew_tridiag_rankk(int64_t m, int64_t b, double alpha, const double *A,
     sa.b = b;
     ProfScope ps(kProfSkr2k, static_cast<cudaStream_t>(stream), skr2k_flops(m, b / 2), skr2k_bytes(m));
     return launch_skr2k(PairKind::Tridiag, sa, static_cast<cudaStream_t>(stream));
+}
+
+size_t skew_batched_workspace_bytes(int count, int max_n) {
+    if (count < 0 || max_n < 0 || max_n > SKEW_BATCH_MAX_N) return 0;
+    return batched_workspace_bytes(count, max_n);
+}
+
+int skew_ltlt_batched(int count, const skew_problem *problems, double *logabs,
+                      int32_t *sign, int32_t *info, int max_n, void *workspace,
+                      size_t workspace_bytes, void *stream) {
+    if (count < 0) return -1;
+    if (problems == nullptr && count > 0) return -2;
+    if (max_n < 0 || max_n > SKEW_BATCH_MAX_N) return -6;
+    const size_t need = batched_workspace_bytes(count, max_n);
+    if (workspace != nullptr && workspace_bytes < need) return -8;
+    if (count == 0) return SKEW_OK;
+    DeviceInfo di;
+    SKEW_TRY_STATUS(current_device_info(&di));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *ws = workspace;
+    bool own = false;
+    if (ws == nullptr) {
+        SKEW_TRY_STATUS(pool_alloc(&ws, need, st));
+        own = true;
+    }
+    int status;
+    {
+        ProfScope ps(kProfBatched, st, 0.0, 0.0);
+        status = launch_batched(count, problems, logabs, sign, info, max_n, ws, st, di.sms);
+    }
+    if (own) {
+        cudaError_t e = cudaFreeAsync(ws, st);
+        if (e != cudaSuccess && status == SKEW_OK) {
+            set_last_error(e);
+            status = SKEW_ERR_CUDA;
+        }
+    }
+    return status;
 }
 
 int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,

@@ -1,0 +1,322 @@
+// batched.cu -- many independent small/medium factorizations in one persistent launch.
+//
+// Each CTA factors whole matrices, one at a time, taken from a device work queue in
+// descending order of size (largest first, so the launch ends evenly).  A matrix is
+// factored in place in its own storage (at n <= 256 the whole lower triangle, at
+// most 512 KB, stays in L2) by the pivoted right-looking algorithm of Section 4.1
+// (Eq. (1)) with the pivoting of Section 5.2: per step k, the pivot of column k
+// (largest magnitude, lowest index on ties), the symmetric exchange of k+1 and r in
+// lower storage, the Gauss transform l = x_31 / chi_21, and the skew rank-2 update
+// X33 += l x32^T - x32 l^T (two FMAs per stored entry).  Synchronisation is the CTA
+// barrier only.  The Pfaffian and the info word of each matrix are written at the
+// end, as in the single-matrix path.
+#include <climits>
+
+#include "common.cuh"
+
+namespace skew {
+namespace {
+
+constexpr int kBatchThreads = 512;
+constexpr unsigned long long kAbs = 0x7fffffffffffffffull;
+constexpr unsigned long long kExp = 0x7ff0000000000000ull;
+
+struct Cand {
+    unsigned long long raw;  // bits of the signed value
+    int i;
+};
+
+__device__ __forceinline__ bool cand_better(unsigned long long ra, int ia, unsigned long long rb,
+                                            int ib) {
+    const unsigned long long a = ra & kAbs, b = rb & kAbs;
+    return (a > b) || (a == b && ia < ib);
+}
+
+__device__ __forceinline__ Cand warp_cand(Cand x) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long orw = __shfl_down_sync(0xffffffffu, x.raw, off);
+        const int oi = __shfl_down_sync(0xffffffffu, x.i, off);
+        if (cand_better(orw, oi, x.raw, x.i)) { x.raw = orw; x.i = oi; }
+    }
+    return x;
+}
+
+struct BatchShared {
+    unsigned long long w_raw[kBatchThreads / 32];
+    int w_i[kBatchThreads / 32];
+    int w_bad[kBatchThreads / 32];
+    double w_sum[kBatchThreads / 32];
+    int w_par[kBatchThreads / 32];
+    int w_zero[kBatchThreads / 32];
+    unsigned long long best_raw;
+    int best_i;
+    int bad;
+    int item;
+};
+
+// argmax over the candidates of all threads; also ORs the non-finite flags
+__device__ Cand block_cand(Cand x, bool bad, BatchShared &sh, bool &any_bad) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    x = warp_cand(x);
+    const int wb = __any_sync(0xffffffffu, bad);
+    if (lane == 0) { sh.w_raw[w] = x.raw; sh.w_i[w] = x.i; sh.w_bad[w] = wb; }
+    __syncthreads();
+    if (w == 0) {
+        Cand y;
+        y.raw = 0ull;
+        y.i = INT_MAX;
+        int b = 0;
+        if (lane < kBatchThreads / 32) { y.raw = sh.w_raw[lane]; y.i = sh.w_i[lane]; b = sh.w_bad[lane]; }
+        y = warp_cand(y);
+        b = __any_sync(0xffffffffu, b);
+        if (lane == 0) { sh.best_raw = y.raw; sh.best_i = y.i; sh.bad = b; }
+    }
+    __syncthreads();
+    Cand r;
+    r.raw = sh.best_raw;
+    r.i = sh.best_i;
+    any_bad = sh.bad != 0;
+    return r;
+}
+
+__device__ void factor_one(const skew_problem &P, double *logabs, int32_t *sign, int32_t *info,
+                           double *s_l, double *s_x, BatchShared &sh) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+    const int n = (int)P.n;
+    double *X = P.A;
+    const int64_t ldx = P.lda;
+    double *L = P.L;
+    const int64_t ldl = P.ldl;
+    double *t = P.t;
+    int32_t *piv = P.piv;
+
+    for (int i = tid; i < n; i += nthr) piv[i] = i;
+    if (L != nullptr)
+        for (int j = warp; j < n; j += nwarps)
+            for (int i = lane; i < n; i += 32) L[i + j * ldl] = (i == j) ? 1.0 : 0.0;
+    bool nonfinite = false;
+    __syncthreads();
+
+    for (int k = 0; k + 1 < n; ++k) {
+        const int p = k + 1;
+        double *colk = X + (int64_t)k * ldx;
+        // ---- pivot: largest |X[i, k]|, i > k (Definition of iamax, Section 5.1)
+        Cand c;
+        c.raw = 0ull;
+        c.i = INT_MAX;
+        bool bad = false;
+        for (int i = p + tid; i < n; i += nthr) {
+            const unsigned long long raw = (unsigned long long)__double_as_longlong(colk[i]);
+            if ((raw & kExp) == kExp) { bad = true; continue; }
+            if (cand_better(raw, i, c.raw, c.i)) { c.raw = raw; c.i = i; }
+        }
+        bool any_bad;
+        const Cand best = block_cand(c, bad, sh, any_bad);
+        nonfinite |= any_bad;
+        const int r = (best.i == INT_MAX) ? p : best.i;
+        // ---- exchange k+1 <-> r: pivot column, rows of L, trailing skew block
+        if (r != p) {
+            for (int i = p + 1 + tid; i < n; i += nthr) {
+                double *colp = X + (int64_t)p * ldx;
+                if (i < r) {
+                    double *xri = X + (int64_t)i * ldx + r;
+                    const double tmp = colp[i];
+                    colp[i] = -*xri;
+                    *xri = -tmp;
+                } else if (i == r) {
+                    colp[i] = -colp[i];
+                } else {
+                    double *colr = X + (int64_t)r * ldx;
+                    const double tmp = colp[i];
+                    colp[i] = colr[i];
+                    colr[i] = tmp;
+                }
+            }
+            if (L != nullptr)
+                for (int c2 = 1 + tid; c2 <= k; c2 += nthr) {
+                    double *lc = L + (int64_t)c2 * ldl;
+                    const double tmp = lc[p];
+                    lc[p] = lc[r];
+                    lc[r] = tmp;
+                }
+            if (tid == 0) {
+                const double tmp = colk[p];
+                colk[p] = colk[r];
+                colk[r] = tmp;
+            }
+        }
+        __syncthreads();
+        // ---- Gauss transform (Eq. (1)): tau = X[k+1, k], l = X[k+2:, k] / tau
+        const double tau = colk[p];
+        if (tid == 0) {
+            t[k] = tau;
+            piv[p] = r;
+        }
+        const double *colp = X + (int64_t)p * ldx;
+        for (int i = p + 1 + tid; i < n; i += nthr) {
+            const double l = (tau != 0.0) ? colk[i] / tau : 0.0;
+            s_l[i] = l;
+            s_x[i] = colp[i];
+            if (L != nullptr) L[i + (int64_t)p * ldl] = l;
+        }
+        __syncthreads();
+        // ---- X33 += l x32^T - x32 l^T on the strictly lower part (columns k+2..n-1)
+        for (int j = k + 2 + warp; j < n; j += nwarps) {
+            double *colj = X + (int64_t)j * ldx;
+            const double xj = s_x[j], lj = s_l[j];
+            for (int i = j + 1 + lane; i < n; i += 32)
+                colj[i] = fma(-s_x[i], lj, fma(s_l[i], xj, colj[i]));
+        }
+        __syncthreads();
+    }
+
+    // ---- Pf = det(P) prod_i (-t[2i]) (Section 1), fixed reduction order
+    double sum = 0.0;
+    int par = 0, zero = 0;
+    const int half = n / 2;
+    if ((n & 1) == 0)
+        for (int j = tid; j < half; j += nthr) {
+            const double v = -t[2 * j];
+            if (v == 0.0) zero = 1;
+            else {
+                if (v < 0.0) par ^= 1;
+                sum += log(fabs(v));
+            }
+        }
+    for (int i = tid; i < n; i += nthr)
+        if (piv[i] != i) par ^= 1;
+    int first_zero = INT_MAX;
+    for (int j = tid; j + 1 < n; j += nthr)
+        if (t[j] == 0.0 && j < first_zero) first_zero = j;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        sum += __shfl_down_sync(0xffffffffu, sum, off);
+        par ^= __shfl_down_sync(0xffffffffu, par, off);
+        zero |= __shfl_down_sync(0xffffffffu, zero, off);
+        first_zero = min(first_zero, __shfl_down_sync(0xffffffffu, first_zero, off));
+    }
+    if (lane == 0) {
+        sh.w_sum[warp] = sum;
+        sh.w_par[warp] = par;
+        sh.w_zero[warp] = zero;
+        sh.w_i[warp] = first_zero;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        int pr = 0, z = 0, fz = INT_MAX;
+        for (int w = 0; w < nwarps; ++w) {
+            s += sh.w_sum[w];
+            pr ^= sh.w_par[w];
+            z |= sh.w_zero[w];
+            fz = min(fz, sh.w_i[w]);
+        }
+        const bool pf_zero = (n & 1) || z;
+        if (logabs) *logabs = pf_zero ? -INFINITY : s;
+        if (sign) *sign = pf_zero ? 0 : (pr ? -1 : 1);
+        if (info) *info = nonfinite ? SKEW_ERR_NONFINITE : (fz == INT_MAX ? 0 : fz + 1);
+    }
+    __syncthreads();
+}
+
+// Persistent: each CTA takes the next matrix of the size-ordered queue.
+__global__ void __launch_bounds__(kBatchThreads)
+batched_kernel(int count, const skew_problem *problems, const int32_t *order,
+               unsigned int *counter, double *logabs, int32_t *sign, int32_t *info, int max_n) {
+    extern __shared__ double s_vec[];
+    __shared__ BatchShared sh;
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int item = sh.item;
+        __syncthreads();
+        if (item >= count) return;
+        const int b = order[item];
+        const skew_problem P = problems[b];
+        const int n = (int)P.n;
+        if (n < 0 || n > max_n || (n > 0 && P.A == nullptr) || P.lda < (n > 1 ? n : 1) ||
+            (P.L != nullptr && P.ldl < (n > 1 ? n : 1)) || (n > 1 && P.t == nullptr) ||
+            (n > 0 && P.piv == nullptr)) {
+            if (threadIdx.x == 0 && info) info[b] = -2;   // a bad problem descriptor
+            continue;
+        }
+        factor_one(P, logabs ? logabs + b : nullptr, sign ? sign + b : nullptr,
+                   info ? info + b : nullptr, s_vec, s_vec + (n > 0 ? n : 1), sh);
+    }
+}
+
+// Counting sort of the problems by order, largest first (one CTA).
+__global__ void __launch_bounds__(1024)
+order_kernel(int count, const skew_problem *problems, int max_n, int32_t *order,
+             unsigned int *counter, unsigned int *hist) {
+    for (int v = threadIdx.x; v <= max_n + 1; v += blockDim.x) hist[v] = 0u;
+    if (threadIdx.x == 0) *counter = 0u;
+    __syncthreads();
+    for (int b = threadIdx.x; b < count; b += blockDim.x) {
+        int64_t n = problems[b].n;
+        int key = (n < 0 || n > max_n) ? 0 : (int)(max_n - n);   // descending size
+        atomicAdd(&hist[key], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int run = 0;
+        for (int v = 0; v <= max_n; ++v) {
+            const unsigned int h = hist[v];
+            hist[v] = run;
+            run += h;
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < count; b += blockDim.x) {
+        int64_t n = problems[b].n;
+        int key = (n < 0 || n > max_n) ? 0 : (int)(max_n - n);
+        const unsigned int pos = atomicAdd(&hist[key], 1u);
+        order[pos] = b;
+    }
+}
+
+}  // namespace
+
+size_t batched_workspace_bytes(int count, int max_n) {
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    return al(sizeof(unsigned int)) + al(sizeof(int32_t) * (size_t)(count > 0 ? count : 1)) +
+           al(sizeof(unsigned int) * (size_t)(max_n + 2));
+}
+
+int launch_batched(int count, const skew_problem *problems, double *logabs, int32_t *sign,
+                   int32_t *info, int max_n, void *ws, cudaStream_t stream, int sms) {
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    char *base = static_cast<char *>(ws);
+    unsigned int *counter = reinterpret_cast<unsigned int *>(base);
+    int32_t *order = reinterpret_cast<int32_t *>(base + al(sizeof(unsigned int)));
+    unsigned int *hist = reinterpret_cast<unsigned int *>(
+        base + al(sizeof(unsigned int)) + al(sizeof(int32_t) * (size_t)(count > 0 ? count : 1)));
+    order_kernel<<<1, 1024, 0, stream>>>(count, problems, max_n, order, counter, hist);
+    note_launches(1);
+    SKEW_TRY_STATUS(check_launch());
+    const size_t smem = 2 * sizeof(double) * (size_t)(max_n > 1 ? max_n : 1);
+    static_assert(kBatchThreads == 512, "launch shape");
+    cudaError_t e = cudaFuncSetAttribute((const void *)batched_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) {
+        set_last_error(e);
+        return SKEW_ERR_CUDA;
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, kBatchThreads, smem);
+    if (e != cudaSuccess || per_sm < 1) {
+        if (e != cudaSuccess) set_last_error(e);
+        return SKEW_ERR_CUDA;
+    }
+    int grid = sms * per_sm;
+    if (grid > count) grid = count;
+    batched_kernel<<<grid, kBatchThreads, smem, stream>>>(count, problems, order, counter,
+                                                          logabs, sign, info, max_n);
+    note_launches(1);
+    return check_launch();
+}
+
+}  // namespace skew

@@ -197,6 +197,11 @@ struct Skr2kArgs {
 };
 int launch_skr2k(PairKind kind, const Skr2kArgs &a, cudaStream_t stream);
 
+// Batched persistent factorization (batched.cu).
+size_t batched_workspace_bytes(int count, int max_n);
+int launch_batched(int count, const skew_problem *problems, double *logabs, int32_t *sign,
+                   int32_t *info, int max_n, void *ws, cudaStream_t stream, int sms);
+
 // log|Pf|, sign (either may be null), and the final info word (may be null).
 int launch_finish(int64_t n, const double *t, const int32_t *piv, const Ctrl *ctrl,
                   double *logabs, int32_t *sign, int32_t *info, cudaStream_t stream);

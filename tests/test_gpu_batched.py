@@ -1,0 +1,117 @@
+"""Batched persistent form (skew_ltlt_batched) against the oracle and the single
+matrix path: identical pivots, factors within the element-wise tolerance of the
+single-matrix tests, log|Pf| within 1e-10 relative with the same sign."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import oracle  # noqa: E402
+import paper_2411_09859_gb300 as skew  # noqa: E402
+from paper_2411_09859_gb300 import inputs  # noqa: E402
+from skewcheck import EPS, check_structure  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL_C = 2000.0
+
+
+def dev(A):
+    return torch.from_numpy(np.asfortranarray(A, dtype=np.float64)).cuda()
+
+
+def run_batch(mats, want_L):
+    As = [dev(A) for A in mats]
+    la, sg, info, ts, pivs, Ls = skew.ltlt_batched(As, want_L=want_L)
+    torch.cuda.synchronize()
+    return (la.cpu().numpy(), sg.cpu().numpy(), info.cpu().numpy(),
+            [t.cpu().numpy() for t in ts], [p.cpu().numpy() for p in pivs],
+            [None if L is None else L.cpu().numpy() for L in Ls])
+
+
+def check_against_oracle(A, la, sg, info, t, piv, L):
+    n = A.shape[0]
+    L0, t0, p0, i0 = oracle.ltlt(A)
+    assert np.array_equal(piv, p0)
+    assert info == i0
+    tol = TOL_C * max(n, 1) * EPS
+    if n > 1:
+        assert np.max(np.abs(t - t0)) <= tol * max(1.0, np.max(np.abs(t0)))
+    if L is not None:
+        if n > 1:
+            assert np.max(np.abs(L - L0)) <= tol
+        check_structure(L, t, piv, n)
+    la0, sg0 = oracle.pfaffian_from_factors(n, t0, p0)
+    assert sg == sg0
+    if sg0 != 0:
+        assert abs(la - la0) <= 1e-10 * max(1.0, abs(la0))
+
+
+@pytest.mark.parametrize("want_L", [False, True])
+def test_mixed_orders_against_oracle(want_L):
+    sizes = [0, 1, 2, 3, 4, 5, 16, 17, 31, 64, 100, 127, 128, 200, 255, 256, 257, 300, 513]
+    mats = [inputs.skew_gaussian(n, 5000 + n) for n in sizes]
+    la, sg, info, ts, pivs, Ls = run_batch(mats, want_L)
+    for b, A in enumerate(mats):
+        check_against_oracle(A, la[b], sg[b], info[b], ts[b], pivs[b], Ls[b])
+
+
+def test_batched_workload_sample():
+    """The 4096-matrix workload (orders even in [16, 256], matrix i from seed 1000+i):
+    all of it in one launch; every 32nd matrix checked against the oracle, all of
+    them for the invariants."""
+    sizes = inputs.batched_sizes(4096)
+    mats = [inputs.skew_gaussian(int(n), inputs.SEED_BATCH_BASE + i) for i, n in enumerate(sizes)]
+    la, sg, info, ts, pivs, Ls = run_batch(mats, False)
+    assert np.all(info == 0)
+    assert np.all(sg != 0)
+    for b in range(0, 4096, 32):
+        check_against_oracle(mats[b], la[b], sg[b], info[b], ts[b], pivs[b], None)
+    for b in range(4096):
+        n = int(sizes[b])
+        assert pivs[b][0] == 0 and np.all(pivs[b] >= np.arange(n))
+
+
+def test_batched_equals_single_calls():
+    mats = [inputs.skew_gaussian(n, 6000 + n) for n in (40, 96, 180, 256)]
+    la, sg, info, ts, pivs, Ls = run_batch(mats, True)
+    for b, A in enumerate(mats):
+        L1, t1, p1, i1 = skew.ltlt(dev(A), nb=16)
+        torch.cuda.synchronize()
+        assert np.array_equal(pivs[b], p1.cpu().numpy())
+        n = A.shape[0]
+        assert np.max(np.abs(ts[b] - t1.cpu().numpy())) <= TOL_C * n * EPS * np.max(np.abs(ts[b]))
+        assert np.max(np.abs(Ls[b] - L1.cpu().numpy())) <= TOL_C * n * EPS
+
+
+def test_zero_pivots_block_diagonal():
+    D = inputs.block_diag_skew([1.0, 3.0, 5.0])
+    la, sg, info, ts, pivs, Ls = run_batch([D, D.copy()], True)
+    for b in range(2):
+        assert np.array_equal(ts[b], [-1.0, 0.0, -3.0, 0.0, -5.0])
+        assert info[b] == 2 and sg[b] == 1 and math.isclose(la[b], math.log(15.0), rel_tol=1e-15)
+        assert np.array_equal(Ls[b], np.eye(6))
+
+
+def test_bad_descriptor_and_nonfinite():
+    good = inputs.skew_gaussian(20, 1)
+    bad = inputs.skew_gaussian(20, 2)
+    bad[10, 3] = np.nan
+    As = [dev(good), dev(bad), dev(good)]
+    ts = [torch.empty(19, dtype=torch.float64, device="cuda") for _ in range(3)]
+    pivs = [torch.empty(20, dtype=torch.int32, device="cuda") for _ in range(3)]
+    table = skew.problem_table(As, [None] * 3, ts, pivs, "cuda")
+    table[2, 2] = 5                     # lda < n: an invalid descriptor
+    la, sg, info, *_ = skew.ltlt_batched(As, table=table, outs=(ts, pivs, [None] * 3))
+    torch.cuda.synchronize()
+    info = info.cpu().numpy()
+    assert info[0] == 0 and info[1] == -100 and info[2] == -2
+
+
+def test_rejects_bad_arguments():
+    st = skew.lib().skew_ltlt_batched(-1, None, None, None, None, 16, None, 0, None)
+    assert st == -1
+    st = skew.lib().skew_ltlt_batched(3, None, None, None, None, 16, None, 0, None)
+    assert st == -2
+    st = skew.lib().skew_ltlt_batched(0, None, None, None, None, 99999, None, 0, None)
+    assert st == -6
