@@ -52,6 +52,9 @@ def parse_args():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-poisson", type=int, default=500)
     ap.add_argument("--plain-calls", type=int, default=1024,
                     help="matrices of the batched workload timed as back-to-back plain calls")
     return ap.parse_args()
@@ -252,6 +255,94 @@ def run_batched_leg(skew, inputs, torch, dev, steps: int, warmup: int, plain_cou
                         "log|Pf| within 1e-10 relative on the tested sample"}
 
 
+# ----------------------------------------------------------------------------- serving
+def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int):
+    """The serving workload: requests with even orders log-uniform in [32, 4096]
+    (seed 6); request i is the leading n_i x n_i block of one seeded 4096 x 4096 skew
+    matrix (every principal block of an iid N(0,1) skew matrix is one of order n_i).
+    Compared: serial back-to-back skew_pfaffian calls; the continuous-batching server
+    (64 GB budget, 4 streams, batched kernel up to n = 512) with all requests
+    submitted at once; and the server fed by a Poisson stream at 0.8x the serial rate
+    (seeded gaps), reporting p50/p99 latency from submission to completion."""
+    rng = np.random.default_rng(inputs.SEED_SERVING)
+    logn = rng.uniform(np.log(32), np.log(4096), size=n_requests)
+    sizes = np.clip(2 * np.round(np.exp(logn) / 2), 32, 4096).astype(np.int64)
+    master = torch.from_numpy(inputs.skew_gaussian(4096, inputs.SEED_SERVING)).to(dev)
+    views = [master[:int(n), :int(n)] for n in sizes]
+    flops = float(np.sum(sizes.astype(np.float64) ** 3) / 3.0)
+    stream = torch.cuda.Stream(device=dev)
+    work = skew.fortran_empty(4096, 4096, dev)
+
+    def serial(idx):
+        for i in idx:
+            n = int(sizes[i])
+            w = work[:n, :n]
+            w.copy_(views[i])
+            skew.pfaffian(w, stream=stream)
+
+    with torch.cuda.stream(stream):
+        serial(range(min(8, n_requests)))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        serial(range(n_requests))
+        e1.record(stream)
+    torch.cuda.synchronize()
+    serial_s = e0.elapsed_time(e1) / 1e3
+    serial_rate = n_requests / serial_s
+
+    srv = skew.Server(64 << 30, n_streams=4, small_n_max=512)
+    for tk in [srv.submit(views[i]) for i in range(min(16, n_requests))]:
+        srv.wait(tk)
+        srv.release(tk)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(v) for v in views]
+    res = [srv.wait(tk) for tk in tickets]
+    sat_s = time.perf_counter() - t0
+    for tk in tickets:
+        srv.release(tk)
+    sat_lat = np.array([r["latency_s"] for r in res]) * 1e3
+    bad = sum(1 for r in res if r["info"] != 0)
+
+    lam = 0.8 * serial_rate
+    gaps = np.random.default_rng(inputs.SEED_SERVING + 1).exponential(1.0 / lam, size=n_poisson)
+    t0 = time.perf_counter()
+    tickets = []
+    next_t = t0
+    for i in range(n_poisson):
+        next_t += gaps[i]
+        delay = next_t - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(views[i]))
+    res2 = [srv.wait(tk) for tk in tickets]
+    poi_s = time.perf_counter() - t0
+    for tk in tickets:
+        srv.release(tk)
+    srv.close()
+    poi_lat = np.array([r["latency_s"] for r in res2]) * 1e3
+    bad += sum(1 for r in res2 if r["info"] != 0)
+    if bad:
+        raise RuntimeError(f"{bad} served requests reported a nonzero info")
+    return {"metric": "served Pfaffians/s and latency", "unit": "Pfaffians/s",
+            "workload": (f"{n_requests} requests, even n log-uniform in [32, 4096] (seed 6), "
+                         "leading blocks of one seeded 4096^2 iid N(0,1) skew matrix; the "
+                         "20000-request stream is shortened to keep the run short"),
+            "serial_plain_calls": {"value": serial_rate, "seconds": serial_s,
+                                   "tflops": flops / serial_s / 1e12},
+            "saturation": {"value": n_requests / sat_s, "seconds": sat_s,
+                           "tflops": flops / sat_s / 1e12,
+                           "p50_ms": float(np.percentile(sat_lat, 50)),
+                           "p99_ms": float(np.percentile(sat_lat, 99)),
+                           "speedup_vs_serial": serial_s / sat_s},
+            "poisson": {"rate_per_s": lam, "requests": n_poisson,
+                        "value": n_poisson / poi_s,
+                        "p50_ms": float(np.percentile(poi_lat, 50)),
+                        "p99_ms": float(np.percentile(poi_lat, 99))},
+            "server": "budget 64 GB, 4 streams, batched kernel for n <= 512"}
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -415,6 +506,11 @@ def run_ours(args):
         batched = run_batched_leg(skew, inputs, torch, dev, steps=3, warmup=1,
                                   plain_count=args.plain_calls)
 
+    serving = None
+    if not args.skip_serving:
+        serving = run_serving_leg(skew, inputs, torch, dev, args.serve_requests,
+                                  args.serve_poisson)
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu_baseline:
         r = oracle_sample(A_host, max(1, min(args.cpu_sample_steps, n - 1)))
@@ -437,6 +533,7 @@ def run_ours(args):
             "kernels": kernels,
             "e2e": e2e,
             "batched": batched,
+            "serving": serving,
             "cpu_baseline": cpu,
             "gpu_launches": launches,
             "clocks": clocks,

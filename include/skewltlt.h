@@ -55,8 +55,9 @@ typedef enum {
     SKEW_ERR_CUDA = -102,       /* a CUDA runtime call failed (see skew_last_error) */
     SKEW_ERR_TIMEOUT = -103,    /* a bounded device-side wait gave up */
     SKEW_ERR_NODEVICE = -104,   /* no usable sm_103 device is current */
-    SKEW_ERR_SCRATCH_LIMIT = -105 /* skew_pfaffian_noalloc: the problem needs more
-                                     than its fixed scratch (see there) */
+    SKEW_ERR_SCRATCH_LIMIT = -105, /* skew_pfaffian_noalloc: the problem needs more
+                                      than its fixed scratch (see there) */
+    SKEW_ERR_BUSY = -106           /* skew_server_release: the request is in flight */
 } skew_status;
 
 /* Library version as 10000*major + 100*minor + patch. */
@@ -265,6 +266,67 @@ size_t skew_batched_workspace_bytes(int count, int max_n);
 int skew_ltlt_batched(int count, const skew_problem *problems, double *logabs,
                       int32_t *sign, int32_t *info, int max_n, void *workspace,
                       size_t workspace_bytes, void *stream);
+
+/*
+ * Serving form: a continuous-batching server of factorizations / Pfaffians.
+ *
+ * skew_server_submit queues a request (an order-n skew matrix in device memory) and
+ * returns at once with a ticket.  A worker thread of the server admits queued
+ * requests in arrival order as soon as their device memory (a copy of the matrix, t,
+ * piv, and L if asked for) fits in the budget; it launches admitted work on the first
+ * free stream -- all admitted requests of order <= small_n_max together in one
+ * skew_ltlt_batched launch, larger ones one at a time through skew_ltlt /
+ * skew_pfaffian -- so that requests arriving while others are on the GPU are batched
+ * and run beside them on other streams.  Results (log|Pf|, sign, info, and the
+ * factors t, piv, L in device memory) stay resident until skew_server_release.
+ * The matrix a request points to must be fully written when it is submitted (its
+ * producing work complete), and is read before the request completes: keep it
+ * unchanged until skew_server_poll reports it done.  A request whose buffers exceed
+ * the whole budget is refused with SKEW_ERR_NOMEM.  All calls are thread-safe.
+ */
+typedef struct skew_server skew_server;
+
+/*   1 device_budget_bytes  device memory the requests' buffers may hold at once
+ *   2 n_streams            concurrent launches (1 .. 64)
+ *   3 small_n_max          largest order sent to the batched kernel (0 .. 8192)
+ *   4 out                  the new server (on the current device) */
+int skew_server_create(size_t device_budget_bytes, int n_streams, int small_n_max,
+                       skew_server **out);
+
+/*   1 server, 2 n, 3 A (device, lda x n, strictly lower triangle read, not modified),
+ *   4 lda, 5 want_L (nonzero: keep L), 6 ticket (out) */
+int skew_server_submit(skew_server *server, int64_t n, const double *A, int64_t lda,
+                       int want_L, uint64_t *ticket);
+
+/* done = 1 once the request has completed (or failed), else 0.  -2: unknown ticket. */
+int skew_server_poll(skew_server *server, uint64_t ticket, int *done);
+
+/*
+ * Wait up to timeout_s seconds (negative: no limit) for a request; then return its
+ * status and, through the non-NULL pointers, log|Pf|, its sign and the info word
+ * (host values), the device pointers of t, piv and L (L NULL unless kept) and the
+ * latency from submission to completion in seconds.  SKEW_ERR_TIMEOUT if it has not
+ * completed in time (it keeps running).
+ */
+int skew_server_wait(skew_server *server, uint64_t ticket, double timeout_s, double *logabs,
+                     int32_t *sign, int32_t *info, const double **t, const int32_t **piv,
+                     const double **L, double *latency_s);
+
+/* Free a completed (or still queued) request's device buffers and forget the ticket.
+ * SKEW_ERR_BUSY while it is admitted or running. */
+int skew_server_release(skew_server *server, uint64_t ticket);
+
+/* Copy a completed request's factors to host buffers (any of them NULL to skip):
+ * t_host (n-1 values), piv_host (n), L_host (ldl x n; the request must have kept L).
+ * Synchronous.  SKEW_ERR_BUSY if the request has not completed. */
+int skew_server_copy_factors(skew_server *server, uint64_t ticket, double *t_host,
+                             int32_t *piv_host, double *L_host, int64_t ldl);
+
+/* Budget bytes in use, requests waiting for admission, requests admitted or running. */
+int skew_server_stats(skew_server *server, size_t *used_bytes, int *queued, int *in_flight);
+
+/* Finish admitted work, drop requests never admitted, free everything. */
+int skew_server_destroy(skew_server *server);
 
 /*
  * skew_ltlt_host -- convenience form of skew_ltlt + skew_pfaffian_from_factors on

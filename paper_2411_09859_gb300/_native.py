@@ -18,6 +18,7 @@ STATUS = {
     -103: "SKEW_ERR_TIMEOUT",
     -104: "SKEW_ERR_NODEVICE",
     -105: "SKEW_ERR_SCRATCH_LIMIT",
+    -106: "SKEW_ERR_BUSY",
 }
 
 _lock = threading.Lock()
@@ -44,6 +45,14 @@ SIGNATURES = {
     "skew_ltlt_host": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32], _i32),
     "skew_batched_workspace_bytes": ([_i32, _i32], _sz),
     "skew_ltlt_batched": ([_i32, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
+    "skew_server_create": ([_sz, _i32, _i32, _vp], _i32),
+    "skew_server_submit": ([_vp, _i64, _vp, _i64, _i32, _vp], _i32),
+    "skew_server_poll": ([_vp, ctypes.c_uint64, _vp], _i32),
+    "skew_server_wait": ([_vp, ctypes.c_uint64, _dbl, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
+    "skew_server_release": ([_vp, ctypes.c_uint64], _i32),
+    "skew_server_stats": ([_vp, _vp, _vp, _vp], _i32),
+    "skew_server_copy_factors": ([_vp, ctypes.c_uint64, _vp, _vp, _vp, _i64], _i32),
+    "skew_server_destroy": ([_vp], _i32),
 }
 
 
@@ -312,3 +321,74 @@ def ltlt_batched(As, want_L: bool = False, stream=None, max_n: int | None = None
                                  _ptr(sign), _ptr(info), mx, None, 0, _stream_handle(stream))
     _check("skew_ltlt_batched", st)
     return logabs, sign, info, ts, pivs, Ls
+
+
+
+class Server:
+    """Continuous-batching server (skew_server_*).  Requests are column-major float64
+    CUDA tensors; keep each one unchanged until its result has been waited for."""
+
+    def __init__(self, budget_bytes: int, n_streams: int = 4, small_n_max: int = 512):
+        self._h = ctypes.c_void_p()
+        _check("skew_server_create", lib().skew_server_create(int(budget_bytes), n_streams,
+                                                              small_n_max, ctypes.byref(self._h)))
+        self._keep = {}
+
+    def submit(self, A, want_L: bool = False) -> int:
+        n = A.shape[0]
+        lda = _colmajor("A", A, n)
+        tk = ctypes.c_uint64()
+        _check("skew_server_submit", lib().skew_server_submit(
+            self._h, n, _ptr(A) if n > 0 else None, lda, 1 if want_L else 0, ctypes.byref(tk)))
+        self._keep[tk.value] = A
+        return tk.value
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int()
+        _check("skew_server_poll", lib().skew_server_poll(self._h, ticket, ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_s: float = -1.0):
+        """Returns dict(logabs, sign, info, t_ptr, piv_ptr, L_ptr, latency_s)."""
+        la, sg, inf, lat = ctypes.c_double(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        tp, pp, lp = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        st = lib().skew_server_wait(self._h, ticket, float(timeout_s), ctypes.byref(la),
+                                    ctypes.byref(sg), ctypes.byref(inf), ctypes.byref(tp),
+                                    ctypes.byref(pp), ctypes.byref(lp), ctypes.byref(lat))
+        _check("skew_server_wait", st)
+        return {"logabs": la.value, "sign": sg.value, "info": inf.value, "t_ptr": tp.value,
+                "piv_ptr": pp.value, "L_ptr": lp.value, "latency_s": lat.value}
+
+    def factors(self, ticket: int, n: int, want_L: bool = False):
+        """Host copies (t, piv, L or None) of a completed request's factors."""
+        t = np.zeros(max(n - 1, 1), dtype=np.float64)
+        piv = np.zeros(max(n, 1), dtype=np.int32)
+        L = np.zeros((n, n), dtype=np.float64, order="F") if want_L else None
+        st = lib().skew_server_copy_factors(self._h, ticket, ctypes.c_void_p(t.ctypes.data),
+                                            ctypes.c_void_p(piv.ctypes.data),
+                                            None if L is None else ctypes.c_void_p(L.ctypes.data),
+                                            max(n, 1))
+        _check("skew_server_copy_factors", st)
+        return t[: max(n - 1, 0)], piv[:n], L
+
+    def release(self, ticket: int):
+        _check("skew_server_release", lib().skew_server_release(self._h, ticket))
+        self._keep.pop(ticket, None)
+
+    def stats(self):
+        used, q, f = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
+        _check("skew_server_stats", lib().skew_server_stats(self._h, ctypes.byref(used),
+                                                            ctypes.byref(q), ctypes.byref(f)))
+        return {"used_bytes": used.value, "queued": q.value, "in_flight": f.value}
+
+    def close(self):
+        if self._h:
+            _check("skew_server_destroy", lib().skew_server_destroy(self._h))
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

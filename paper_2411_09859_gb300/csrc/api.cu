@@ -159,6 +159,8 @@ int device_pool(int dev, cudaMemPool_t *out) {
     return SKEW_OK;
 }
 
+}  // namespace
+
 int pool_alloc(void **p, size_t bytes, cudaStream_t st) {
     int dev;
     SKEW_TRY(cudaGetDevice(&dev));
@@ -172,7 +174,6 @@ int pool_alloc(void **p, size_t bytes, cudaStream_t st) {
     }
     return SKEW_OK;
 }
-}  // namespace
 
 int current_device_info(DeviceInfo *out) {
     int dev = -1;

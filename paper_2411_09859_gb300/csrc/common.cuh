@@ -36,6 +36,10 @@ struct DeviceInfo {
 // Properties of the current device; SKEW_ERR_NODEVICE unless it is an sm_103 part.
 int current_device_info(DeviceInfo *out);
 
+// Stream-ordered allocation from the library's private pool of the current device
+// (freed blocks stay reserved for reuse); release with cudaFreeAsync.
+int pool_alloc(void **p, size_t bytes, cudaStream_t st);
+
 // ------------------------------------------------------------------ device control block
 // Lives at the start of every workspace.  Zeroed (cudaMemsetAsync) at the start of
 // each factorization.
