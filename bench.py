@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--skip-precision", action="store_true")
+    ap.add_argument("--qdq-n", type=int, default=2048)
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-poisson", type=int, default=500)
     ap.add_argument("--plain-calls", type=int, default=1024,
@@ -253,6 +255,78 @@ def run_batched_leg(skew, inputs, torch, dev, steps: int, warmup: int, plain_cou
             "speedup_vs_plain_calls": rate / plain_rate,
             "accuracy": "same algorithm in FP64; pivots identical to the oracle and "
                         "log|Pf| within 1e-10 relative on the tested sample"}
+
+
+# ----------------------------------------------------------------------------- precision
+def run_precision_leg(skew, inputs, torch, dev, A_host, nb_fp64, fp64_ms, fp64_t, fp64_piv,
+                      steps: int, warmup: int, n_qdq: int):
+    """The precision form: the same n = 16384 matrix with the trailing update run as
+    split-precision bf16 tensor-core products (panel, pivots, division, t and
+    log|Pf| in FP64), timed like the FP64 run, compared with it (pivots, log|Pf|);
+    and A = Q D Q^T (Q Haar in SO(n), D blocks [[0,s],[-s,0]], s log-spaced in
+    [1, 1e6], seed 5) at a reduced order n_qdq, against its closed form
+    log|Pf| = sum ln s and against the CPU oracle, for both precisions."""
+    import oracle
+    n = A_host.shape[0]
+    split = skew.PRECISION_SPLIT_BF16
+    nb = min(nb_fp64, 64)
+    pristine = torch.from_numpy(A_host).to(dev)
+    L = skew.fortran_empty(n, n, dev)
+    t = torch.empty(n - 1, dtype=torch.float64, device=dev)
+    piv = torch.empty(n, dtype=torch.int32, device=dev)
+    info = torch.empty(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    work = skew.fortran_empty(n, n, dev)
+    times = []
+    for i in range(warmup + steps):
+        work.copy_(pristine)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        skew.ltlt(work, nb=nb, stream=stream, L=L, t=t, piv=piv, info=info, precision=split)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= warmup:
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    t_s, piv_s = t.cpu().numpy(), piv.cpu().numpy()
+    la_f, sg_f = skew.pfaffian_from_factors(torch.from_numpy(fp64_t).to(dev),
+                                            torch.from_numpy(fp64_piv).to(dev), n)
+    la_s, sg_s = skew.pfaffian_from_factors(t, piv, n)
+    torch.cuda.synchronize()
+    la_f, la_s = float(la_f.item()), float(la_s.item())
+    first_diff = int(np.argmax(piv_s != fp64_piv)) if not np.array_equal(piv_s, fp64_piv) else None
+    del pristine, work, L
+    torch.cuda.empty_cache()
+
+    # QDQ^T accuracy at a reduced order
+    Aq, s_vals = inputs.qdq_skew(n_qdq, inputs.SEED_PRECISION, smax=1e6)
+    closed = float(np.sum(np.log(s_vals)))
+    L0, t0, p0, _ = oracle.ltlt(Aq)
+    la_o, sg_o = oracle.pfaffian_from_factors(n_qdq, t0, p0)
+    acc = {}
+    for name, prec in (("fp64_dmma", skew.PRECISION_FP64), ("split_bf16", split)):
+        la, sg, tq, pq, iq = skew.pfaffian(torch.from_numpy(Aq).to(dev), nb=min(64, nb_fp64),
+                                           precision=prec)
+        torch.cuda.synchronize()
+        la = float(la.item())
+        acc[name] = {"log_abs_pf": la, "sign": int(sg.item()),
+                     "rel_err_vs_closed_form": abs(la - closed) / abs(closed),
+                     "rel_err_vs_oracle": abs(la - la_o) / abs(la_o),
+                     "pivots_equal_oracle": bool(np.array_equal(pq.cpu().numpy(), p0))}
+    flops = factorization_flops(n)
+    return {"metric": "skew LTLt TFLOP/s (n^3/3) with the split-precision trailing update",
+            "value": flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+            "speedup_vs_fp64": fp64_ms / ms, "nb": nb,
+            "vs_fp64_run": {"pivots_equal": first_diff is None, "first_pivot_difference": first_diff,
+                            "log_abs_pf_fp64": la_f, "log_abs_pf_split": la_s,
+                            "rel_diff": abs(la_s - la_f) / abs(la_f), "sign_equal": int(sg_f.item()) == int(sg_s.item()),
+                            "max_rel_t_diff": float(np.max(np.abs(t_s - fp64_t)) / np.max(np.abs(fp64_t)))},
+            "qdq": {"n": n_qdq, "closed_form_log_abs_pf": closed, "oracle_log_abs_pf": la_o,
+                    "oracle_rel_err_vs_closed_form": abs(la_o - closed) / abs(closed), **acc,
+                    "note": "QDQ^T workload run at a reduced order: its O(n^3) host generation "
+                            "at n = 16384 would dominate the run"}}
 
 
 # ----------------------------------------------------------------------------- serving
@@ -501,6 +575,12 @@ def run_ours(args):
                "ms_per_step": el / K * 1e3,
                "api": "skew_ltlt_host (page-locked host A in, L, t, piv, log|Pf|, sign out)"}
 
+    precision = None
+    if not args.skip_precision:
+        precision = run_precision_leg(skew, inputs, torch, dev, A_host, nb, ms / K,
+                                      t.cpu().numpy(), piv.cpu().numpy(), steps=2, warmup=1,
+                                      n_qdq=args.qdq_n)
+
     batched = None
     if not args.skip_batched:
         batched = run_batched_leg(skew, inputs, torch, dev, steps=3, warmup=1,
@@ -532,6 +612,7 @@ def run_ours(args):
                          "algorithmic_flops_per_launch": sk["flops"] / max(sk["launches"], 1)},
             "kernels": kernels,
             "e2e": e2e,
+            "precision": precision,
             "batched": batched,
             "serving": serving,
             "cpu_baseline": cpu,

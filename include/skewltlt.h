@@ -195,6 +195,39 @@ int skew_pfaffian_noalloc(int64_t n, double *A, int64_t lda, double *logabs,
                           int32_t *sign, int32_t *info, int nb, void *stream);
 
 /*
+ * Precision of the trailing (skew rank-2k) update.  The panel, the pivot search,
+ * the Gauss-transform division, t and the log-Pfaffian stay FP64 in both.
+ *   SKEW_PRECISION_FP64       FP64 tensor-core (DMMA) products: rounding as in an FP64
+ *                             dot product, entry by entry.
+ *   SKEW_PRECISION_SPLIT_BF16 the FP64 operands cut into seven 8-bit digit slices per
+ *                             row (relative to the row's largest entry) and multiplied
+ *                             on bf16 tensor cores with exact FP32 sums, recombined
+ *                             exactly in 64-bit integers (Ozaki-type error-free
+ *                             splitting); the update differs from the exact one by
+ *                             about 2^-53 K (row max of U)(row max of V).  At most 32
+ *                             column pairs per update (panel width nb <= 64).
+ */
+#define SKEW_PRECISION_FP64 0
+#define SKEW_PRECISION_SPLIT_BF16 1
+
+/* skew_ltlt / skew_pfaffian with the trailing-update precision chosen by argument 10
+ * (`precision`; for SKEW_PRECISION_SPLIT_BF16, nb must be at most 64 and 0 picks
+ * min(default, 64)).  Other arguments as there; workspace (argument 11) of
+ * skew_workspace_bytes_ex bytes, or NULL. */
+int skew_ltlt_ex(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
+                 int32_t *piv, int32_t *info, int nb, int precision, void *workspace,
+                 size_t workspace_bytes, void *stream);
+int skew_pfaffian_ex(int64_t n, double *A, int64_t lda, double *logabs, int32_t *sign,
+                     double *t, int32_t *piv, int32_t *info, int nb, int precision,
+                     void *workspace, size_t workspace_bytes, void *stream);
+size_t skew_workspace_bytes_ex(int64_t n, int nb, int with_L, int precision);
+
+/* skew_rank2k with the precision of argument 11 (split: k <= 32). */
+int skew_rank2k_ex(int64_t m, int64_t k, double alpha, const double *X, int64_t ldx,
+                   const double *Y, int64_t ldy, double beta, double *C, int64_t ldc,
+                   int precision, void *stream);
+
+/*
  * skew_rank2k -- C := beta C + alpha (X Y^T - Y X^T) on the strictly lower
  * triangle of the m x m skew matrix C (operation skew_rank2k of the table of
  * BLAS-like operations in Section 4.2).  FP64 tensor-core (DMMA) tiles.

@@ -44,6 +44,10 @@ SIGNATURES = {
     "skew_tridiag_rankk": ([_i64, _i64, _dbl, _vp, _i64, _vp, _dbl, _vp, _i64, _vp], _i32),
     "skew_ltlt_host": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32], _i32),
     "skew_batched_workspace_bytes": ([_i32, _i32], _sz),
+    "skew_ltlt_ex": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i32, _i32, _vp, _sz, _vp], _i32),
+    "skew_pfaffian_ex": ([_i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _vp, _sz, _vp], _i32),
+    "skew_workspace_bytes_ex": ([_i64, _i32, _i32, _i32], _sz),
+    "skew_rank2k_ex": ([_i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _i32, _vp], _i32),
     "skew_ltlt_batched": ([_i32, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
     "skew_server_create": ([_sz, _i32, _i32, _vp], _i32),
     "skew_server_submit": ([_vp, _i64, _vp, _i64, _i32, _vp], _i32),
@@ -164,7 +168,12 @@ def trim_memory():
     _check("skew_trim_memory", lib().skew_trim_memory())
 
 
-def ltlt(A, nb: int = 0, stream=None, L=None, t=None, piv=None, info=None, workspace=None):
+PRECISION_FP64 = 0
+PRECISION_SPLIT_BF16 = 1
+
+
+def ltlt(A, nb: int = 0, stream=None, L=None, t=None, piv=None, info=None, workspace=None,
+         precision: int = PRECISION_FP64):
     """P A P^T = L T L^T of the column-major float64 CUDA tensor ``A`` (destroyed).
 
     Returns ``(L, t, piv, info)`` as CUDA tensors (L column-major n x n, t (n-1,),
@@ -179,13 +188,14 @@ def ltlt(A, nb: int = 0, stream=None, L=None, t=None, piv=None, info=None, works
     piv = torch.empty(n, dtype=torch.int32, device=A.device) if piv is None else piv
     info = torch.empty(1, dtype=torch.int32, device=A.device) if info is None else info
     ws, wsb = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
-    st = lib().skew_ltlt(n, _ptr(A), lda, _ptr(L), ldl, _ptr(t) if n > 1 else None,
-                         _ptr(piv), _ptr(info), nb, ws, wsb, _stream_handle(stream))
-    _check("skew_ltlt", st)
+    st = lib().skew_ltlt_ex(n, _ptr(A), lda, _ptr(L), ldl, _ptr(t) if n > 1 else None,
+                            _ptr(piv), _ptr(info), nb, precision, ws, wsb, _stream_handle(stream))
+    _check("skew_ltlt_ex", st)
     return L, t, piv, info
 
 
-def pfaffian(A, nb: int = 0, stream=None, t=None, piv=None, info=None, workspace=None):
+def pfaffian(A, nb: int = 0, stream=None, t=None, piv=None, info=None, workspace=None,
+             precision: int = PRECISION_FP64):
     """log|Pf(A)| and sign through the factorization (A destroyed).
 
     Returns ``(logabs, sign, t, piv, info)`` CUDA tensors (logabs float64 (1,),
@@ -201,10 +211,10 @@ def pfaffian(A, nb: int = 0, stream=None, t=None, piv=None, info=None, workspace
     piv = torch.empty(n, dtype=torch.int32, device=dev) if piv is None else piv
     info = torch.empty(1, dtype=torch.int32, device=dev) if info is None else info
     ws, wsb = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
-    st = lib().skew_pfaffian(n, _ptr(A), lda, _ptr(logabs), _ptr(sign),
-                             _ptr(t) if n > 1 else None, _ptr(piv) if n > 0 else None,
-                             _ptr(info), nb, ws, wsb, _stream_handle(stream))
-    _check("skew_pfaffian", st)
+    st = lib().skew_pfaffian_ex(n, _ptr(A), lda, _ptr(logabs), _ptr(sign),
+                                _ptr(t) if n > 1 else None, _ptr(piv) if n > 0 else None,
+                                _ptr(info), nb, precision, ws, wsb, _stream_handle(stream))
+    _check("skew_pfaffian_ex", st)
     return logabs, sign, t, piv, info
 
 
@@ -220,16 +230,16 @@ def pfaffian_from_factors(t, piv, n: int, stream=None):
     return logabs, sign
 
 
-def rank2k(alpha: float, X, Y, beta: float, C, stream=None):
+def rank2k(alpha: float, X, Y, beta: float, C, stream=None, precision: int = PRECISION_FP64):
     """C := beta C + alpha (X Y^T - Y X^T) on the strictly lower triangle (in place)."""
     m = C.shape[0]
     k = X.shape[1]
     ldx = _colmajor("X", X, m)
     ldy = _colmajor("Y", Y, m)
     ldc = _colmajor("C", C, m)
-    st = lib().skew_rank2k(m, k, float(alpha), _ptr(X), ldx, _ptr(Y), ldy, float(beta),
-                           _ptr(C), ldc, _stream_handle(stream))
-    _check("skew_rank2k", st)
+    st = lib().skew_rank2k_ex(m, k, float(alpha), _ptr(X), ldx, _ptr(Y), ldy, float(beta),
+                              _ptr(C), ldc, precision, _stream_handle(stream))
+    _check("skew_rank2k_ex", st)
     return C
 
 

@@ -208,7 +208,7 @@ int current_device_info(DeviceInfo *out) {
     return SKEW_OK;
 }
 
-WsLayout workspace_layout(int64_t n, int nb, bool with_L) {
+WsLayout workspace_layout(int64_t n, int nb, bool with_L, int precision) {
     WsLayout w;
     size_t off = 0;
     w.ctrl = off;
@@ -221,6 +221,8 @@ WsLayout workspace_layout(int64_t n, int nb, bool with_L) {
     off += align256(sizeof(int32_t) * (size_t)(n > 1 ? n : 1));
     w.lbuf = off;
     if (!with_L) off += align256(sizeof(double) * (size_t)(n > 1 ? n : 1) * (size_t)nb);
+    w.split = off;
+    if (precision == SKEW_PRECISION_SPLIT_BF16) off += split_scratch_bytes(n);
     w.total = off;
     return w;
 }
@@ -230,11 +232,12 @@ namespace {
 
 int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
            int32_t *piv, int32_t *info, double *logabs, int32_t *sign, int nb,
-           void *workspace, size_t workspace_bytes, cudaStream_t st, bool with_L) {
+           void *workspace, size_t workspace_bytes, cudaStream_t st, bool with_L,
+           int precision) {
     DeviceInfo di;
     SKEW_TRY_STATUS(current_device_info(&di));
     if (nb == 0) nb = skew_default_nb(n);
-    const WsLayout lay = workspace_layout(n, nb, with_L);
+    const WsLayout lay = workspace_layout(n, nb, with_L, precision);
     char *base = static_cast<char *>(workspace);
     bool own = false;
     if (base == nullptr) {
@@ -343,7 +346,10 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
                 sa.b = kend - k0;
                 ProfScope ps(kProfSkr2k, st, skr2k_flops(sa.m, sa.b / 2 + (sa.b & 1)),
                              skr2k_bytes(sa.m));
-                status = launch_skr2k(PairKind::Fused, sa, st);
+                if (precision == SKEW_PRECISION_SPLIT_BF16)
+                    status = launch_skr2k_split(PairKind::Fused, sa, base + lay.split, st);
+                else
+                    status = launch_skr2k(PairKind::Fused, sa, st);
             }
             k0 = kend;
         }
@@ -462,7 +468,7 @@ int skew_ltlt(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double 
         return SKEW_OK;
     }
     return factor(n, A, lda, L, ldl, t, piv, info, nullptr, nullptr, nb, workspace,
-                  workspace_bytes, st, true);
+                  workspace_bytes, st, true, SKEW_PRECISION_FP64);
 }
 
 int skew_pfaffian(int64_t n, double *A, int64_t lda, double *logabs, int32_t *sign,
@@ -484,7 +490,115 @@ int skew_pfaffian(int64_t n, double *A, int64_t lda, double *logabs, int32_t *si
         return SKEW_OK;
     }
     return factor(n, A, lda, nullptr, 0, t, piv, info, logabs, sign, nb, workspace,
-                  workspace_bytes, st, false);
+                  workspace_bytes, st, false, SKEW_PRECISION_FP64);
+}
+
+size_t skew_workspace_bytes_ex(int64_t n, int nb, int with_L, int precision) {
+    if (n < 0 || (precision != SKEW_PRECISION_FP64 && precision != SKEW_PRECISION_SPLIT_BF16))
+        return 0;
+    if (nb <= 0) nb = skew_default_nb(n);
+    if (nb > kMaxNb) nb = kMaxNb;
+    return workspace_layout(n, nb, with_L != 0, precision).total;
+}
+
+int skew_ltlt_ex(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
+                 int32_t *piv, int32_t *info, int nb, int precision, void *workspace,
+                 size_t workspace_bytes, void *stream) {
+    if (precision != SKEW_PRECISION_FP64 && precision != SKEW_PRECISION_SPLIT_BF16) return -10;
+    if (precision == SKEW_PRECISION_FP64)
+        return skew_ltlt(n, A, lda, L, ldl, t, piv, info, nb, workspace, workspace_bytes, stream);
+    if (n < 0 || n > kMaxOrder) return -1;
+    const int64_t ld_min = n > 1 ? n : 1;
+    if (A == nullptr && n > 0) return -2;
+    if (lda < ld_min) return -3;
+    if (L == nullptr && n > 0) return -4;
+    if (ldl < ld_min) return -5;
+    if (t == nullptr && n >= 2) return -6;
+    if (piv == nullptr && n >= 1) return -7;
+    if (nb < 0 || nb > 64) return -9;                  // split update: at most 32 pairs
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n == 0) {
+        if (info) SKEW_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
+        return SKEW_OK;
+    }
+    if (nb == 0 && skew_default_nb(n) > 64) nb = 64;
+    if (workspace != nullptr &&
+        workspace_bytes < workspace_layout(n, nb == 0 ? skew_default_nb(n) : nb, true, precision).total)
+        return -12;
+    return factor(n, A, lda, L, ldl, t, piv, info, nullptr, nullptr, nb, workspace,
+                  workspace_bytes, st, true, precision);
+}
+
+int skew_pfaffian_ex(int64_t n, double *A, int64_t lda, double *logabs, int32_t *sign,
+                     double *t, int32_t *piv, int32_t *info, int nb, int precision,
+                     void *workspace, size_t workspace_bytes, void *stream) {
+    if (precision != SKEW_PRECISION_FP64 && precision != SKEW_PRECISION_SPLIT_BF16) return -10;
+    if (precision == SKEW_PRECISION_FP64)
+        return skew_pfaffian(n, A, lda, logabs, sign, t, piv, info, nb, workspace,
+                             workspace_bytes, stream);
+    if (n < 0 || n > kMaxOrder) return -1;
+    const int64_t ld_min = n > 1 ? n : 1;
+    if (A == nullptr && n > 0) return -2;
+    if (lda < ld_min) return -3;
+    if (logabs == nullptr) return -4;
+    if (sign == nullptr) return -5;
+    if (nb < 0 || nb > 64) return -9;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n == 0) return skew_pfaffian(n, A, lda, logabs, sign, t, piv, info, nb, nullptr, 0, stream);
+    if (nb == 0 && skew_default_nb(n) > 64) nb = 64;
+    if (workspace != nullptr &&
+        workspace_bytes < workspace_layout(n, nb == 0 ? skew_default_nb(n) : nb, false, precision).total)
+        return -12;
+    return factor(n, A, lda, nullptr, 0, t, piv, info, logabs, sign, nb, workspace,
+                  workspace_bytes, st, false, precision);
+}
+
+int skew_rank2k_ex(int64_t m, int64_t k, double alpha, const double *X, int64_t ldx,
+                   const double *Y, int64_t ldy, double beta, double *C, int64_t ldc,
+                   int precision, void *stream) {
+    if (precision != SKEW_PRECISION_FP64 && precision != SKEW_PRECISION_SPLIT_BF16) return -11;
+    if (precision == SKEW_PRECISION_FP64)
+        return skew_rank2k(m, k, alpha, X, ldx, Y, ldy, beta, C, ldc, stream);
+    if (m < 0 || m > kMaxOrder) return -1;
+    if (k < 0 || k > 32) return -2;                    // split update: at most 32 pairs
+    const int64_t ld_min = m > 1 ? m : 1;
+    const bool need_ops = m > 1 && k > 0;
+    if (X == nullptr && need_ops) return -4;
+    if (ldx < ld_min) return -5;
+    if (Y == nullptr && need_ops) return -6;
+    if (ldy < ld_min) return -7;
+    if (C == nullptr && m > 1) return -9;
+    if (ldc < ld_min) return -10;
+    if (m <= 1) return SKEW_OK;
+    DeviceInfo di;
+    SKEW_TRY_STATUS(current_device_info(&di));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *scratch = nullptr;
+    SKEW_TRY_STATUS(pool_alloc(&scratch, split_scratch_bytes(m), st));
+    Skr2kArgs sa;
+    sa.m = m;
+    sa.C = C;
+    sa.ldc = ldc;
+    sa.alpha = alpha;
+    sa.beta = beta;
+    sa.P = X;
+    sa.ldp = ldx;
+    sa.Q = Y;
+    sa.ldq = ldy;
+    sa.tt = nullptr;
+    sa.x = nullptr;
+    sa.b = k;
+    int status;
+    {
+        ProfScope ps(kProfSkr2k, st, skr2k_flops(m, k), skr2k_bytes(m));
+        status = launch_skr2k_split(PairKind::Rank2k, sa, scratch, st);
+    }
+    cudaError_t e = cudaFreeAsync(scratch, st);
+    if (e != cudaSuccess && status == SKEW_OK) {
+        set_last_error(e);
+        status = SKEW_ERR_CUDA;
+    }
+    return status;
 }
 
 int skew_pfaffian_from_factors(int64_t n, const double *t, const int32_t *piv,

@@ -69,9 +69,9 @@ constexpr int64_t kMaxOrder = int64_t(1) << 22;   // keeps every tile count belo
 
 // Workspace layout (byte offsets), see workspace_layout().
 struct WsLayout {
-    size_t ctrl, partials, tbuf, pivbuf, lbuf, total;
+    size_t ctrl, partials, tbuf, pivbuf, lbuf, split, total;
 };
-WsLayout workspace_layout(int64_t n, int nb, bool with_L);
+WsLayout workspace_layout(int64_t n, int nb, bool with_L, int precision = 0);
 
 // ------------------------------------------------------------------ device helpers
 __device__ __forceinline__ uint64_t global_ns() {
@@ -200,6 +200,12 @@ struct Skr2kArgs {
     int64_t b;             // Rank2k: k; Tridiag/Fused: number of A columns
 };
 int launch_skr2k(PairKind kind, const Skr2kArgs &a, cudaStream_t stream);
+
+// Split-precision variant (skr2k_split.cu): at most 32 pairs; `scratch` holds
+// split_scratch_bytes(m) bytes (digit slices and row exponents).
+size_t split_z_bytes(int64_t m);
+size_t split_scratch_bytes(int64_t m);
+int launch_skr2k_split(PairKind kind, const Skr2kArgs &a, void *scratch, cudaStream_t stream);
 
 // Batched persistent factorization (batched.cu).
 size_t batched_workspace_bytes(int count, int max_n);

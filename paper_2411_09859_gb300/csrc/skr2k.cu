@@ -29,6 +29,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "pairs.cuh"
 
 namespace skew {
 namespace {
@@ -38,42 +39,6 @@ constexpr int PC = 16;            // pairs per staging round
 constexpr int KC = 2 * PC;        // K columns per staging round
 constexpr int LDS = KC + 4;       // padded smem row (doubles): conflict-free fragments
 constexpr int kThreads = 128;     // four warps
-
-template <PairKind KIND>
-struct PairSource {
-    const double *P;
-    int64_t ldp;
-    const double *Q;
-    int64_t ldq;
-    const double *tt;
-    const double *x;
-    int64_t b;
-
-    __device__ __forceinline__ int64_t npairs() const {
-        if (KIND == PairKind::Rank2k) return b;
-        if (KIND == PairKind::Tridiag) return b / 2;
-        return b / 2 + (b & 1);
-    }
-    // (a_p, w_p) at row i (0 <= i < m)
-    __device__ __forceinline__ void get(int64_t p, int64_t i, double &av, double &wv) const {
-        if (KIND == PairKind::Rank2k) {
-            av = P[i + p * ldp];
-            wv = Q[i + p * ldq];
-            return;
-        }
-        const int64_t j = 2 * p + 1;
-        if (j < b) {
-            av = P[i + j * ldp];
-            double w = -tt[j - 1] * P[i + (j - 1) * ldp];
-            if (j + 1 < b) w += tt[j] * P[i + (j + 1) * ldp];
-            if (KIND == PairKind::Fused && j == b - 1) w += x[i];
-            wv = w;
-        } else {                                    // Fused, b odd: (a_{b-1}, x)
-            av = P[i + (b - 1) * ldp];
-            wv = x[i];
-        }
-    }
-};
 
 __device__ __forceinline__ void dmma_8x8x4(double &c0, double &c1, double a, double b) {
     asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
