@@ -281,6 +281,9 @@ def run_precision_leg(skew, inputs, torch, dev, A_host, nb_fp64, fp64_ms, fp64_t
     for i in range(warmup + steps):
         work.copy_(pristine)
         torch.cuda.synchronize()
+        if i == warmup:
+            skew.profile_read()
+            skew.profile_enable(True)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -289,7 +292,13 @@ def run_precision_leg(skew, inputs, torch, dev, A_host, nb_fp64, fp64_ms, fp64_t
         torch.cuda.synchronize()
         if i >= warmup:
             times.append(e0.elapsed_time(e1))
+    prof = skew.profile_read()
+    skew.profile_enable(False)
     ms = statistics.median(times)
+    kernels = {k: {"ms_per_step": v["ms"] / steps, "share": v["ms"] / steps / ms}
+               for k, v in prof.items() if v["launches"]}
+    sk = prof["skr2k"]
+    split_tflops = (sk["flops"] / (sk["ms"] / 1e3) / 1e12) if sk["ms"] > 0 else None
     t_s, piv_s = t.cpu().numpy(), piv.cpu().numpy()
     la_f, sg_f = skew.pfaffian_from_factors(torch.from_numpy(fp64_t).to(dev),
                                             torch.from_numpy(fp64_piv).to(dev), n)
@@ -318,7 +327,8 @@ def run_precision_leg(skew, inputs, torch, dev, A_host, nb_fp64, fp64_ms, fp64_t
     flops = factorization_flops(n)
     return {"metric": "skew LTLt TFLOP/s (n^3/3) with the split-precision trailing update",
             "value": flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
-            "speedup_vs_fp64": fp64_ms / ms, "nb": nb,
+            "speedup_vs_fp64": fp64_ms / ms, "nb": nb, "kernels": kernels,
+            "update_fp64_equivalent_tflops": split_tflops,
             "vs_fp64_run": {"pivots_equal": first_diff is None, "first_pivot_difference": first_diff,
                             "log_abs_pf_fp64": la_f, "log_abs_pf_split": la_s,
                             "rel_diff": abs(la_s - la_f) / abs(la_f), "sign_equal": int(sg_f.item()) == int(sg_s.item()),
@@ -415,6 +425,24 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int):
                         "p50_ms": float(np.percentile(poi_lat, 50)),
                         "p99_ms": float(np.percentile(poi_lat, 99))},
             "server": "budget 64 GB, 4 streams, batched kernel for n <= 512"}
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max of `value` over the ranks of the default process group (the timing rule:
+    the slowest rank defines the whole-job time).  Identity for a single process."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, seconds_max: float, world: int) -> float:
+    """Units processed by all ranks divided by the slowest rank's time (replicas:
+    every rank processes the same number of units)."""
+    return world * units_per_rank / seconds_max
 
 
 def dist_setup(args):
@@ -524,17 +552,13 @@ def run_ours(args):
     skew.profile_enable(False)
     if world > 1:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        tm = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ms = float(tm.item())
+    ms = reduce_max(e0.elapsed_time(e1), world, dev)
     if int(info.item()) != 0:
         raise RuntimeError(f"timed factorization reported info={int(info.item())}")
     del copies
     torch.cuda.empty_cache()
 
-    value = world * K * factorization_flops(n) / (ms / 1e3) / 1e12
+    value = whole_job_rate(K * factorization_flops(n), ms / 1e3, world) / 1e12
     peak, peak_note = fp64_peak()
     sk = prof["skr2k"]
     achieved = sk["flops"] / (sk["ms"] / 1e3) / 1e12 if sk["ms"] > 0 else None
@@ -564,12 +588,8 @@ def run_ours(args):
             res = skew.ltlt_host(A_np, True, nb, L_out=L_np, t_out=t_np, piv_out=p_np)
             if res[5] != 0:
                 raise RuntimeError(f"host-buffer factorization reported info={res[5]}")
-        el = time.perf_counter() - t0
-        if world > 1:
-            tm = torch.tensor([el], dtype=torch.float64, device=dev)
-            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-            el = float(tm.item())
-        e2e = {"value": world * K * factorization_flops(n) / el / 1e12, "unit": UNIT,
+        el = reduce_max(time.perf_counter() - t0, world, dev)
+        e2e = {"value": whole_job_rate(K * factorization_flops(n), el, world) / 1e12, "unit": UNIT,
                "h2d_bytes_per_step": n * n * 8,
                "d2h_bytes_per_step": n * n * 8 + (n - 1) * 8 + n * 4 + 8 + 4 + 4,
                "ms_per_step": el / K * 1e3,

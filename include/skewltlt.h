@@ -101,6 +101,14 @@ typedef struct {
 int skew_profile_enable(int on);
 int skew_profile_read(skew_kernel_stat *stats /* SKEW_KIND_COUNT entries */);
 
+/* Self-test of the device-side bounded waits (failure detection without a fault):
+ * launches two CTAs into a grid barrier that waits for a third one, which never
+ * comes; after timeout_s seconds (0 < timeout_s <= 10) the wait gives up, records
+ * SKEW_ERR_TIMEOUT and the kernel returns normally.  Synchronous; *status receives
+ * the recorded status (SKEW_ERR_TIMEOUT when the mechanism works).  The device stays
+ * usable afterwards. */
+int skew_selftest_bounded_wait(double timeout_s, int32_t *status);
+
 /* Panel width used when `nb` is 0 for a matrix of order n. */
 int skew_default_nb(int64_t n);
 

@@ -441,6 +441,33 @@ int skew_profile_read(skew_kernel_stat *stats) {
     return status;
 }
 
+int skew_selftest_bounded_wait(double timeout_s, int32_t *status) {
+    if (!(timeout_s > 0.0 && timeout_s <= 10.0)) return -1;
+    if (status == nullptr) return -2;
+    DeviceInfo di;
+    SKEW_TRY_STATUS(current_device_info(&di));
+    cudaStream_t st;
+    SKEW_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    void *p = nullptr;
+    int rc = pool_alloc(&p, sizeof(Ctrl), st);
+    if (rc == SKEW_OK) {
+        Ctrl *ctrl = static_cast<Ctrl *>(p);
+        cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
+        if (e != cudaSuccess) { set_last_error(e); rc = SKEW_ERR_CUDA; }
+        if (rc == SKEW_OK)
+            rc = launch_selftest_wait(ctrl, 2, (uint64_t)(timeout_s * 1e9), st);
+        if (rc == SKEW_OK) {
+            e = cudaMemcpyAsync(status, &ctrl->err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) { set_last_error(e); rc = SKEW_ERR_CUDA; }
+        }
+        cudaFreeAsync(p, st);
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess && rc == SKEW_OK) { set_last_error(e); rc = SKEW_ERR_CUDA; }
+    cudaStreamDestroy(st);
+    return rc;
+}
+
 int skew_trim_memory(void) {
     int dev;
     SKEW_TRY(cudaGetDevice(&dev));

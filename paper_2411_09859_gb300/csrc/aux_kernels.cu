@@ -105,7 +105,19 @@ finish_kernel(int64_t n, const double *t, const int32_t *piv, const Ctrl *ctrl,
     }
 }
 
+__global__ void selftest_wait_kernel(Ctrl *ctrl, unsigned int expected, uint64_t timeout_ns) {
+    unsigned int gen = 0;
+    if (threadIdx.x == 0) gen = ld_acquire_u32(&ctrl->bar_gen);
+    grid_barrier(ctrl, expected, gen, timeout_ns);
+}
+
 }  // namespace
+
+int launch_selftest_wait(Ctrl *ctrl, int blocks, uint64_t timeout_ns, cudaStream_t stream) {
+    selftest_wait_kernel<<<blocks, 32, 0, stream>>>(ctrl, (unsigned int)blocks + 1u, timeout_ns);
+    note_launches(1);
+    return check_launch();
+}
 
 int launch_prologue(int64_t n, const double *A, int64_t lda, double *L, int64_t ldl,
                     int32_t *piv, Ctrl *ctrl, cudaStream_t stream) {

@@ -221,6 +221,349 @@ __device__ void factor_one(const skew_problem &P, double *logabs, int32_t *sign,
     __syncthreads();
 }
 
+// ------------------------------------------------------------------------------------
+// Blocked variant for n <= kBlkMaxN: the blocked right-looking algorithm of
+// Section 4.2 (Variant 1) with the pivoted left-looking panel of Section 5.2, inside
+// one CTA.  Panels of kBlkNb columns: each step forms v = X[k+1:, k] - Lp h from the
+// panel's L columns kept in shared memory (h = T L[k, :]^T), takes the pivot, exchanges
+// k+1 and r in place, and scales.  The trailing update is one skew rank-2k update
+// with the pairs (a_j, w_j), W = A S (Section 2.2 theorem), plus the pair of the last
+// Gauss transform, on FP64 DMMA (mma.sync.m8n8k4.f64): n^3/3 flops per matrix.
+// ------------------------------------------------------------------------------------
+constexpr int kBlkThreads = 256;
+constexpr int kBlkNb = 16;
+constexpr int kBlkMaxN = 512;
+
+__device__ __forceinline__ void dmma884(double &c0, double &c1, double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                 : "+d"(c0), "+d"(c1)
+                 : "d"(a), "d"(b));
+}
+
+struct BlkShared {
+    double h[kBlkNb + 1];
+    double t[kBlkNb + 1];
+    unsigned long long w_raw[kBlkThreads / 32];
+    int w_i[kBlkThreads / 32];
+    int w_bad[kBlkThreads / 32];
+    unsigned long long best_raw;
+    int best_i;
+    int bad;
+};
+
+__device__ Cand blk_cand(Cand x, bool bad, BlkShared &sh, bool &any_bad) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    x = warp_cand(x);
+    const int wb = __any_sync(0xffffffffu, bad);
+    if (lane == 0) { sh.w_raw[w] = x.raw; sh.w_i[w] = x.i; sh.w_bad[w] = wb; }
+    __syncthreads();
+    if (w == 0) {
+        Cand y;
+        y.raw = 0ull;
+        y.i = INT_MAX;
+        int b = 0;
+        if (lane < kBlkThreads / 32) { y.raw = sh.w_raw[lane]; y.i = sh.w_i[lane]; b = sh.w_bad[lane]; }
+        y = warp_cand(y);
+        b = __any_sync(0xffffffffu, b);
+        if (lane == 0) { sh.best_raw = y.raw; sh.best_i = y.i; sh.bad = b; }
+    }
+    __syncthreads();
+    Cand r;
+    r.raw = sh.best_raw;
+    r.i = sh.best_i;
+    any_bad = sh.bad != 0;
+    return r;
+}
+
+// smem: Lp[kBlkNb][nmax] (panel L columns), Ws[kBlkNb/2+1][nmax] (odd W columns),
+// sv[nmax] (v of the current step)
+__device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_t *sign,
+                                   int32_t *info, double *smem, int nmax, BlkShared &sh,
+                                   BatchShared &fin) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+    const int n = (int)P.n;
+    double *X = P.A;
+    const int64_t ldx = P.lda;
+    double *L = P.L;
+    const int64_t ldl = P.ldl;
+    double *t = P.t;
+    int32_t *piv = P.piv;
+    double *Lp = smem;                                  // Lp[q * nmax + i]
+    double *Ws = smem + (size_t)kBlkNb * nmax;          // Ws[pp * nmax + i]
+    double *sv = Ws + (size_t)(kBlkNb / 2 + 1) * nmax;
+
+    for (int i = tid; i < n; i += nthr) piv[i] = i;
+    if (L != nullptr)
+        for (int j = warp; j < n; j += nwarps)
+            for (int i = lane; i < n; i += 32) L[i + j * ldl] = (i == j) ? 1.0 : 0.0;
+    bool nonfinite = false;
+    __syncthreads();
+
+    // h for step k of the panel starting at k0 (L[k, k] = 1): into sh.h[q - k0 - 1]
+    auto form_h = [&](int k, int k0) {
+        for (int q = k0 + 1 + tid; q <= k; q += nthr) {
+            double hq = 0.0;
+            if (q - 1 >= k0 + 1) hq = sh.t[q - 1 - k0] * Lp[(q - 2 - k0) * nmax + k];
+            if (q + 1 <= k) {
+                const double lq1 = (q + 1 == k) ? 1.0 : Lp[(q - k0) * nmax + k];
+                hq -= sh.t[q - k0] * lq1;
+            }
+            sh.h[q - k0 - 1] = hq;
+        }
+        __syncthreads();
+    };
+
+    for (int k0 = 0; k0 + 1 < n;) {
+        const int kend = (k0 + kBlkNb < n - 1) ? k0 + kBlkNb : n - 1;
+        const int b = kend - k0;
+        // ---------------- the panel
+        for (int k = k0; k < kend; ++k) {
+            const int nq = k - k0, p = k + 1;
+            form_h(k, k0);
+            const double *colk = X + (int64_t)k * ldx;
+            Cand c;
+            c.raw = 0ull;
+            c.i = INT_MAX;
+            bool bad = false;
+            for (int i = p + tid; i < n; i += nthr) {
+                double v = colk[i];
+                for (int q = 0; q < nq; ++q) v -= Lp[q * nmax + i] * sh.h[q];
+                sv[i] = v;
+                const unsigned long long raw = (unsigned long long)__double_as_longlong(v);
+                if ((raw & kExp) == kExp) { bad = true; continue; }
+                if (cand_better(raw, i, c.raw, c.i)) { c.raw = raw; c.i = i; }
+            }
+            bool any_bad;
+            const Cand best = blk_cand(c, bad, sh, any_bad);
+            nonfinite |= any_bad;
+            const int r = (best.i == INT_MAX) ? p : best.i;
+            if (r != p) {
+                double *colp = X + (int64_t)p * ldx;
+                for (int i = p + 1 + tid; i < n; i += nthr) {
+                    if (i < r) {
+                        double *xri = X + (int64_t)i * ldx + r;
+                        const double tmp = colp[i];
+                        colp[i] = -*xri;
+                        *xri = -tmp;
+                    } else if (i == r) {
+                        colp[i] = -colp[i];
+                    } else {
+                        double *colr = X + (int64_t)r * ldx;
+                        const double tmp = colp[i];
+                        colp[i] = colr[i];
+                        colr[i] = tmp;
+                    }
+                }
+                for (int q = tid; q < nq; q += nthr) {
+                    const double tmp = Lp[q * nmax + p];
+                    Lp[q * nmax + p] = Lp[q * nmax + r];
+                    Lp[q * nmax + r] = tmp;
+                }
+                if (tid == 0) {
+                    const double tmp = sv[p];
+                    sv[p] = sv[r];
+                    sv[r] = tmp;
+                }
+            }
+            __syncthreads();
+            const double tau = sv[p];
+            if (tid == 0) {
+                sh.t[nq] = tau;
+                t[k] = tau;
+                piv[p] = r;
+            }
+            double *lnew = Lp + (size_t)nq * nmax;             // panel column k+1
+            for (int i = p + tid; i < n; i += nthr)
+                lnew[i] = (i == p) ? 1.0 : ((tau != 0.0) ? sv[i] / tau : 0.0);
+            __syncthreads();
+        }
+        const int s = kend;
+        if (s < n - 1) {
+            // ---------------- the updated column x = X[s+1:, s] (left-looking, k = s)
+            form_h(s, k0);
+            double *cols = X + (int64_t)s * ldx;
+            for (int i = s + 1 + tid; i < n; i += nthr) {
+                double v = cols[i];
+                for (int q = 0; q < b; ++q) v -= Lp[q * nmax + i] * sh.h[q];
+                cols[i] = v;
+            }
+            __syncthreads();
+            // ---------------- odd W columns (W = A S), the last pair merged with x
+            const int npairs = b / 2 + (b & 1);
+            for (int i = s + 1 + tid; i < n; i += nthr) {
+                for (int pp = 0; pp < npairs; ++pp) {
+                    const int j = 2 * pp + 1;
+                    double w;
+                    if (j < b) {
+                        w = -sh.t[j] * Lp[(j - 1) * nmax + i];             // t_p[j-1] = t[k0+j]
+                        if (j + 1 < b) w += sh.t[j + 1] * Lp[(j + 1) * nmax + i];
+                        if (j == b - 1) w += cols[i];
+                    } else {
+                        w = cols[i];                                      // b odd: (a_{b-1}, x)
+                    }
+                    Ws[(size_t)pp * nmax + i] = w;
+                }
+            }
+            __syncthreads();
+            // ---------------- C = X[s+1:, s+1:] += sum_p (a_p w_p^T - w_p a_p^T), DMMA
+            const int m = n - s - 1;
+            const int K = 2 * npairs;                  // U = [a | -w], V = [w | a]
+            const int K4 = (K + 3) / 4 * 4;
+            const int nt = (m + 31) / 32;
+            const int ntiles = nt * (nt + 1) / 2;
+            const int g = lane >> 2, tg = lane & 3;
+            auto acol = [&](int pp) { return (2 * pp + 1 < b) ? 2 * pp + 1 : b - 1; };
+            for (int tile = warp; tile < ntiles; tile += nwarps) {
+                int bi = 0;
+                while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
+                const int bj = tile - bi * (bi + 1) / 2;
+                double acc[4][4][2];
+#pragma unroll
+                for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+                    for (int ni = 0; ni < 4; ++ni) acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
+                for (int kb = 0; kb < K4; kb += 4) {
+                    const int kc = kb + tg;
+                    double af[4], bf[4];
+#pragma unroll
+                    for (int mi = 0; mi < 4; ++mi) {
+                        const int li = bi * 32 + mi * 8 + g;          // local row in C
+                        const int i = s + 1 + li;
+                        double u = 0.0;
+                        if (li < m && kc < K)
+                            u = kc < npairs ? Lp[acol(kc) * nmax + i] : -Ws[(size_t)(kc - npairs) * nmax + i];
+                        af[mi] = u;
+                    }
+#pragma unroll
+                    for (int ni = 0; ni < 4; ++ni) {
+                        const int lj = bj * 32 + ni * 8 + g;
+                        const int j = s + 1 + lj;
+                        double v = 0.0;
+                        if (lj < m && kc < K)
+                            v = kc < npairs ? Ws[(size_t)kc * nmax + j] : Lp[acol(kc - npairs) * nmax + j];
+                        bf[ni] = v;
+                    }
+#pragma unroll
+                    for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+                        for (int ni = 0; ni < 4; ++ni)
+                            dmma884(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
+                }
+#pragma unroll
+                for (int mi = 0; mi < 4; ++mi) {
+                    const int li = bi * 32 + mi * 8 + g;
+#pragma unroll
+                    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+                        for (int cc = 0; cc < 2; ++cc) {
+                            const int lj = bj * 32 + ni * 8 + 2 * tg + cc;
+                            if (li < m && lj < m && li > lj) {
+                                double *dst = X + (int64_t)(s + 1 + lj) * ldx + (s + 1 + li);
+                                *dst = *dst + acc[mi][ni][cc];
+                            }
+                        }
+                }
+            }
+        }
+        // ---------------- L: the panel's columns, and its exchanges on earlier columns
+        if (L != nullptr) {
+            for (int q = warp; q < b; q += nwarps) {
+                const int col = k0 + 1 + q;
+                for (int i = col + lane; i < n; i += 32) L[i + (int64_t)col * ldl] = Lp[(size_t)q * nmax + i];
+            }
+            for (int c2 = 1 + tid; c2 <= k0; c2 += nthr) {
+                double *lc = L + (int64_t)c2 * ldl;
+                for (int k = k0; k < kend; ++k) {
+                    const int r = piv[k + 1], p = k + 1;
+                    if (r != p) {
+                        const double tmp = lc[p];
+                        lc[p] = lc[r];
+                        lc[r] = tmp;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        k0 = kend;
+    }
+
+    // ---- Pf = det(P) prod_i (-t[2i]) (Section 1), fixed reduction order
+    double sum = 0.0;
+    int par = 0, zero = 0;
+    const int half = n / 2;
+    if ((n & 1) == 0)
+        for (int j = tid; j < half; j += nthr) {
+            const double v = -t[2 * j];
+            if (v == 0.0) zero = 1;
+            else {
+                if (v < 0.0) par ^= 1;
+                sum += log(fabs(v));
+            }
+        }
+    for (int i = tid; i < n; i += nthr)
+        if (piv[i] != i) par ^= 1;
+    int first_zero = INT_MAX;
+    for (int j = tid; j + 1 < n; j += nthr)
+        if (t[j] == 0.0 && j < first_zero) first_zero = j;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        sum += __shfl_down_sync(0xffffffffu, sum, off);
+        par ^= __shfl_down_sync(0xffffffffu, par, off);
+        zero |= __shfl_down_sync(0xffffffffu, zero, off);
+        first_zero = min(first_zero, __shfl_down_sync(0xffffffffu, first_zero, off));
+    }
+    if (lane == 0) {
+        fin.w_sum[warp] = sum;
+        fin.w_par[warp] = par;
+        fin.w_zero[warp] = zero;
+        fin.w_i[warp] = first_zero;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double sm = 0.0;
+        int pr = 0, z = 0, fz = INT_MAX;
+        for (int w = 0; w < nwarps; ++w) {
+            sm += fin.w_sum[w];
+            pr ^= fin.w_par[w];
+            z |= fin.w_zero[w];
+            fz = min(fz, fin.w_i[w]);
+        }
+        const bool pf_zero = (n & 1) || z;
+        if (logabs) *logabs = pf_zero ? -INFINITY : sm;
+        if (sign) *sign = pf_zero ? 0 : (pr ? -1 : 1);
+        if (info) *info = nonfinite ? SKEW_ERR_NONFINITE : (fz == INT_MAX ? 0 : fz + 1);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBlkThreads, 2)
+batched_blocked_kernel(int count, const skew_problem *problems, const int32_t *order,
+                       unsigned int *counter, double *logabs, int32_t *sign, int32_t *info,
+                       int max_n) {
+    extern __shared__ double s_blk[];
+    __shared__ BlkShared sh;
+    __shared__ BatchShared fin;
+    for (;;) {
+        if (threadIdx.x == 0) fin.item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int item = fin.item;
+        __syncthreads();
+        if (item >= count) return;
+        const int b = order[item];
+        const skew_problem P = problems[b];
+        const int n = (int)P.n;
+        if (n < 0 || n > max_n || (n > 0 && P.A == nullptr) || P.lda < (n > 1 ? n : 1) ||
+            (P.L != nullptr && P.ldl < (n > 1 ? n : 1)) || (n > 1 && P.t == nullptr) ||
+            (n > 0 && P.piv == nullptr)) {
+            if (threadIdx.x == 0 && info) info[b] = -2;
+            continue;
+        }
+        factor_one_blocked(P, logabs ? logabs + b : nullptr, sign ? sign + b : nullptr,
+                           info ? info + b : nullptr, s_blk, max_n > 1 ? max_n : 1, sh, fin);
+    }
+}
+
 // Persistent: each CTA takes the next matrix of the size-ordered queue.
 __global__ void __launch_bounds__(kBatchThreads)
 batched_kernel(int count, const skew_problem *problems, const int32_t *order,
@@ -296,6 +639,31 @@ int launch_batched(int count, const skew_problem *problems, double *logabs, int3
     order_kernel<<<1, 1024, 0, stream>>>(count, problems, max_n, order, counter, hist);
     note_launches(1);
     SKEW_TRY_STATUS(check_launch());
+    if (max_n <= kBlkMaxN) {
+        // blocked variant: Lp, Ws and sv in shared memory
+        const size_t nm = (size_t)(max_n > 1 ? max_n : 1);
+        const size_t bsmem = sizeof(double) * nm * (kBlkNb + (kBlkNb / 2 + 1) + 1);
+        cudaError_t e = cudaFuncSetAttribute((const void *)batched_blocked_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bsmem);
+        if (e != cudaSuccess) {
+            set_last_error(e);
+            return SKEW_ERR_CUDA;
+        }
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_blocked_kernel,
+                                                          kBlkThreads, bsmem);
+        if (e != cudaSuccess || per_sm < 1) {
+            if (e != cudaSuccess) set_last_error(e);
+            return SKEW_ERR_CUDA;
+        }
+        int grid = sms * per_sm;
+        if (grid > count) grid = count;
+        batched_blocked_kernel<<<grid, kBlkThreads, bsmem, stream>>>(
+            count, problems, order, counter, logabs, sign, info, max_n);
+        note_launches(1);
+        return check_launch();
+    }
     const size_t smem = 2 * sizeof(double) * (size_t)(max_n > 1 ? max_n : 1);
     static_assert(kBatchThreads == 512, "launch shape");
     cudaError_t e = cudaFuncSetAttribute((const void *)batched_kernel,

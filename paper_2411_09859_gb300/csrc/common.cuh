@@ -117,7 +117,8 @@ __device__ __forceinline__ void raise_error(Ctrl *c, int status) {
 constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;   // 2 s
 
 __device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned int nblocks,
-                                             unsigned int &gen) {
+                                             unsigned int &gen,
+                                             uint64_t timeout_ns = kBarrierTimeoutNs) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -137,7 +138,7 @@ __device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned int nblocks,
                 if ((++polls & 255u) == 0u) {
                     uint64_t now = global_ns();
                     if (t0 == 0) t0 = now;
-                    else if (now - t0 > kBarrierTimeoutNs) {
+                    else if (now - t0 > timeout_ns) {
                         raise_error(c, SKEW_ERR_TIMEOUT);
                         ok = 0;
                         break;
@@ -211,6 +212,10 @@ int launch_skr2k_split(PairKind kind, const Skr2kArgs &a, void *scratch, cudaStr
 size_t batched_workspace_bytes(int count, int max_n);
 int launch_batched(int count, const skew_problem *problems, double *logabs, int32_t *sign,
                    int32_t *info, int max_n, void *ws, cudaStream_t stream, int sms);
+
+// Self-test of the bounded waits: `blocks` CTAs enter a grid barrier that expects one
+// more CTA than launched, so it can only end by its time limit.
+int launch_selftest_wait(Ctrl *ctrl, int blocks, uint64_t timeout_ns, cudaStream_t stream);
 
 // log|Pf|, sign (either may be null), and the final info word (may be null).
 int launch_finish(int64_t n, const double *t, const int32_t *piv, const Ctrl *ctrl,

@@ -114,10 +114,20 @@ skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
         __syncthreads();
     }
 
-    // ---- epilogue: strictly lower entries inside the block
+    // ---- epilogue: strictly lower entries inside the block.  All C loads of a row
+    // block are issued before its stores, so their latencies overlap.
 #pragma unroll
     for (int mi = 0; mi < 4; ++mi) {
         const int64_t gi = I0 + wm * 32 + mi * 8 + g;
+        double cv[4][2];
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int64_t gj = J0 + wn * 32 + ni * 8 + 2 * tg + c;
+                const bool in = gi < m && gj < m && gi > gj && beta != 0.0;
+                cv[ni][c] = in ? C[gi + gj * ldc] : 0.0;
+            }
 #pragma unroll
         for (int ni = 0; ni < 4; ++ni) {
 #pragma unroll
@@ -126,7 +136,7 @@ skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
                 if (gi < m && gj < m && gi > gj) {
                     double *dst = C + gi + gj * ldc;
                     const double upd = alpha * acc[mi][ni][c];
-                    *dst = (beta == 0.0) ? upd : ((beta == 1.0) ? *dst + upd : beta * *dst + upd);
+                    *dst = (beta == 0.0) ? upd : ((beta == 1.0) ? cv[ni][c] + upd : beta * cv[ni][c] + upd);
                 }
             }
         }

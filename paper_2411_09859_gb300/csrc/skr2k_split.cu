@@ -201,26 +201,33 @@ split_update_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta
 
     const int nchunks = KP / kChunk;
     for (int ch = 0; ch < nchunks; ++ch) {
-        // U columns [ch*32, ch*32+32) of [a | -w]; V columns are those of [w | a]
+        // U columns [ch*32, ch*32+32) of [a | -w] and the same columns of V = [w | a].
+        // The digits are copied as stored (+a, +w) with cp.async, all copies of a
+        // thread in flight at once (rows past m are zero-filled); a chunk of the w-part
+        // of U enters the accumulator with a minus sign instead.
         const int ucol = ch * kChunk;
-        const bool uneg = ucol >= P32;                        // in the w-part: negate
+        const bool uneg = ucol >= P32;                        // U holds -w here
         const int vcol = uneg ? ucol - P32 : ucol + P32;      // the other half
         for (int it = tid; it < kSlices * kTile * (kChunk / 8); it += kThreads) {
             const int seg = it % (kChunk / 8);
             const int r = (it / (kChunk / 8)) % kTile;
             const int s = it / ((kChunk / 8) * kTile);
-            uint4 u = make_uint4(0, 0, 0, 0), v = make_uint4(0, 0, 0, 0);
-            if (I0 + r < m) {
-                u = *reinterpret_cast<const uint4 *>(Z + s * slice_stride + (size_t)(I0 + r) * KP +
-                                                     ucol + seg * 8);
-                if (uneg) { u.x ^= 0x80008000u; u.y ^= 0x80008000u; u.z ^= 0x80008000u; u.w ^= 0x80008000u; }
-            }
-            if (J0 + r < m)
-                v = *reinterpret_cast<const uint4 *>(Z + s * slice_stride + (size_t)(J0 + r) * KP +
-                                                     vcol + seg * 8);
-            *reinterpret_cast<uint4 *>(&Us[s][r][seg * 8]) = u;
-            *reinterpret_cast<uint4 *>(&Vs[s][r][seg * 8]) = v;
+            const bool iu = I0 + r < m, jv = J0 + r < m;
+            const unsigned short *su =
+                iu ? Z + s * slice_stride + (size_t)(I0 + r) * KP + ucol + seg * 8 : Z;
+            const unsigned short *sv =
+                jv ? Z + s * slice_stride + (size_t)(J0 + r) * KP + vcol + seg * 8 : Z;
+            const unsigned int du = (unsigned int)__cvta_generic_to_shared(&Us[s][r][seg * 8]);
+            const unsigned int dv = (unsigned int)__cvta_generic_to_shared(&Vs[s][r][seg * 8]);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(du), "l"(su),
+                         "r"(iu ? 16 : 0)
+                         : "memory");
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dv), "l"(sv),
+                         "r"(jv ? 16 : 0)
+                         : "memory");
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
 #pragma unroll 1
         for (int d = 2; d <= kSlices + 1; ++d) {
@@ -268,34 +275,58 @@ split_update_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta
                 for (int ni = 0; ni < 4; ++ni)
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        const long long q = (long long)__float2int_rn(f[mi][ni][c]);
-                        acc[mi][ni][c] += shl >= 0 ? (q << shl) : (q >> (-shl));
+                        long long q = (long long)__float2int_rn(f[mi][ni][c]);
+                        q = shl >= 0 ? (q << shl) : (q >> (-shl));
+                        acc[mi][ni][c] += uneg ? -q : q;
                     }
         }
         __syncthreads();
     }
 
-    // epilogue: C[i,j] = beta C[i,j] + alpha 2^(E_i+E_j+2-56) acc, strictly lower part
+    // epilogue: C[i,j] = beta C[i,j] + alpha 2^(E_i+E_j+2-56) acc, strictly lower part.
+    // All loads of a row block (row exponents, C entries) are issued before any
+    // store, so their latencies overlap instead of adding up.
+    int Ej[4][2];
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int64_t gj = J0 + wn * 32 + ni * 8 + 2 * tg + c;
+            Ej[ni][c] = gj < m ? __ldg(rowexp + gj) : 0;
+        }
 #pragma unroll
     for (int mi = 0; mi < 2; ++mi) {
+        int Ei[2];
+        double cv[2][4][2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int64_t gi = I0 + wm * 32 + mi * 16 + g + 8 * h;
-            if (gi >= m) continue;
-            const int Ei = rowexp[gi];
+            Ei[h] = gi < m ? __ldg(rowexp + gi) : 0;
 #pragma unroll
-            for (int ni = 0; ni < 4; ++ni) {
+            for (int ni = 0; ni < 4; ++ni)
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     const int64_t gj = J0 + wn * 32 + ni * 8 + 2 * tg + c;
-                    if (gj >= m || gi <= gj) continue;
-                    const double upd = scaled_to_double(acc[mi][ni][2 * h + c], Ei + rowexp[gj] + 2 - 56);
-                    double *dst = C + gi + gj * ldc;
-                    if (beta == 1.0 && alpha == 1.0) *dst = *dst + upd;
-                    else if (beta == 0.0) *dst = alpha * upd;
-                    else *dst = beta * *dst + alpha * upd;
+                    const bool in = gi < m && gj < m && gi > gj && beta != 0.0;
+                    cv[h][ni][c] = in ? C[gi + gj * ldc] : 0.0;
                 }
-            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t gi = I0 + wm * 32 + mi * 16 + g + 8 * h;
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int64_t gj = J0 + wn * 32 + ni * 8 + 2 * tg + c;
+                    if (gi >= m || gj >= m || gi <= gj) continue;
+                    const double upd =
+                        scaled_to_double(acc[mi][ni][2 * h + c], Ei[h] + Ej[ni][c] + 2 - 56);
+                    double *dst = C + gi + gj * ldc;
+                    if (beta == 1.0 && alpha == 1.0) *dst = cv[h][ni][c] + upd;
+                    else if (beta == 0.0) *dst = alpha * upd;
+                    else *dst = beta * cv[h][ni][c] + alpha * upd;
+                }
         }
     }
 }

@@ -115,3 +115,23 @@ def test_rejects_bad_arguments():
     assert st == -2
     st = skew.lib().skew_ltlt_batched(0, None, None, None, None, 99999, None, 0, None)
     assert st == -6
+
+
+@pytest.mark.parametrize("want_L", [False, True])
+def test_blocked_kernel_orders_against_oracle(want_L):
+    """Batches with every order <= 512 take the blocked (panel + DMMA) kernel."""
+    sizes = [0, 1, 2, 3, 5, 16, 17, 18, 31, 32, 33, 47, 64, 100, 129, 255, 256, 300, 511, 512]
+    mats = [inputs.skew_gaussian(n, 9000 + n) for n in sizes]
+    la, sg, info, ts, pivs, Ls = run_batch(mats, want_L)
+    for b, A in enumerate(mats):
+        check_against_oracle(A, la[b], sg[b], info[b], ts[b], pivs[b], Ls[b])
+
+
+def test_blocked_kernel_zero_pivots_and_ties():
+    D = inputs.block_diag_skew(np.arange(1.0, 21.0))          # n = 40, zero columns
+    rng = np.random.default_rng(3)
+    Mi = np.triu(rng.integers(-2, 3, size=(70, 70)).astype(float), 1)
+    I = np.asfortranarray(Mi - Mi.T)                           # many ties
+    la, sg, info, ts, pivs, Ls = run_batch([D, I], True)
+    check_against_oracle(D, la[0], sg[0], info[0], ts[0], pivs[0], Ls[0])
+    check_against_oracle(I, la[1], sg[1], info[1], ts[1], pivs[1], Ls[1])
