@@ -291,11 +291,13 @@ BATCH_MAX_N = 8192
 
 
 def problem_table(As, Ls, ts, pivs, device):
-    """Device array of skew_problem descriptors (n, A, lda, L, ldl, t, piv)."""
+    """Device array of skew_problem descriptors (n, A, lda, L, ldl, t, piv).  Checks
+    that every A is a column-major float64 CUDA tensor."""
     import torch
     rows = []
     for A, L, t, piv in zip(As, Ls, ts, pivs):
         n = A.shape[0]
+        _colmajor("A", A, n)
         lda = max(A.stride(1) if n > 1 else 1, 1)
         ldl = 0 if L is None else max(L.stride(1) if n > 1 else 1, 1)
         rows.append([n, A.data_ptr() if n > 0 else 0, lda,
@@ -310,7 +312,9 @@ def ltlt_batched(As, want_L: bool = False, stream=None, max_n: int | None = None
     """Factor every column-major float64 CUDA tensor of the list ``As`` (destroyed) in
     one batched launch.  Returns ``(logabs, sign, info, ts, pivs, Ls)``: per-problem
     CUDA tensors (logabs float64 (count,), sign/info int32 (count,)) and lists of the
-    factors (``Ls`` entries are None unless ``want_L``)."""
+    factors (``Ls`` entries are None unless ``want_L``).  A ``table`` from
+    :func:`problem_table` (built, and checked, once for the same tensors) skips the
+    per-tensor work on the host."""
     import torch
     count = len(As)
     dev = As[0].device if count else torch.device("cuda")
@@ -320,8 +324,6 @@ def ltlt_batched(As, want_L: bool = False, stream=None, max_n: int | None = None
         Ls = [fortran_empty(A.shape[0], A.shape[0], dev) if want_L else None for A in As]
     else:
         ts, pivs, Ls = outs
-    for A in As:
-        _colmajor("A", A, A.shape[0])
     if table is None:
         table = problem_table(As, Ls, ts, pivs, dev)
     logabs = torch.empty(count, dtype=torch.float64, device=dev)

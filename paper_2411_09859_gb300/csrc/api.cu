@@ -347,7 +347,7 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
                 ProfScope ps(kProfSkr2k, st, skr2k_flops(sa.m, sa.b / 2 + (sa.b & 1)),
                              skr2k_bytes(sa.m));
                 if (precision == SKEW_PRECISION_SPLIT_BF16)
-                    status = launch_skr2k_split(PairKind::Fused, sa, base + lay.split, st);
+                    status = launch_skr2k_split(PairKind::Fused, sa, base + lay.split, &ctrl->err, di.sms, st);
                 else
                     status = launch_skr2k(PairKind::Fused, sa, st);
             }
@@ -618,7 +618,7 @@ int skew_rank2k_ex(int64_t m, int64_t k, double alpha, const double *X, int64_t 
     int status;
     {
         ProfScope ps(kProfSkr2k, st, skr2k_flops(m, k), skr2k_bytes(m));
-        status = launch_skr2k_split(PairKind::Rank2k, sa, scratch, st);
+        status = launch_skr2k_split(PairKind::Rank2k, sa, scratch, nullptr, di.sms, st);
     }
     cudaError_t e = cudaFreeAsync(scratch, st);
     if (e != cudaSuccess && status == SKEW_OK) {

@@ -203,10 +203,11 @@ struct Skr2kArgs {
 int launch_skr2k(PairKind kind, const Skr2kArgs &a, cudaStream_t stream);
 
 // Split-precision variant (skr2k_split.cu): at most 32 pairs; `scratch` holds
-// split_scratch_bytes(m) bytes (digit slices and row exponents).
-size_t split_z_bytes(int64_t m);
+// split_scratch_bytes(m) bytes (digit slices and row exponents); a timed-out wait is
+// recorded in *err (may be null); `sms` = multiprocessors of the device.
 size_t split_scratch_bytes(int64_t m);
-int launch_skr2k_split(PairKind kind, const Skr2kArgs &a, void *scratch, cudaStream_t stream);
+int launch_skr2k_split(PairKind kind, const Skr2kArgs &a, void *scratch, int *err, int sms,
+                       cudaStream_t stream);
 
 // Batched persistent factorization (batched.cu).
 size_t batched_workspace_bytes(int count, int max_n);

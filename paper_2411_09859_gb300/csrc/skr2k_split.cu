@@ -1,43 +1,82 @@
-// skr2k_split.cu -- the skew rank-2k update C += U V^T (strictly lower part) with
-// FP64 operands split into 8-bit digit slices multiplied on bf16 tensor cores
-// (mma.sync.m16n8k16, FP32 accumulation), recombined exactly in 64-bit integers.
+// skr2k_split.cu -- the skew rank-2k update C += U V^T (strictly lower part) with the
+// FP64 operands split into 8-bit digit slices multiplied on the fifth-generation tensor
+// cores (tcgen05.mma kind::f16, bf16 inputs, FP32 accumulators in tensor memory), the
+// slices loaded by TMA, and the products recombined exactly in 64-bit integers.
 //
 // This is the error-free splitting of Ozaki, Ogita, Oishi and Rump (2012), "Error-
 // free transformations of matrix multiplication by using fast routines of matrix
-// multiplication and its applications", in fixed-point form:
+// multiplication and its applications", in fixed-point form with balanced digits:
 //
 //   - every row i of the pair columns (a_p, w_p) gets the exponent E_i of its
-//     largest entry; each entry x becomes the 56-bit integer X = trunc(|x| 2^(55-E_i))
-//     (|x| < 2^(E_i+1)) with the sign of x, cut into seven 8-bit digits
-//     x ~ sign * sum_{s=1..7} d_s 2^(E_i+1-8s), 0 <= d_s <= 255 (exact in bf16);
-//   - U = [a | -w] and V = [w | a] share the digits of the row (negation flips a
-//     sign bit, V swaps the halves);
-//   - (U V^T)[i,j] ~ 2^(E_i+E_j+2) sum_{d=2..8} 2^(-8d) P_d[i,j] with
-//     P_d = sum_{s+t=d} U_s V_t^T.  Over a K-chunk of 32 columns every P_d is an
-//     integer below 7 * 32 * 255^2 < 2^24, so its FP32 tensor-core sum is exact;
-//     chunk results are added as integers into a 64-bit fixed-point accumulator
-//     (weight 2^(56-8d)), and one conversion to FP64 plus one FP64 add per entry
-//     finishes the update.
+//     largest entry; each entry x becomes the signed integer X = trunc(x 2^(54-E_i)),
+//     |X| < 2^55 (exact for entries within a factor 4 of the row maximum), written
+//     with seven base-256 digits X = sum_{s=1..7} d_s 2^(8(7-s)): d_7 .. d_2 balanced
+//     in [-128, 127], d_1 what remains (|d_1| <= 128); every digit is exact in bf16;
+//   - U = [a | -w] and V = [w | a] (64 columns, zero padded past the pairs);
+//   - (U V^T)[i,j] ~ 2^(E_i+E_j-54) acc with acc = sum_{d=2..9} P_d 2^(58-8d) and
+//     P_d = sum_{s+t=d} U_s V_t^T.  |P_d| <= 7 * 64 * 2^14 < 2^24, so each P_d is an
+//     exact FP32 tensor-core sum and its conversion to an integer is exact; acc is
+//     exact up to the truncation of the lowest bits of P_8 and P_9 (|acc| < 2^62).
 //
-// The products with s + t > 8 and the digits beyond the seventh are dropped: the
-// result differs from the exact update by about 2^-53 * K * (max row entry of U) *
-// (max row entry of V), the size of FP64 rounding in an ordinary dot product, but
-// measured against row maxima rather than entry by entry.  K (2 * pairs) is limited
-// to 64 so that the accumulator cannot overflow.
+// The products with s + t > 9 and the bits below 2^(E_i-54) are dropped: the result
+// differs from the exact update by at most about 1.1 * 2^-53 * K * (max row entry of
+// U) * (max row entry of V) -- the size of FP64 rounding in an ordinary dot product,
+// but measured against row maxima rather than entry by entry.  K = 2 * pairs <= 64.
+//
+// Update kernel: persistent, one CTA per SM, tiles of 128 rows x 32 columns of the
+// lower triangle of C, each CTA taking a contiguous run of tiles (consecutive tiles
+// share their 128-row block, so the U slices are loaded once per run).  For one digit
+// s of U, the products with every digit t of V are a single MMA: the V slices t = 1..T
+// lie one after another in shared memory, so together they form one B operand of
+// 32 T rows, and the result columns (t, j) are exactly the accumulator columns of the
+// groups d = s + t, 32 columns per group.  Seven MMAs per K-step (N = 256, 224, 192,
+// ..., 64; the first one reads one extra all-zero slice so that it initialises all
+// eight groups) cover the 34 slice products.  Warp roles:
+//   warp 0   TMA producer: U slices of the row block (7 x 128 x 64 bf16, 112 KB, one
+//            3-D box) and V slices of the column block (7 x 32 x 64, 28 KB) into three
+//            V buffers;
+//   warp 1   allocates 512 tensor-memory columns (two accumulators of 8 groups x 32
+//            columns, so the MMAs of the next tile overlap the epilogue of this one);
+//            one thread issues the 28 MMAs of a tile and commits them to an mbarrier;
+//   warps 2-17 epilogue: warp w reads lanes 32 (w mod 4) .. +31 (its 32 rows) and one
+//            8-column quarter of the tile for all eight groups, combines them in 64-bit
+//            integers, and updates C in FP64.
+// Every wait is bounded (kSplitTimeoutNs); on a timeout the kernel records
+// SKEW_ERR_TIMEOUT, every role leaves its loop, the issued copies and MMAs are waited
+// for (bounded again), the tensor memory is freed and the kernel returns.
 #include <climits>
+#include <mutex>
+
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "common.cuh"
 #include "pairs.cuh"
+#include "tc.cuh"
 
 namespace skew {
 namespace {
 
 constexpr int kSlices = 7;
-constexpr int kTile = 64;
-constexpr int kChunk = 32;               // K columns per staging round
-constexpr int kRowPad = kChunk + 8;      // bf16 per smem row (conflict-free fragments)
-constexpr int kThreads = 128;
+constexpr int kGroups = 8;                  // d = s + t = 2 .. 9
+constexpr int kK = 64;                      // columns of U and V (bf16): one 128-byte row
+constexpr int kTM = 128;                    // tile rows (MMA M)
+constexpr int kTN = 32;                     // tile columns = accumulator columns per group
+constexpr int kEpiWarps = 16;
+constexpr int kEpiCols = 8;                 // tile columns per epilogue warp
+constexpr int kThreads = 32 * (2 + kEpiWarps);   // producer, MMA, epilogue
+constexpr int kVBufs = 3;
+constexpr uint32_t kAccCols = kGroups * kTN;            // 256 per accumulator
+constexpr uint32_t kTmemCols = 2 * kAccCols;            // two accumulators
+constexpr uint32_t kUSlice = kTM * kK * 2;              // 16384
+constexpr uint32_t kVSlice = kTN * kK * 2;              // 4096
+constexpr uint32_t kUBytes = kSlices * kUSlice;         // 114688
+constexpr uint32_t kVLoad = kSlices * kVSlice;          // 28672: slices 1..7
+constexpr uint32_t kVBuf = (kSlices + 1) * kVSlice;     // 32768: + one zero slice
+constexpr size_t kSmemBytes = 1024 + kUBytes + kVBufs * kVBuf + 256;
+static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+static_assert(kTmemCols <= 512, "tensor memory");
+constexpr uint64_t kSplitTimeoutNs = 2000000000ull;    // 2 s
 
 // unbiased exponent and 53-bit significand of |x| (subnormals: exponent -1022)
 __device__ __forceinline__ void decompose(double x, int &ex, unsigned long long &mant) {
@@ -59,86 +98,91 @@ __device__ __forceinline__ int exponent_of(double x) {
     return m == 0 ? INT_MIN / 2 : ex;
 }
 
-// 56-bit fixed point of |x| relative to 2^(E+1): X = trunc(|x| 2^(55-E))
-__device__ __forceinline__ unsigned long long fixed56(double x, int E) {
+// X = trunc(x 2^(54-E)) with the sign of x (|x| < 2^(E+1), so |X| < 2^55)
+__device__ __forceinline__ long long fixed55(double x, int E) {
     int ex;
     unsigned long long m;
     decompose(x, ex, m);
-    const int sh = ex - E + 3;              // |x| = m 2^(ex-52); X = m 2^(ex-52+55-E)
-    if (sh >= 0) return m << sh;             // sh <= 3: at most 56 bits
-    if (sh <= -64) return 0ull;
-    return m >> (-sh);
+    const int sh = ex - E + 2;             // |x| = m 2^(ex-52); X = m 2^(ex+2-E)
+    unsigned long long X;
+    if (sh >= 0) X = m << sh;              // sh <= 2
+    else if (sh <= -64) X = 0ull;
+    else X = m >> (-sh);
+    return x < 0.0 ? -(long long)X : (long long)X;
 }
 
-__device__ __forceinline__ unsigned short bf16_bits_of_digit(unsigned int d, bool neg) {
-    // d in [0, 255] is exact in bf16
-    const __nv_bfloat16 h = __uint2bfloat16_rn(d);
-    unsigned short u = *reinterpret_cast<const unsigned short *>(&h);
-    if (neg && d != 0) u ^= 0x8000u;
-    return u;
+__device__ __forceinline__ unsigned int bf16_bits(int d) {
+    const __nv_bfloat16 h = __int2bfloat16_rn(d);   // |d| <= 128: exact
+    return (unsigned int)*reinterpret_cast<const unsigned short *>(&h);
 }
 
-// Pre-pass: for each row i, the exponent E_i of its largest pair entry and the seven
-// digit slices of its a-part (columns [0, P)) and w-part (columns [P32, P32+P)) into
-// Z[s][i][kk] (bf16, row length 2*P32, zero padded).
+__device__ __forceinline__ unsigned int pack2(int lo, int hi) {
+    return bf16_bits(lo) | (bf16_bits(hi) << 16);
+}
+
+// Pre-pass, four threads per row i (thread g of the row takes pairs 8g .. 8g+7): the
+// exponent E_i of the row's largest pair entry and the digit slices
+// Zu[s][i][0..63] = digits of [a | -w], Zv[s][i][0..63] = digits of [w | a] (pair p in
+// column p of each half, zero past P).
 template <PairKind KIND>
 __global__ void __launch_bounds__(256)
-split_prepare_kernel(int64_t m, PairSource<KIND> src, int P, int P32, unsigned short *Z,
-                     int *rowexp) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
+split_prepare_kernel(int64_t m, PairSource<KIND> src, int P, unsigned short *Zu,
+                     unsigned short *Zv, int *rowexp) {
+    const int64_t i = (int64_t)blockIdx.x * 64 + (threadIdx.x >> 2);
+    const int g = threadIdx.x & 3;
+    double av[8], wv[8];
     int E = INT_MIN / 2;
-    for (int p = 0; p < P; ++p) {
-        double av, wv;
-        src.get(p, i, av, wv);
-        E = max(E, max(exponent_of(av), exponent_of(wv)));
-    }
-    if (E < -1022) E = -1022;                  // an all-zero row
-    rowexp[i] = E;
-    const int KP = 2 * P32;
-    const size_t slice_stride = (size_t)m * KP;
-    unsigned short *zrow = Z + (size_t)i * KP;
-    for (int half = 0; half < 2; ++half) {
-        for (int p0 = 0; p0 < P32; p0 += 8) {
-            unsigned long long X[8];
-            bool neg[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int p = p0 + q;
-                X[q] = 0ull;
-                neg[q] = false;
-                if (p < P) {
-                    double av, wv;
-                    src.get(p, i, av, wv);
-                    const double v = half == 0 ? av : wv;
-                    X[q] = fixed56(v, E);
-                    neg[q] = v < 0.0;
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < kSlices; ++s) {
-                unsigned int w[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const unsigned int d0 = (unsigned int)(X[2 * q] >> (48 - 8 * s)) & 0xffu;
-                    const unsigned int d1 = (unsigned int)(X[2 * q + 1] >> (48 - 8 * s)) & 0xffu;
-                    w[q] = (unsigned int)bf16_bits_of_digit(d0, neg[2 * q]) |
-                           ((unsigned int)bf16_bits_of_digit(d1, neg[2 * q + 1]) << 16);
-                }
-                uint4 *dst = reinterpret_cast<uint4 *>(zrow + s * slice_stride + half * P32 + p0);
-                *dst = make_uint4(w[0], w[1], w[2], w[3]);
-            }
+    for (int q = 0; q < 8; ++q) {
+        const int p = 8 * g + q;
+        av[q] = 0.0;
+        wv[q] = 0.0;
+        if (i < m && p < P) {
+            src.get(p, i, av[q], wv[q]);
+            E = max(E, max(exponent_of(av[q]), exponent_of(wv[q])));
         }
     }
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned int (&a)[4],
-                                         const unsigned int (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
-        "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    E = max(E, __shfl_xor_sync(0xffffffffu, E, 1));
+    E = max(E, __shfl_xor_sync(0xffffffffu, E, 2));
+    if (i >= m) return;
+    if (E < -1022) E = -1022;                  // an all-zero row
+    if (g == 0) rowexp[i] = E;
+    long long Xa[8], Xw[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        Xa[q] = fixed55(av[q], E);
+        Xw[q] = fixed55(wv[q], E);
+    }
+    const size_t slice = (size_t)m * kK;
+    // digits from the least significant (slice 7) up; slice 1 takes what remains
+#pragma unroll
+    for (int s = kSlices - 1; s >= 0; --s) {
+        int da[8], dw[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (s > 0) {
+                da[q] = (int)((Xa[q] + 128) & 255) - 128;
+                dw[q] = (int)((Xw[q] + 128) & 255) - 128;
+                Xa[q] = (Xa[q] - da[q]) >> 8;
+                Xw[q] = (Xw[q] - dw[q]) >> 8;
+            } else {
+                da[q] = (int)Xa[q];
+                dw[q] = (int)Xw[q];
+            }
+        }
+        unsigned short *zu = Zu + s * slice + (size_t)i * kK + 8 * g;
+        unsigned short *zv = Zv + s * slice + (size_t)i * kK + 8 * g;
+        const uint4 ua = make_uint4(pack2(da[0], da[1]), pack2(da[2], da[3]), pack2(da[4], da[5]),
+                                    pack2(da[6], da[7]));
+        const uint4 uw = make_uint4(pack2(dw[0], dw[1]), pack2(dw[2], dw[3]), pack2(dw[4], dw[5]),
+                                    pack2(dw[6], dw[7]));
+        const uint4 nw = make_uint4(pack2(-dw[0], -dw[1]), pack2(-dw[2], -dw[3]),
+                                    pack2(-dw[4], -dw[5]), pack2(-dw[6], -dw[7]));
+        *reinterpret_cast<uint4 *>(zu) = ua;
+        *reinterpret_cast<uint4 *>(zu + 32) = nw;
+        *reinterpret_cast<uint4 *>(zv) = uw;
+        *reinterpret_cast<uint4 *>(zv + 32) = ua;
+    }
 }
 
 // v * 2^e2 rounded to nearest (ties to even), built with integer operations
@@ -164,224 +208,374 @@ __device__ __forceinline__ double scaled_to_double(long long v, int e2) {
     return __longlong_as_double((long long)bits);
 }
 
-__device__ __forceinline__ void tri_tile(int64_t idx, int64_t &bi, int64_t &bj) {
-    int64_t r = (int64_t)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
-    while (r * (r + 1) / 2 > idx) --r;
-    while ((r + 1) * (r + 2) / 2 <= idx) ++r;
-    bi = r;
-    bj = idx - r * (r + 1) / 2;
+// Lower tiles of the (128-row x 32-column) grid in row-block order: row block bi holds
+// column blocks 0 .. 4 bi + 3 (the last row block is cut at the last column block), so
+// tile idx belongs to the largest bi with 2 bi (bi + 1) <= idx.
+__device__ __forceinline__ void tile_of(int64_t idx, int &bi, int &bj) {
+    int64_t r = (int64_t)((sqrt(2.0 * (double)idx + 1.0) - 1.0) * 0.5);
+    while (r > 0 && 2 * r * (r + 1) > idx) --r;
+    while (2 * (r + 1) * (r + 2) <= idx) ++r;
+    bi = (int)r;
+    bj = (int)(idx - 2 * r * (r + 1));
 }
 
-__global__ void __launch_bounds__(kThreads, 3)
-split_update_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
-                    const unsigned short *Z, const int *rowexp, int P32) {
-    // U slices of the tile's rows I and V slices of its rows J (bf16 bit patterns),
-    // in dynamic shared memory: [kSlices][kTile][kRowPad] each
-    extern __shared__ __align__(16) unsigned char split_smem[];
-    typedef unsigned short SliceTile[kTile][kRowPad];
-    SliceTile *Us = reinterpret_cast<SliceTile *>(split_smem);
-    SliceTile *Vs = reinterpret_cast<SliceTile *>(split_smem + sizeof(SliceTile) * kSlices);
-
-    int64_t bi, bj;
-    tri_tile(blockIdx.x, bi, bj);
-    const int64_t I0 = bi * kTile, J0 = bj * kTile;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp & 1, wn = warp >> 1;
-    const int g = lane >> 2, tg = lane & 3;
-    const int KP = 2 * P32;
-    const size_t slice_stride = (size_t)m * KP;
-
-    long long acc[2][4][4];                    // [mi][ni][c] fixed point, weight 2^-56
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[mi][ni][c] = 0;
-
-    const int nchunks = KP / kChunk;
-    for (int ch = 0; ch < nchunks; ++ch) {
-        // U columns [ch*32, ch*32+32) of [a | -w] and the same columns of V = [w | a].
-        // The digits are copied as stored (+a, +w) with cp.async, all copies of a
-        // thread in flight at once (rows past m are zero-filled); a chunk of the w-part
-        // of U enters the accumulator with a minus sign instead.
-        const int ucol = ch * kChunk;
-        const bool uneg = ucol >= P32;                        // U holds -w here
-        const int vcol = uneg ? ucol - P32 : ucol + P32;      // the other half
-        for (int it = tid; it < kSlices * kTile * (kChunk / 8); it += kThreads) {
-            const int seg = it % (kChunk / 8);
-            const int r = (it / (kChunk / 8)) % kTile;
-            const int s = it / ((kChunk / 8) * kTile);
-            const bool iu = I0 + r < m, jv = J0 + r < m;
-            const unsigned short *su =
-                iu ? Z + s * slice_stride + (size_t)(I0 + r) * KP + ucol + seg * 8 : Z;
-            const unsigned short *sv =
-                jv ? Z + s * slice_stride + (size_t)(J0 + r) * KP + vcol + seg * 8 : Z;
-            const unsigned int du = (unsigned int)__cvta_generic_to_shared(&Us[s][r][seg * 8]);
-            const unsigned int dv = (unsigned int)__cvta_generic_to_shared(&Vs[s][r][seg * 8]);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(du), "l"(su),
-                         "r"(iu ? 16 : 0)
-                         : "memory");
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dv), "l"(sv),
-                         "r"(jv ? 16 : 0)
-                         : "memory");
+// Walks the tiles lo, lo+1, ... of the same order in O(1) per step.
+struct TileWalk {
+    int bi, bj;
+    int64_t nbj;
+    __device__ __forceinline__ TileWalk(int64_t idx, int64_t nbj_) : nbj(nbj_) { tile_of(idx, bi, bj); }
+    __device__ __forceinline__ void next() {
+        const int64_t cols = 4 * (int64_t)bi + 4 < nbj ? 4 * (int64_t)bi + 4 : nbj;
+        if (++bj >= cols) {
+            ++bi;
+            bj = 0;
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        __syncthreads();
+    }
+};
+
+struct SplitShared {
+    uint64_t u_full, u_empty, v_full[kVBufs], v_empty[kVBufs], acc_full[2], acc_empty[2], drain;
+    uint32_t tmem;
+    int abort;
+};
+static_assert(sizeof(SplitShared) <= 256, "barrier block");
+
+// Bounded wait for the phase of the given parity; false on a timeout (recorded in
+// *err when err is given) or when another role has given up.
+__device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, SplitShared *sh,
+                                           int *err) {
+    if (tc::mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!tc::mbar_wait_for(bar, parity, 20000u)) {
+        if (ld_volatile_i32(&sh->abort)) return false;
+        if (global_ns() - t0 > kSplitTimeoutNs) {
+            *reinterpret_cast<volatile int *>(&sh->abort) = 1;
+            if (err) atomicCAS(err, 0, SKEW_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// The 8 entries C[i, j0 .. j0+7] of the strictly lower part that a thread updates
+// (0 elsewhere, and not read when beta = 0); issued before the accumulator is ready.
+__device__ __forceinline__ void load_row(const double *crow, int64_t ldc, int64_t i, int64_t j0,
+                                         int64_t m, bool interior, bool read,
+                                         double (&cv)[kEpiCols]) {
+#pragma unroll
+    for (int k = 0; k < kEpiCols; ++k) {
+        const int64_t j = j0 + k;
+        const bool in = interior || (i < m && j < m && i > j);
+        cv[k] = (in && read) ? crow[k * ldc] : 0.0;
+    }
+}
+
+// C[i,j] = beta C[i,j] + alpha 2^(E_i+E_j-54) acc[k] for the 8 columns j0 .. j0+7 of
+// row i, strictly lower part only.  PLAIN: alpha = beta = 1 (one FP64 add per entry).
+template <bool PLAIN>
+__device__ __forceinline__ void store_row(double *crow, int64_t ldc, int64_t i, int64_t j0,
+                                          int64_t m, bool interior, int Ei, int Ej_lane,
+                                          const long long (&acc)[kEpiCols],
+                                          const double (&cv)[kEpiCols], double alpha,
+                                          double beta) {
+#pragma unroll
+    for (int k = 0; k < kEpiCols; ++k) {
+        const int Ej = __shfl_sync(0xffffffffu, Ej_lane, k);
+        const int64_t j = j0 + k;
+        if (!(interior || (i < m && j < m && i > j))) continue;
+        const double upd = scaled_to_double(acc[k], Ei + Ej - 54);
+        if (PLAIN) crow[k * ldc] = cv[k] + upd;
+        else crow[k * ldc] = fma(beta, cv[k], alpha * upd);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+split_tc_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
+                const __grid_constant__ CUtensorMap mapU, const __grid_constant__ CUtensorMap mapV,
+                const int *rowexp, int64_t ntiles, int64_t nbj, int *err) {
+    extern __shared__ unsigned char split_raw[];
+    unsigned char *base =
+        split_raw + ((1024u - (tc::smem_u32(split_raw) & 1023u)) & 1023u);   // 1024-aligned
+    unsigned char *sU = base;
+    unsigned char *sV = base + kUBytes;                                        // kVBufs buffers
+    SplitShared *sh = reinterpret_cast<SplitShared *>(base + kUBytes + kVBufs * kVBuf);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t lo = (int64_t)blockIdx.x * ntiles / gridDim.x;
+    const int64_t hi = (int64_t)(blockIdx.x + 1) * ntiles / gridDim.x;
+
+    // the zero slice after the seven V slices of every buffer (read by the N = 256 MMA)
+    for (int b = 0; b < kVBufs; ++b)
+        for (int o = threadIdx.x * 16; o < (int)kVSlice; o += kThreads * 16)
+            *reinterpret_cast<uint4 *>(sV + b * kVBuf + kVLoad + o) = make_uint4(0, 0, 0, 0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&sh->u_full, 1);
+        tc::mbar_init(&sh->u_empty, 1);
+        for (int b = 0; b < kVBufs; ++b) {
+            tc::mbar_init(&sh->v_full[b], 1);
+            tc::mbar_init(&sh->v_empty[b], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(&sh->acc_full[a], 1);
+            tc::mbar_init(&sh->acc_empty[a], kEpiWarps);
+        }
+        tc::mbar_init(&sh->drain, 1);
+        sh->abort = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(&sh->tmem, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = sh->tmem;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------------------- producer
+        tc::tma_prefetch_map(&mapU);
+        tc::tma_prefetch_map(&mapV);
+        uint32_t u_loads = 0, v_loads[kVBufs] = {0, 0, 0};
+        int prev_bi = -1;
+        TileWalk tw(lo, nbj);
+        for (int64_t idx = lo; idx < hi; ++idx, tw.next()) {
+            const int bi = tw.bi, bj = tw.bj;
+            if (bi != prev_bi) {
+                if (u_loads > 0 && !wait_phase(&sh->u_empty, (u_loads - 1) & 1, sh, err)) break;
+                tc::mbar_arrive_expect_tx(&sh->u_full, kUBytes);
+                tc::tma_load_3d(sU, &mapU, 0, bi * kTM, 0, &sh->u_full);
+                ++u_loads;
+                prev_bi = bi;
+            }
+            const int b = (int)((idx - lo) % kVBufs);
+            if (!wait_phase(&sh->v_empty[b], (v_loads[b] & 1) ^ 1, sh, err)) break;
+            tc::mbar_arrive_expect_tx(&sh->v_full[b], kVLoad);
+            tc::tma_load_3d(sV + b * kVBuf, &mapV, 0, bj * kTN, 0, &sh->v_full[b]);
+            ++v_loads[b];
+        }
+        // every issued copy has landed before the shared memory is released
+        if (u_loads > 0) wait_phase(&sh->u_full, (u_loads - 1) & 1, sh, nullptr);
+        for (int b = 0; b < kVBufs; ++b)
+            if (v_loads[b] > 0) wait_phase(&sh->v_full[b], (v_loads[b] - 1) & 1, sh, nullptr);
+    } else if (warp == 1 && lane == 0) {
+        // ---------------------------------------------------------------- MMA issue
+        const uint32_t u_addr = tc::smem_u32(sU), v_addr = tc::smem_u32(sV);
+        uint32_t u_uses = 0;
+        int prev_bi = -1;
+        TileWalk tw(lo, nbj);
+        for (int64_t idx = lo; idx < hi; ++idx) {
+            const int bi = tw.bi;
+            tw.next();                               // tw is now the next tile
+            if (bi != prev_bi) {
+                if (!wait_phase(&sh->u_full, u_uses & 1, sh, err)) break;
+                ++u_uses;
+                prev_bi = bi;
+            }
+            const int64_t tau = idx - lo;
+            const int b = (int)(tau % kVBufs);
+            const int ab = (int)(tau & 1);
+            if (!wait_phase(&sh->v_full[b], (uint32_t)((tau / kVBufs) & 1), sh, err)) break;
+            if (!wait_phase(&sh->acc_empty[ab], (uint32_t)(((tau >> 1) & 1) ^ 1), sh, err)) break;
+            tc::fence_after_sync();
+            const uint32_t vb = v_addr + (uint32_t)b * kVBuf;
+            const uint32_t acc_base = tmem + (uint32_t)ab * kAccCols;
 #pragma unroll 1
-        for (int d = 2; d <= kSlices + 1; ++d) {
-            float f[2][4][4];
+            for (int s = 1; s <= kSlices; ++s) {
+                // digit s of U times V slices 1..T into groups s+1 .. s+T
+                const int T = s == 1 ? kSlices + 1 : (kSlices < 9 - s ? kSlices : 9 - s);
+                const uint32_t idesc = tc::idesc_bf16_f32(kTM, kTN * T);
+                const uint32_t dt = acc_base + (uint32_t)(s - 1) * kTN;
 #pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) f[mi][ni][c] = 0.0f;
-            const int s_lo = d - kSlices > 1 ? d - kSlices : 1;
-            const int s_hi = d - 1 < kSlices ? d - 1 : kSlices;
-#pragma unroll 1
-            for (int s = s_lo; s <= s_hi; ++s) {
-                const int t = d - s;
-#pragma unroll
-                for (int ks = 0; ks < kChunk / 16; ++ks) {
-                    const int kb = ks * 16 + 2 * tg;
-                    unsigned int a[2][4], b[4][2];
-#pragma unroll
-                    for (int mi = 0; mi < 2; ++mi) {
-                        const int r0 = wm * 32 + mi * 16 + g;
-                        a[mi][0] = *reinterpret_cast<const unsigned int *>(&Us[s - 1][r0][kb]);
-                        a[mi][1] = *reinterpret_cast<const unsigned int *>(&Us[s - 1][r0 + 8][kb]);
-                        a[mi][2] = *reinterpret_cast<const unsigned int *>(&Us[s - 1][r0][kb + 8]);
-                        a[mi][3] = *reinterpret_cast<const unsigned int *>(&Us[s - 1][r0 + 8][kb + 8]);
-                    }
-#pragma unroll
-                    for (int ni = 0; ni < 4; ++ni) {
-                        const int c0 = wn * 32 + ni * 8 + g;
-                        b[ni][0] = *reinterpret_cast<const unsigned int *>(&Vs[t - 1][c0][kb]);
-                        b[ni][1] = *reinterpret_cast<const unsigned int *>(&Vs[t - 1][c0][kb + 8]);
-                    }
-#pragma unroll
-                    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                        for (int ni = 0; ni < 4; ++ni) mma_bf16(f[mi][ni], a[mi], b[ni]);
+                for (int ks = 0; ks < kK / 16; ++ks) {
+                    const uint64_t ad = tc::sdesc_kmajor_sw128(u_addr + (s - 1) * kUSlice + ks * 32);
+                    const uint64_t bd = tc::sdesc_kmajor_sw128(vb + ks * 32);
+                    tc::mma_bf16(dt, ad, bd, idesc, (s > 1 || ks > 0) ? 1u : 0u);
                 }
             }
-            // exact integers below 2^24: add with weight 2^(56-8d) (d = 8: 2^-8, truncated)
-            const int shl = 56 - 8 * d;
+            tc::mma_commit(&sh->acc_full[ab]);
+            tc::mma_commit(&sh->v_empty[b]);
+            if (idx + 1 >= hi || tw.bi != bi) tc::mma_commit(&sh->u_empty);
+        }
+        // every issued MMA has completed before the tensor memory is released
+        tc::mma_commit(&sh->drain);
+        wait_phase(&sh->drain, 0, sh, nullptr);
+    } else if (warp >= 2) {
+        // ---------------------------------------------------------------- epilogue
+        const int q = warp & 3;                      // lane quarter of the tensor memory
+        const int cq = (warp - 2) >> 2;              // 8-column quarter of the tile
+        const uint32_t lane_off = ((uint32_t)(q * 32) << 16) + (uint32_t)(cq * kEpiCols);
+        const bool plain = alpha == 1.0 && beta == 1.0;
+        const bool read = beta != 0.0;
+        TileWalk tw(lo, nbj);
+        for (int64_t idx = lo; idx < hi; ++idx, tw.next()) {
+            const int64_t tau = idx - lo;
+            const int ab = (int)(tau & 1);
+            const int64_t r0 = (int64_t)tw.bi * kTM + q * 32;
+            const int64_t i = r0 + lane;
+            const int64_t j0 = (int64_t)tw.bj * kTN + cq * kEpiCols;
+            // everything that does not depend on the accumulator is loaded first, so its
+            // latency passes while the MMAs run
+            const bool interior = r0 + 31 < m && j0 + kEpiCols - 1 < m && r0 > j0 + kEpiCols - 1;
+            double *crow = C + i + j0 * ldc;
+            const int Ei = i < m ? __ldg(rowexp + i) : 0;
+            const int Ej_lane = (lane < kEpiCols && j0 + lane < m) ? __ldg(rowexp + j0 + lane) : 0;
+            double cv[kEpiCols];
+            load_row(crow, ldc, i, j0, m, interior, read, cv);
+            int got = 1;
+            if (lane == 0) got = wait_phase(&sh->acc_full[ab], (uint32_t)((tau >> 1) & 1), sh, err);
+            if (!__shfl_sync(0xffffffffu, got, 0)) break;   // warp-uniform: tcgen05.ld is collective
+            tc::fence_after_sync();
+            const uint32_t ta = tmem + (uint32_t)ab * kAccCols + lane_off;
+            // acc = Q23 2^34 + Q45 2^18 + Q67 2^2 + Q89 2^-14 with Q = 256 P_d + P_(d+1)
+            // (|Q| < 2^31: exact in 32 bits).  Q89 only reaches acc shifted right by 14,
+            // so it is formed in FP32: its rounding (< 2^7) stays below one unit of acc.
+            long long acc[kEpiCols];
 #pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
+            for (int h = 0; h < 2; ++h) {            // groups 2..5, then 6..9
+                uint32_t r[4][kEpiCols];
 #pragma unroll
-                for (int ni = 0; ni < 4; ++ni)
+                for (int g = 0; g < 4; ++g) tc::tmem_ld8(ta + (uint32_t)(4 * h + g) * kTN, r[g]);
+                tc::tmem_ld_wait();
+                if (h == 1) {                        // the accumulator can take the next tile
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&sh->acc_empty[ab]);
+                }
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        long long q = (long long)__float2int_rn(f[mi][ni][c]);
-                        q = shl >= 0 ? (q << shl) : (q >> (-shl));
-                        acc[mi][ni][c] += uneg ? -q : q;
+                for (int k = 0; k < kEpiCols; ++k) {
+                    const float f0 = __uint_as_float(r[0][k]), f1 = __uint_as_float(r[1][k]);
+                    const float f2 = __uint_as_float(r[2][k]), f3 = __uint_as_float(r[3][k]);
+                    const long long Qa = (long long)(__float2int_rn(f0) * 256 + __float2int_rn(f1));
+                    if (h == 0) {
+                        const long long Qb =
+                            (long long)(__float2int_rn(f2) * 256 + __float2int_rn(f3));
+                        acc[k] = (Qa << 34) + (Qb << 18);
+                    } else {
+                        acc[k] += (Qa << 2) +
+                                  (long long)__float2int_rd(fmaf(f2, 256.0f, f3) * 0x1p-14f);
                     }
+                }
+            }
+            if (plain) store_row<true>(crow, ldc, i, j0, m, interior, Ei, Ej_lane, acc, cv, alpha, beta);
+            else store_row<false>(crow, ldc, i, j0, m, interior, Ei, Ej_lane, acc, cv, alpha, beta);
+            if (lane < kEpiCols) {   // bring the next tile's block of C (32 x 8) towards L2
+                TileWalk nx = tw;
+                nx.next();
+                const int64_t nr0 = (int64_t)nx.bi * kTM + q * 32;
+                const int64_t j = (int64_t)nx.bj * kTN + cq * kEpiCols + lane;
+                if (idx + 1 < hi && nr0 < m && j < m && nr0 + 31 > j) {
+                    const int64_t rl = (nr0 + 31 < m ? nr0 + 31 : m - 1);
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(C + nr0 + j * ldc));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(C + (nr0 + rl) / 2 + j * ldc));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(C + rl + j * ldc));
+                }
+            }
         }
-        __syncthreads();
     }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc::tmem_dealloc(tmem, kTmemCols);
+    }
+}
 
-    // epilogue: C[i,j] = beta C[i,j] + alpha 2^(E_i+E_j+2-56) acc, strictly lower part.
-    // All loads of a row block (row exponents, C entries) are issued before any
-    // store, so their latencies overlap instead of adding up.
-    int Ej[4][2];
-#pragma unroll
-    for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int64_t gj = J0 + wn * 32 + ni * 8 + 2 * tg + c;
-            Ej[ni][c] = gj < m ? __ldg(rowexp + gj) : 0;
-        }
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi) {
-        int Ei[2];
-        double cv[2][4][2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t gi = I0 + wm * 32 + mi * 16 + g + 8 * h;
-            Ei[h] = gi < m ? __ldg(rowexp + gi) : 0;
-#pragma unroll
-            for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const int64_t gj = J0 + wn * 32 + ni * 8 + 2 * tg + c;
-                    const bool in = gi < m && gj < m && gi > gj && beta != 0.0;
-                    cv[h][ni][c] = in ? C[gi + gj * ldc] : 0.0;
-                }
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t gi = I0 + wm * 32 + mi * 16 + g + 8 * h;
-#pragma unroll
-            for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const int64_t gj = J0 + wn * 32 + ni * 8 + 2 * tg + c;
-                    if (gi >= m || gj >= m || gi <= gj) continue;
-                    const double upd =
-                        scaled_to_double(acc[mi][ni][2 * h + c], Ei[h] + Ej[ni][c] + 2 - 56);
-                    double *dst = C + gi + gj * ldc;
-                    if (beta == 1.0 && alpha == 1.0) *dst = cv[h][ni][c] + upd;
-                    else if (beta == 0.0) *dst = alpha * upd;
-                    else *dst = beta * cv[h][ni][c] + alpha * upd;
-                }
-        }
-    }
+// ---------------------------------------------------------------- tensor maps (host)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// [7][m][64] bf16 slices; box of 64 x rows x 7, 128-byte swizzle, rows past m read as 0
+int make_slice_map(CUtensorMap *map, const unsigned short *Z, int64_t m, int rows) {
+    EncodeTiledFn enc = encode_fn();
+    if (enc == nullptr) return SKEW_ERR_CUDA;
+    const cuuint64_t dims[3] = {(cuuint64_t)kK, (cuuint64_t)m, (cuuint64_t)kSlices};
+    const cuuint64_t strides[2] = {(cuuint64_t)kK * 2, (cuuint64_t)m * kK * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)kK, (cuuint32_t)rows, (cuuint32_t)kSlices};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                           const_cast<unsigned short *>(Z), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? SKEW_OK : SKEW_ERR_CUDA;
+}
+
+size_t slice_bytes(int64_t m) {
+    const size_t z = (size_t)kSlices * (size_t)(m > 0 ? m : 1) * kK * sizeof(unsigned short);
+    return (z + 1023) & ~size_t(1023);
 }
 
 template <PairKind KIND>
-int launch_split_kind(const Skr2kArgs &a, void *scratch, cudaStream_t stream) {
+int launch_split_kind(const Skr2kArgs &a, void *scratch, int *err, int sms,
+                      cudaStream_t stream) {
     if (a.m <= 1) return SKEW_OK;
+    if (a.m > INT_MAX / 2) return SKEW_ERR_CUDA;
     PairSource<KIND> src{a.P, a.ldp, a.Q, a.ldq, a.tt, a.x, a.b};
     int P;
     if (KIND == PairKind::Rank2k) P = (int)a.b;
     else if (KIND == PairKind::Tridiag) P = (int)(a.b / 2);
     else P = (int)(a.b / 2 + (a.b & 1));
-    const int P32 = P <= 0 ? 32 : ((P + 31) / 32) * 32;
-    if (P32 > 32) return SKEW_ERR_CUDA;           // guarded by the callers (<= 32 pairs)
+    if (P > 32) return SKEW_ERR_CUDA;             // guarded by the callers (<= 32 pairs)
+    if (P < 0) P = 0;
     char *base = static_cast<char *>(scratch);
-    unsigned short *Z = reinterpret_cast<unsigned short *>(base);
-    int *rowexp = reinterpret_cast<int *>(base + split_z_bytes(a.m));
-    const int pgrid = (int)((a.m + 255) / 256);
-    split_prepare_kernel<KIND><<<pgrid, 256, 0, stream>>>(a.m, src, P, P32, Z, rowexp);
+    unsigned short *Zu = reinterpret_cast<unsigned short *>(base);
+    unsigned short *Zv = reinterpret_cast<unsigned short *>(base + slice_bytes(a.m));
+    int *rowexp = reinterpret_cast<int *>(base + 2 * slice_bytes(a.m));
+    const int pgrid = (int)((a.m + 63) / 64);            // 64 rows per 256-thread CTA
+    split_prepare_kernel<KIND><<<pgrid, 256, 0, stream>>>(a.m, src, P, Zu, Zv, rowexp);
     note_launches(1);
     SKEW_TRY_STATUS(check_launch());
-    const int64_t nt = (a.m + kTile - 1) / kTile;
-    const int64_t tiles = nt * (nt + 1) / 2;
-    if (tiles > INT_MAX) return SKEW_ERR_CUDA;
-    const size_t smem = 2 * sizeof(unsigned short) * kSlices * kTile * kRowPad;
-    static_assert(2 * sizeof(unsigned short) * kSlices * kTile * kRowPad <= 227 * 1024, "smem");
-    cudaError_t e = cudaFuncSetAttribute((const void *)split_update_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+
+    CUtensorMap mapU, mapV;
+    SKEW_TRY_STATUS(make_slice_map(&mapU, Zu, a.m, kTM));
+    SKEW_TRY_STATUS(make_slice_map(&mapV, Zv, a.m, kTN));
+    const int64_t nbi = (a.m + kTM - 1) / kTM, nbj = (a.m + kTN - 1) / kTN;
+    const int64_t ntiles = 2 * (nbi - 1) * nbi + nbj;
+    const int grid = (int)(ntiles < sms ? ntiles : sms);
+    cudaError_t e = cudaFuncSetAttribute((const void *)split_tc_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemBytes);
     if (e != cudaSuccess) {
         set_last_error(e);
         return SKEW_ERR_CUDA;
     }
-    split_update_kernel<<<(unsigned)tiles, kThreads, smem, stream>>>(a.m, a.C, a.ldc, a.alpha,
-                                                                     a.beta, Z, rowexp, P32);
+    split_tc_kernel<<<grid, kThreads, kSmemBytes, stream>>>(a.m, a.C, a.ldc, a.alpha, a.beta,
+                                                           mapU, mapV, rowexp, ntiles, nbj, err);
     note_launches(1);
     return check_launch();
 }
 
 }  // namespace
 
-size_t split_z_bytes(int64_t m) {
-    // seven slices of m rows of 64 bf16 (the largest K), 256-byte aligned
-    const size_t z = (size_t)kSlices * (size_t)(m > 0 ? m : 1) * 64 * sizeof(unsigned short);
-    return (z + 255) & ~size_t(255);
-}
-
 size_t split_scratch_bytes(int64_t m) {
-    return split_z_bytes(m) + (((size_t)(m > 0 ? m : 1) * sizeof(int) + 255) & ~size_t(255));
+    return 2 * slice_bytes(m) + (((size_t)(m > 0 ? m : 1) * sizeof(int) + 255) & ~size_t(255));
 }
 
-int launch_skr2k_split(PairKind kind, const Skr2kArgs &a, void *scratch, cudaStream_t stream) {
+int launch_skr2k_split(PairKind kind, const Skr2kArgs &a, void *scratch, int *err, int sms,
+                       cudaStream_t stream) {
     switch (kind) {
-        case PairKind::Rank2k: return launch_split_kind<PairKind::Rank2k>(a, scratch, stream);
-        case PairKind::Tridiag: return launch_split_kind<PairKind::Tridiag>(a, scratch, stream);
-        default: return launch_split_kind<PairKind::Fused>(a, scratch, stream);
+        case PairKind::Rank2k:
+            return launch_split_kind<PairKind::Rank2k>(a, scratch, err, sms, stream);
+        case PairKind::Tridiag:
+            return launch_split_kind<PairKind::Tridiag>(a, scratch, err, sms, stream);
+        default: return launch_split_kind<PairKind::Fused>(a, scratch, err, sms, stream);
     }
 }
 
