@@ -185,6 +185,12 @@ split_prepare_kernel(int64_t m, PairSource<KIND> src, int P, unsigned short *Zu,
     }
 }
 
+// v * 2^e2 outside the normal range of the result (rare; kept out of line so that its
+// FP64 operations are not executed speculatively for every entry)
+__device__ __noinline__ double scaled_to_double_slow(long long v, int e2) {
+    return ldexp((double)v, e2);
+}
+
 // v * 2^e2 rounded to nearest (ties to even), built with integer operations
 __device__ __forceinline__ double scaled_to_double(long long v, int e2) {
     if (v == 0) return 0.0;
@@ -202,7 +208,7 @@ __device__ __forceinline__ double scaled_to_double(long long v, int e2) {
             ++E;
         }
     }
-    if (E <= 0 || E >= 2047) return ldexp((double)v, e2);   // outside the normal range
+    if (E <= 0 || E >= 2047) return scaled_to_double_slow(v, e2);
     const unsigned long long bits =
         ((unsigned long long)neg << 63) | ((unsigned long long)E << 52) | mant;
     return __longlong_as_double((long long)bits);
@@ -318,7 +324,7 @@ split_tc_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
         }
         for (int a = 0; a < 2; ++a) {
             tc::mbar_init(&sh->acc_full[a], 1);
-            tc::mbar_init(&sh->acc_empty[a], kEpiWarps);
+            tc::mbar_init(&sh->acc_empty[a], kEpiWarps / 2);   // one warp group per accumulator
         }
         tc::mbar_init(&sh->drain, 1);
         sh->abort = 0;
@@ -403,69 +409,92 @@ split_tc_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
         wait_phase(&sh->drain, 0, sh, nullptr);
     } else if (warp >= 2) {
         // ---------------------------------------------------------------- epilogue
+        // Two groups of 8 warps take alternate tiles (group g: accumulator g), so the
+        // FP64 adds of one group overlap the integer work of the other.  In a group,
+        // warp w reads lanes 32 (w mod 4) .. +31 and one 16-column half of the tile, as
+        // two passes of 8 columns.
+        const int e = warp - 2;
+        const int grp = e >> 3;
         const int q = warp & 3;                      // lane quarter of the tensor memory
-        const int cq = (warp - 2) >> 2;              // 8-column quarter of the tile
-        const uint32_t lane_off = ((uint32_t)(q * 32) << 16) + (uint32_t)(cq * kEpiCols);
+        const int ch = (e >> 2) & 1;                 // 16-column half of the tile
         const bool plain = alpha == 1.0 && beta == 1.0;
         const bool read = beta != 0.0;
         TileWalk tw(lo, nbj);
-        for (int64_t idx = lo; idx < hi; ++idx, tw.next()) {
+        if (grp == 1) tw.next();
+        for (int64_t idx = lo + grp; idx < hi; idx += 2, tw.next(), tw.next()) {
             const int64_t tau = idx - lo;
-            const int ab = (int)(tau & 1);
             const int64_t r0 = (int64_t)tw.bi * kTM + q * 32;
             const int64_t i = r0 + lane;
-            const int64_t j0 = (int64_t)tw.bj * kTN + cq * kEpiCols;
-            // everything that does not depend on the accumulator is loaded first, so its
-            // latency passes while the MMAs run
-            const bool interior = r0 + 31 < m && j0 + kEpiCols - 1 < m && r0 > j0 + kEpiCols - 1;
-            double *crow = C + i + j0 * ldc;
             const int Ei = i < m ? __ldg(rowexp + i) : 0;
-            const int Ej_lane = (lane < kEpiCols && j0 + lane < m) ? __ldg(rowexp + j0 + lane) : 0;
-            double cv[kEpiCols];
-            load_row(crow, ldc, i, j0, m, interior, read, cv);
-            int got = 1;
-            if (lane == 0) got = wait_phase(&sh->acc_full[ab], (uint32_t)((tau >> 1) & 1), sh, err);
-            if (!__shfl_sync(0xffffffffu, got, 0)) break;   // warp-uniform: tcgen05.ld is collective
-            tc::fence_after_sync();
-            const uint32_t ta = tmem + (uint32_t)ab * kAccCols + lane_off;
-            // acc = Q23 2^34 + Q45 2^18 + Q67 2^2 + Q89 2^-14 with Q = 256 P_d + P_(d+1)
-            // (|Q| < 2^31: exact in 32 bits).  Q89 only reaches acc shifted right by 14,
-            // so it is formed in FP32: its rounding (< 2^7) stays below one unit of acc.
-            long long acc[kEpiCols];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {            // groups 2..5, then 6..9
-                uint32_t r[4][kEpiCols];
-#pragma unroll
-                for (int g = 0; g < 4; ++g) tc::tmem_ld8(ta + (uint32_t)(4 * h + g) * kTN, r[g]);
-                tc::tmem_ld_wait();
-                if (h == 1) {                        // the accumulator can take the next tile
-                    tc::fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&sh->acc_empty[ab]);
+            const uint32_t ta = tmem + (uint32_t)grp * kAccCols + ((uint32_t)(q * 32) << 16);
+            bool ok = true;
+#pragma unroll 1
+            for (int ps = 0; ps < 2; ++ps) {
+                const int cofs = ch * 16 + ps * kEpiCols;      // column offset in the tile
+                const int64_t j0 = (int64_t)tw.bj * kTN + cofs;
+                // everything that does not depend on the accumulator is loaded first
+                const bool interior =
+                    r0 + 31 < m && j0 + kEpiCols - 1 < m && r0 > j0 + kEpiCols - 1;
+                double *crow = C + i + j0 * ldc;
+                const int Ej_lane =
+                    (lane < kEpiCols && j0 + lane < m) ? __ldg(rowexp + j0 + lane) : 0;
+                double cv[kEpiCols];
+                load_row(crow, ldc, i, j0, m, interior, read, cv);
+                if (ps == 0) {
+                    int got = 1;
+                    if (lane == 0)
+                        got = wait_phase(&sh->acc_full[grp], (uint32_t)((tau >> 1) & 1), sh, err);
+                    if (!__shfl_sync(0xffffffffu, got, 0)) {   // warp-uniform (tcgen05.ld)
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
                 }
+                // acc = Q23 2^34 + Q45 2^18 + Q67 2^2 + Q89 2^-14 with Q = 256 P_d + P_(d+1)
+                // (|Q| < 2^31: exact in 32 bits).  Q89 only reaches acc shifted right by
+                // 14, so it is formed in FP32: its rounding (< 2^7) stays below one unit.
+                long long acc[kEpiCols];
 #pragma unroll
-                for (int k = 0; k < kEpiCols; ++k) {
-                    const float f0 = __uint_as_float(r[0][k]), f1 = __uint_as_float(r[1][k]);
-                    const float f2 = __uint_as_float(r[2][k]), f3 = __uint_as_float(r[3][k]);
-                    const long long Qa = (long long)(__float2int_rn(f0) * 256 + __float2int_rn(f1));
-                    if (h == 0) {
-                        const long long Qb =
-                            (long long)(__float2int_rn(f2) * 256 + __float2int_rn(f3));
-                        acc[k] = (Qa << 34) + (Qb << 18);
-                    } else {
-                        acc[k] += (Qa << 2) +
-                                  (long long)__float2int_rd(fmaf(f2, 256.0f, f3) * 0x1p-14f);
+                for (int h = 0; h < 2; ++h) {        // groups 2..5, then 6..9
+                    uint32_t r[4][kEpiCols];
+#pragma unroll
+                    for (int g = 0; g < 4; ++g)
+                        tc::tmem_ld8(ta + (uint32_t)(4 * h + g) * kTN + cofs, r[g]);
+                    tc::tmem_ld_wait();
+                    if (h == 1 && ps == 1) {         // the accumulator can take a new tile
+                        tc::fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&sh->acc_empty[grp]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < kEpiCols; ++k) {
+                        const float f0 = __uint_as_float(r[0][k]), f1 = __uint_as_float(r[1][k]);
+                        const float f2 = __uint_as_float(r[2][k]), f3 = __uint_as_float(r[3][k]);
+                        const long long Qa =
+                            (long long)(__float2int_rn(f0) * 256 + __float2int_rn(f1));
+                        if (h == 0) {
+                            const long long Qb =
+                                (long long)(__float2int_rn(f2) * 256 + __float2int_rn(f3));
+                            acc[k] = (Qa << 34) + (Qb << 18);
+                        } else {
+                            acc[k] += (Qa << 2) +
+                                      (long long)__float2int_rd(fmaf(f2, 256.0f, f3) * 0x1p-14f);
+                        }
                     }
                 }
+                if (plain)
+                    store_row<true>(crow, ldc, i, j0, m, interior, Ei, Ej_lane, acc, cv, alpha, beta);
+                else
+                    store_row<false>(crow, ldc, i, j0, m, interior, Ei, Ej_lane, acc, cv, alpha, beta);
             }
-            if (plain) store_row<true>(crow, ldc, i, j0, m, interior, Ei, Ej_lane, acc, cv, alpha, beta);
-            else store_row<false>(crow, ldc, i, j0, m, interior, Ei, Ej_lane, acc, cv, alpha, beta);
-            if (lane < kEpiCols) {   // bring the next tile's block of C (32 x 8) towards L2
+            if (!ok) break;
+            if (lane < 16) {   // bring this group's next block of C (32 x 16) towards L2
                 TileWalk nx = tw;
                 nx.next();
+                nx.next();
                 const int64_t nr0 = (int64_t)nx.bi * kTM + q * 32;
-                const int64_t j = (int64_t)nx.bj * kTN + cq * kEpiCols + lane;
-                if (idx + 1 < hi && nr0 < m && j < m && nr0 + 31 > j) {
+                const int64_t j = (int64_t)nx.bj * kTN + ch * 16 + lane;
+                if (idx + 2 < hi && nr0 < m && j < m && nr0 + 31 > j) {
                     const int64_t rl = (nr0 + 31 < m ? nr0 + 31 : m - 1);
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(C + nr0 + j * ldc));
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(C + (nr0 + rl) / 2 + j * ldc));
