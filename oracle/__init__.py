@@ -69,6 +69,8 @@ class OracleLib:
         lib.oracle_skew_rank2k.restype = None
         lib.oracle_skew_tridiag_rankk.argtypes = [i64, i64, dbl, p, i64, p, dbl, p, i64]
         lib.oracle_skew_tridiag_rankk.restype = None
+        lib.oracle_pfaffian_twostep.argtypes = [i64, p, i64, p, p, p, p]
+        lib.oracle_pfaffian_twostep.restype = ctypes.c_int
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = ctypes.c_int
         self.lib = lib
@@ -127,6 +129,23 @@ class OracleLib:
             raise ValueError(f"oracle_ltlt failed with {info}")
         return self.pfaffian_from_factors(A.shape[0], t, piv)
 
+    def pfaffian_twostep(self, A: np.ndarray):
+        """Pf(A) by the two-step elimination with pivoting at even steps only.
+
+        Returns ``(log|Pf|, sign, a, piv, info)``: ``a`` the floor(n/2) pivot-block
+        entries, ``piv`` int32 length n (piv[k+1] at even k, identity elsewhere),
+        ``info`` as returned by the C routine.
+        """
+        n = int(A.shape[0])
+        X = _fortran_copy(A) if n > 0 else np.zeros((1, 1), order="F")
+        a = np.zeros(max(n // 2, 1), dtype=np.float64)
+        piv = np.zeros(max(n, 1), dtype=np.int32)
+        logabs = np.zeros(1, dtype=np.float64)
+        sign = np.zeros(1, dtype=np.int32)
+        info = self.lib.oracle_pfaffian_twostep(n, _ptr(X), max(n, 1), _ptr(a), _ptr(piv),
+                                                _ptr(logabs), _ptr(sign))
+        return float(logabs[0]), int(sign[0]), a[: n // 2], piv[:n], int(info)
+
     def skew_rank2k(self, alpha, A, B, beta, C):
         """Copy of C with its strictly lower part := beta C + alpha (A B^T - B A^T)."""
         m, k = A.shape
@@ -175,6 +194,10 @@ def pfaffian_from_factors(n, t, piv):
 
 def pfaffian(A):
     return default().pfaffian(A)
+
+
+def pfaffian_twostep(A):
+    return default().pfaffian_twostep(A)
 
 
 def skew_rank2k(alpha, A, B, beta, C):

@@ -216,6 +216,96 @@ void oracle_skew_tridiag_rankk(int64_t m, int64_t b, double alpha,
         }
 }
 
+/*
+ * oracle_pfaffian_twostep: Pf(X) by the two-step elimination that keeps only what
+ * the Pfaffian needs -- Wimmer's algorithm, as described in the notes to the two-step
+ * right-looking algorithm of Section 4.1: the second Gauss transform of each step
+ * (l_43) and tau_32 are skipped, since only every other sub-diagonal element of T
+ * enters the Pfaffian.  Pivoting as in Section 5.2, at the even steps only.
+ *
+ * For k = 0, 2, 4, ... while k + 1 < n:
+ *   r = (k+1) + iamax(X[k+1:, k]) (lowest index on ties); piv[k+1] = r; exchange
+ *   of indices k+1 and r in X[k:, k:] (as in oracle_ltlt_steps);
+ *   a[k/2] = X[k+1, k];
+ *   with x0 = X[k+2:, k], y = X[k+2:, k+1] and l = x0 / a[k/2] (0 when a[k/2] = 0):
+ *   X[k+2:, k+2:] := X[k+2:, k+2:] + (l y^T - y l^T).
+ * The last statement is the Schur complement S = D + B^T A^{-1} B of the leading
+ * 2 x 2 skew block A = [[0, -a], [a, 0]] in M = [[A, B], [-B^T, D]] (here B^T = -X21,
+ * A^{-1} = [[0, 1/a], [-1/a, 0]], so B^T A^{-1} B = (x0 y^T - y x0^T) / a), and
+ * Pf(M) = Pf(A) Pf(S) = (-a) Pf(S).  With the exchanges, Pf(X) = det(P) prod (-a[j]).
+ *
+ *   n        order of X (n >= 0)
+ *   X, ldx   strictly lower triangle of X, overwritten (destroyed)
+ *   a        floor(n/2) outputs a[j] = tau_{2j+1,2j} of the two-step elimination
+ *   piv      n outputs: piv[k+1] at even k as above, piv[i] = i elsewhere
+ *   logabs, sign   log|Pf(X)| and sign(Pf(X)) (odd n or a zero a[j]: -inf and 0)
+ *
+ * Returns 0, 1 + the first even k with a[k/2] == 0 (Pf = 0; the elimination still
+ * runs to the end with l = 0), ORACLE_ERR_NONFINITE if the strictly lower triangle
+ * holds a NaN or infinity (nothing written), or -1 for a bad argument.
+ */
+int oracle_pfaffian_twostep(int64_t n, double *X, int64_t ldx, double *a, int32_t *piv,
+                            double *logabs, int *sign)
+{
+    if (n < 0 || ldx < (n > 0 ? n : 1)) return -1;
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = j + 1; i < n; ++i)
+            if (!isfinite(X_(i, j))) return ORACLE_ERR_NONFINITE;
+    for (int64_t i = 0; i < n; ++i) piv[i] = (int32_t)i;
+    for (int64_t j = 0; j < n / 2; ++j) a[j] = 0.0;
+
+    int info = 0;
+    for (int64_t k = 0; k + 1 < n; k += 2) {
+        int64_t r = k + 1;
+        double best = fabs(X_(k + 1, k));
+        for (int64_t i = k + 2; i < n; ++i) {
+            double v = fabs(X_(i, k));
+            if (v > best) { best = v; r = i; }   /* strict: lowest index wins ties */
+        }
+        piv[k + 1] = (int32_t)r;
+        if (r != k + 1) {
+            const int64_t u = k + 1, w = r;   /* exchange indices u and w */
+            double sv = X_(u, k); X_(u, k) = X_(w, k); X_(w, k) = sv;
+            for (int64_t i = u + 1; i < w; ++i) {
+                sv = X_(i, u);
+                X_(i, u) = -X_(w, i);
+                X_(w, i) = -sv;
+            }
+            X_(w, u) = -X_(w, u);
+            for (int64_t i = w + 1; i < n; ++i) {
+                sv = X_(i, u); X_(i, u) = X_(i, w); X_(i, w) = sv;
+            }
+        }
+        const double ak = X_(k + 1, k);
+        a[k / 2] = ak;
+        if (ak == 0.0 && info == 0) info = (int)(k + 1);
+        /* l := X[k+2:, k] / a (stored over x0), y = X[k+2:, k+1] */
+        for (int64_t i = k + 2; i < n; ++i)
+            X_(i, k) = (ak != 0.0) ? X_(i, k) / ak : 0.0;
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t j = k + 2; j < n; ++j) {
+            const double lj = X_(j, k), yj = X_(j, k + 1);
+            for (int64_t i = j + 1; i < n; ++i)
+                X_(i, j) = X_(i, j) + (X_(i, k) * yj - X_(i, k + 1) * lj);
+        }
+    }
+
+    if (n % 2 != 0) { *logabs = -INFINITY; *sign = 0; return info; }
+    double s = 0.0;
+    int sg = 1;
+    for (int64_t j = 0; j < n / 2; ++j) {
+        const double v = -a[j];
+        if (v == 0.0) { *logabs = -INFINITY; *sign = 0; return info; }
+        if (v < 0.0) sg = -sg;
+        s += log(fabs(v));
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (piv[i] != (int32_t)i) sg = -sg;   /* det(P) */
+    *logabs = s;
+    *sign = sg;
+    return info;
+}
+
 #ifdef _OPENMP
 #include <omp.h>
 #endif

@@ -239,3 +239,52 @@ def ltlt_blocked(A: np.ndarray, nb: int, fused_w: bool = False):
                 X[s + 1:, s + 1:] += Xp @ Yp.T - Yp @ Xp.T
         k0 = kend
     return L, t, piv
+
+
+def twostep_blocked(A, nb):
+    """Blocked left-looking restatement of the two-step (Pfaffian-only) elimination,
+    in the order the GPU path takes it.  Returns ``(a, piv)``.
+
+    Within a panel of ``nb`` columns (nb/2 pairs), the current matrix is the matrix at
+    the start of the panel plus the panel's rank-2 terms, X + sum_q (l_q y_q^T -
+    y_q l_q^T), so a column is formed left-looking: v = X[:, k] + sum_q (l_q y_q[k] -
+    y_q l_q[k]).  Pair at column k: r = argmax |v[k+1:]| (lowest index on ties),
+    exchange k+1 <-> r in X, in the stored vectors and in v; a = v[k+1];
+    l = v[k+2:] / a; y = column k+1 formed left-looking.  After the panel the trailing
+    block takes sum_q (l_q y_q^T - y_q l_q^T) (one skew rank-2k update)."""
+    n = A.shape[0]
+    X = np.array(A, dtype=np.float64)
+    piv = np.arange(n, dtype=np.int32)
+    a = np.zeros(n // 2)
+    k = 0
+    while k + 1 < n:
+        kend = k + nb
+        ls, ys = [], []
+        while k < kend and k + 1 < n:
+            v = X[:, k].copy()
+            for lq, yq in zip(ls, ys):
+                v += lq * yq[k] - yq * lq[k]
+            r = k + 1 + int(np.argmax(np.abs(v[k + 1:])))
+            piv[k + 1] = r
+            if r != k + 1:
+                sw = [r, k + 1]
+                X[[k + 1, r], :] = X[sw, :]
+                X[:, [k + 1, r]] = X[:, sw]
+                for w in ls + ys + [v]:
+                    w[[k + 1, r]] = w[sw]
+            ak = v[k + 1]
+            a[k // 2] = ak
+            l = np.zeros(n)
+            if ak != 0.0:
+                l[k + 2:] = v[k + 2:] / ak
+            yy = X[:, k + 1].copy()
+            for lq, yq in zip(ls, ys):
+                yy += lq * yq[k + 1] - yq * lq[k + 1]
+            y = np.zeros(n)
+            y[k + 2:] = yy[k + 2:]
+            ls.append(l)
+            ys.append(y)
+            k += 2
+        for lq, yq in zip(ls, ys):
+            X[k:, k:] += np.outer(lq[k:], yq[k:]) - np.outer(yq[k:], lq[k:])
+    return a, piv

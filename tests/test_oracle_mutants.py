@@ -40,6 +40,13 @@ MUTANTS = {
                     "s -= A[j + a * lda] * t[a] * A[i + (a + 1) * lda];"),
     "rankk_sign": ("s -= A[i + a * lda] * t[a] * A[j + (a + 1) * lda];",
                    "s += A[i + a * lda] * t[a] * A[j + (a + 1) * lda];"),
+    "twostep_update_sign": ("(X_(i, k) * yj - X_(i, k + 1) * lj)",
+                            "(X_(i, k + 1) * lj - X_(i, k) * yj)"),
+    "twostep_update_term_dropped": ("(X_(i, k) * yj - X_(i, k + 1) * lj)", "(X_(i, k) * yj)"),
+    "twostep_multiply": ("(ak != 0.0) ? X_(i, k) / ak : 0.0", "(ak != 0.0) ? X_(i, k) * ak : 0.0"),
+    "twostep_swap_no_flip": ("X_(i, u) = -X_(w, i);", "X_(i, u) = X_(w, i);"),
+    "twostep_pf_sign": ("const double v = -a[j];", "const double v = a[j];"),
+    "twostep_no_detP": ("if (piv[i] != (int32_t)i) sg = -sg;", "if (piv[i] < 0) sg = -sg;"),
 }
 
 
@@ -100,7 +107,22 @@ def battery(orc) -> list:
         ok2 = np.allclose(r2[il], (C + A @ Y.T - Y @ A.T)[il], atol=1e-12)
         return ok1 and ok2
 
+    def twostep():
+        for n in (4, 6, 8):
+            for seed in range(2):
+                A = inputs.skew_gaussian(n, 700 + 10 * n + seed)
+                ref = pfaffian_by_definition(A)
+                la, sg, *_ = orc.pfaffian_twostep(A)
+                if sg != (1 if ref > 0 else -1):
+                    return False
+                if not math.isclose(la, math.log(abs(ref)), rel_tol=1e-11, abs_tol=1e-11):
+                    return False
+        A = inputs.skew_gaussian(30, 5)
+        la, sg, *_ = orc.pfaffian_twostep(A)
+        return math.isclose(2 * la, np.linalg.slogdet(A)[1], rel_tol=1e-10)
+
     check("pfaffian_definition", pf_def)
+    check("twostep", twostep)
     check("factors", factors)
     check("ties", ties)
     check("dense_ops", dense_ops)
