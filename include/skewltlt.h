@@ -230,6 +230,44 @@ int skew_pfaffian_ex(int64_t n, double *A, int64_t lda, double *logabs, int32_t 
                      void *workspace, size_t workspace_bytes, void *stream);
 size_t skew_workspace_bytes_ex(int64_t n, int nb, int with_L, int precision);
 
+/*
+ * skew_pfaffian_twostep -- Pf(A) by the two-step (Pfaffian-only) elimination: Wimmer's
+ * algorithm as described in the notes to the two-step right-looking algorithm of
+ * Section 4.1, i.e. the factorization of skew_pfaffian with the second Gauss transform
+ * of every two-step iteration (l_43) and tau_32 skipped, since only every other
+ * sub-diagonal element of T enters the Pfaffian.  Partial pivoting (Section 5.2) at
+ * the even steps only: for k = 0, 2, 4, ...  r = (k+1) + iamax(X[k+1:, k]), exchange
+ * of k+1 and r, a_(k/2) = X[k+1, k], and the Schur complement of the 2 x 2 pivot block,
+ *     X[k+2:, k+2:] += l y^T - y l^T,  l = X[k+2:, k] / a_(k/2),  y = X[k+2:, k+1];
+ * Pf(A) = det(P) prod_j (-a_j).  The same n^3/3 flops as skew_pfaffian, but half the
+ * pivot searches (n/2 grid-wide exchanges instead of n) and no L.  Blocked: a
+ * left-looking panel of nb columns (nb/2 pairs), then one skew rank-2k update of the
+ * trailing block per panel (precision as for skew_pfaffian_ex).
+ *   1  n          order, 0 <= n - 1 <= 256 x (multiprocessors of the device)
+ *   2  A          device, lda x n, column-major; strictly lower triangle read, and
+ *                 overwritten (destroyed) as workspace
+ *   3  lda        >= max(1, n)
+ *   4  logabs     device, 1 double: log|Pf(A)| (-inf when Pf = 0), or NULL
+ *   5  sign       device, 1 int32: sign of Pf(A) in {-1, 0, 1}, or NULL
+ *   6  a          device, n/2 doubles: the pivot-block entries a_j, or NULL
+ *   7  piv        device, n int32: piv[k+1] = r at even k, piv[i] = i elsewhere, or NULL
+ *   8  info       device, 1 int32: 0; 1 + the first even k with a_(k/2) = 0 (Pf = 0);
+ *                 or a negative device error (SKEW_ERR_NONFINITE, SKEW_ERR_TIMEOUT);
+ *                 or NULL
+ *   9  nb         panel width: even, 2 .. 96 (at most 64 with split precision), 0 = 64
+ *   10 precision  SKEW_PRECISION_FP64 or SKEW_PRECISION_SPLIT_BF16
+ *   11 workspace  device, skew_workspace_bytes_twostep(n, nb, precision) bytes, or NULL
+ *   12 workspace_bytes
+ *   13 stream     cudaStream_t (NULL: legacy default stream)
+ * Returns 0 (asynchronous on the stream), -i for a bad argument i (-1 also when n is
+ * too large for one row per thread of the panel: use skew_pfaffian), or a host-side
+ * status (SKEW_ERR_NOMEM, SKEW_ERR_CUDA, SKEW_ERR_NODEVICE).
+ */
+int skew_pfaffian_twostep(int64_t n, double *A, int64_t lda, double *logabs, int32_t *sign,
+                          double *a, int32_t *piv, int32_t *info, int nb, int precision,
+                          void *workspace, size_t workspace_bytes, void *stream);
+size_t skew_workspace_bytes_twostep(int64_t n, int nb, int precision);
+
 /* skew_rank2k with the precision of argument 11 (split: k <= 32). */
 int skew_rank2k_ex(int64_t m, int64_t k, double alpha, const double *X, int64_t ldx,
                    const double *Y, int64_t ldy, double beta, double *C, int64_t ldc,

@@ -50,6 +50,8 @@ SIGNATURES = {
     "skew_workspace_bytes_ex": ([_i64, _i32, _i32, _i32], _sz),
     "skew_rank2k_ex": ([_i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _i32, _vp], _i32),
     "skew_ltlt_batched": ([_i32, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
+    "skew_pfaffian_twostep": ([_i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _vp, _sz, _vp], _i32),
+    "skew_workspace_bytes_twostep": ([_i64, _i32, _i32], _sz),
     "skew_server_create": ([_sz, _i32, _i32, _vp], _i32),
     "skew_server_submit": ([_vp, _i64, _vp, _i64, _i32, _vp], _i32),
     "skew_server_poll": ([_vp, ctypes.c_uint64, _vp], _i32),
@@ -217,6 +219,30 @@ def pfaffian(A, nb: int = 0, stream=None, t=None, piv=None, info=None, workspace
                                 _ptr(info), nb, precision, ws, wsb, _stream_handle(stream))
     _check("skew_pfaffian_ex", st)
     return logabs, sign, t, piv, info
+
+
+def pfaffian_twostep(A, nb: int = 0, stream=None, a=None, piv=None, info=None,
+                     workspace=None, precision: int = PRECISION_FP64):
+    """log|Pf(A)| and sign by the two-step (Pfaffian-only) elimination (A destroyed).
+
+    Returns ``(logabs, sign, a, piv, info)`` CUDA tensors: ``a`` the n/2 pivot-block
+    entries, ``piv`` int32 (n,) with the even-step exchanges.
+    """
+    import torch
+    n = A.shape[0]
+    lda = _colmajor("A", A, n)
+    dev = A.device
+    logabs = torch.empty(1, dtype=torch.float64, device=dev)
+    sign = torch.empty(1, dtype=torch.int32, device=dev)
+    a = torch.empty(max(n // 2, 1), dtype=torch.float64, device=dev) if a is None else a
+    piv = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if piv is None else piv
+    info = torch.empty(1, dtype=torch.int32, device=dev) if info is None else info
+    ws, wsb = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
+    st = lib().skew_pfaffian_twostep(n, _ptr(A) if n > 0 else None, lda, _ptr(logabs),
+                                     _ptr(sign), _ptr(a), _ptr(piv), _ptr(info), nb, precision,
+                                     ws, wsb, _stream_handle(stream))
+    _check("skew_pfaffian_twostep", st)
+    return logabs, sign, a[: n // 2], piv[:n], info
 
 
 def pfaffian_from_factors(t, piv, n: int, stream=None):

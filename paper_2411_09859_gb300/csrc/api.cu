@@ -379,6 +379,106 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
     return status;
 }
 
+// The two-step (Pfaffian-only) elimination: per panel of nb columns (nb/2 pairs), the
+// two-step panel kernel, then one skew rank-2k update of the trailing block with the
+// panel's pairs (l_j, y_j): X[k1:, k1:] += sum_j (l_j y_j^T - y_j l_j^T).
+int factor_twostep(int64_t n, double *A, int64_t lda, double *a, int32_t *piv, int32_t *info,
+                   double *logabs, int32_t *sign, int nb, void *workspace,
+                   size_t workspace_bytes, cudaStream_t st, int precision) {
+    DeviceInfo di;
+    SKEW_TRY_STATUS(current_device_info(&di));
+    if (!twostep_fits(n, nb, di.panel_grid_max)) return -1;
+    const WsLayout lay = workspace_layout(n, nb, false, precision);
+    char *base = static_cast<char *>(workspace);
+    bool own = false;
+    if (base == nullptr) {
+        SKEW_TRY_STATUS(pool_alloc(reinterpret_cast<void **>(&base), lay.total, st));
+        own = true;
+    } else if (workspace_bytes < lay.total) {
+        return -12;
+    }
+    int status = SKEW_OK;
+    Ctrl *ctrl = reinterpret_cast<Ctrl *>(base + lay.ctrl);
+    ArgmaxPartial *part = reinterpret_cast<ArgmaxPartial *>(base + lay.partials);
+    if (a == nullptr) a = reinterpret_cast<double *>(base + lay.tbuf);
+    if (piv == nullptr) piv = reinterpret_cast<int32_t *>(base + lay.pivbuf);
+    double *V = reinterpret_cast<double *>(base + lay.lbuf);     // n x nb
+    do {
+        cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(part, 0, sizeof(ArgmaxPartial) * 2 * kMaxPanelGrid, st);
+        if (e == cudaSuccess && n >= 2) e = cudaMemsetAsync(a, 0, sizeof(double) * (size_t)(n / 2), st);
+        if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+        {
+            ProfScope ps(kProfPrologue, st, 0.0, 8.0 * (double)n * (double)(n - 1) / 2.0);
+            status = launch_prologue(n, A, lda, nullptr, 0, piv, ctrl, st);
+        }
+        if (status != SKEW_OK) break;
+        for (int64_t k0 = 0; k0 + 1 < n && status == SKEW_OK;) {
+            int64_t np = 0;
+            for (int64_t k = k0; k < k0 + nb && k + 1 < n; k += 2) ++np;
+            const int64_t k1 = k0 + 2 * np;                      // first column left
+            TwoStepArgs ta;
+            ta.X = A;
+            ta.ldx = lda;
+            ta.V = V;
+            ta.ldv = n;
+            ta.a = a;
+            ta.piv = piv;
+            ta.ctrl = ctrl;
+            ta.part = part;
+            ta.n = (int)n;
+            ta.k0 = (int)k0;
+            ta.kend = (int)k1;
+            {
+                double pf = 0.0, pb = 0.0;
+                for (int64_t j = 0; j < np; ++j) {
+                    const double rows = (double)(n - k0 - 2 * j - 2);
+                    pf += 2.0 * rows * (double)(4 * j + 2);
+                    pb += 8.0 * rows * 6.0;
+                }
+                ProfScope ps(kProfPanel, st, pf, pb);
+                status = launch_twostep_panel(ta, di.panel_grid_max, st);
+            }
+            if (status != SKEW_OK) break;
+            const int64_t m = n - k1;
+            if (m >= 2) {
+                Skr2kArgs sa;
+                sa.m = m;
+                sa.C = A + k1 + k1 * lda;
+                sa.ldc = lda;
+                sa.alpha = 1.0;
+                sa.beta = 1.0;
+                sa.P = V + k1;                  // l_j: column 2j
+                sa.ldp = 2 * n;
+                sa.Q = V + n + k1;              // y_j: column 2j+1
+                sa.ldq = 2 * n;
+                sa.tt = nullptr;
+                sa.x = nullptr;
+                sa.b = np;
+                ProfScope ps(kProfSkr2k, st, skr2k_flops(m, np), skr2k_bytes(m));
+                if (precision == SKEW_PRECISION_SPLIT_BF16)
+                    status = launch_skr2k_split(PairKind::Rank2k, sa, base + lay.split, &ctrl->err,
+                                                di.sms, st);
+                else
+                    status = launch_skr2k(PairKind::Rank2k, sa, st);
+            }
+            k0 = k1;
+        }
+        if (status != SKEW_OK) break;
+        ProfScope ps(kProfFinish, st, 0.0, 12.0 * (double)n);
+        status = launch_finish_twostep(n, a, piv, ctrl, logabs, sign, info, st);
+    } while (0);
+    if (own) {
+        cudaError_t e = cudaFreeAsync(base, st);
+        if (e != cudaSuccess && status == SKEW_OK) {
+            set_last_error(e);
+            status = SKEW_ERR_CUDA;
+        }
+    }
+    return status;
+}
+
 }  // namespace
 }  // namespace skew
 
@@ -742,6 +842,29 @@ int skew_ltlt_batched(int count, const skew_problem *problems, double *logabs,
         }
     }
     return status;
+}
+
+size_t skew_workspace_bytes_twostep(int64_t n, int nb, int precision) {
+    if (n < 0) return 0;
+    if (nb <= 0) nb = 64;
+    if (nb > kMaxNb) nb = kMaxNb;
+    return workspace_layout(n, nb, false, precision).total;
+}
+
+int skew_pfaffian_twostep(int64_t n, double *A, int64_t lda, double *logabs, int32_t *sign,
+                          double *a, int32_t *piv, int32_t *info, int nb, int precision,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    if (n < 0 || n > kMaxOrder) return -1;
+    const int64_t ld_min = n > 1 ? n : 1;
+    if (A == nullptr && n > 0) return -2;
+    if (lda < ld_min) return -3;
+    if (nb == 0) nb = 64;
+    if (nb < 2 || nb > 96 || (nb & 1)) return -9;
+    if (precision != SKEW_PRECISION_FP64 && precision != SKEW_PRECISION_SPLIT_BF16) return -10;
+    if (precision == SKEW_PRECISION_SPLIT_BF16 && nb > 64) return -9;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return factor_twostep(n, A, lda, a, piv, info, logabs, sign, nb, workspace, workspace_bytes,
+                          st, precision);
 }
 
 int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,

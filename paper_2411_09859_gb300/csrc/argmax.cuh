@@ -1,0 +1,87 @@
+// argmax.cuh -- the pivot search of the panel kernels: candidates (|v|, row) compared
+// as integers, reduced within a warp and within a CTA.
+#pragma once
+
+#include <climits>
+
+#include "common.cuh"
+
+namespace skew {
+namespace {
+
+// Pivot candidates are compared on the bits of |v| as unsigned integers (for
+// non-negative IEEE doubles the order of the bit patterns is the order of the
+// values), then on the row index: larger magnitude wins, the lower index wins a tie.
+// FP64 instructions are avoided because they are slow on this part.  A NaN is never
+// a candidate.  (0, INT_MAX) is the "no candidate" value: any real entry beats it,
+// since |v| > 0 is larger and |v| == 0 wins on the index.
+constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
+constexpr unsigned long long kExpMask = 0x7ff0000000000000ull;
+
+__device__ __forceinline__ bool finite_bits(unsigned long long raw) {
+    return (raw & kExpMask) != kExpMask;
+}
+
+struct Best {
+    unsigned long long raw;   // bits of the signed v
+    int i;                    // row
+    int c;                    // CTA that published it
+};
+
+__device__ __forceinline__ bool better(unsigned long long ra, int ia, unsigned long long rb,
+                                       int ib) {
+    const unsigned long long a = ra & kAbsMask, b = rb & kAbsMask;
+    return (a > b) || (a == b && ia < ib);
+}
+
+__device__ __forceinline__ Best no_candidate() {
+    Best b;
+    b.raw = 0ull;
+    b.i = INT_MAX;
+    b.c = 0;
+    return b;
+}
+
+// Offer row i with value v; NaN is skipped.
+__device__ __forceinline__ void offer(Best &b, double v, int i) {
+    const unsigned long long raw = (unsigned long long)__double_as_longlong(v);
+    if ((raw & kAbsMask) > kExpMask) return;          // NaN
+    if (better(raw, i, b.raw, b.i)) { b.raw = raw; b.i = i; }
+}
+
+__device__ __forceinline__ Best warp_best(Best x) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long orw = __shfl_down_sync(0xffffffffu, x.raw, off);
+        const int oi = __shfl_down_sync(0xffffffffu, x.i, off);
+        const int oc = __shfl_down_sync(0xffffffffu, x.c, off);
+        if (better(orw, oi, x.raw, x.i)) { x.raw = orw; x.i = oi; x.c = oc; }
+    }
+    return x;
+}
+
+// Reduce one Best per thread; the result is valid in every thread on return.
+__device__ Best block_best(Best x) {
+    __shared__ unsigned long long s_raw[kPanelThreads / 32];
+    __shared__ int s_i[kPanelThreads / 32];
+    __shared__ Best s_res;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    x = warp_best(x);
+    if (lane == 0) { s_raw[w] = x.raw; s_i[w] = x.i; }
+    __syncthreads();
+    if (w == 0) {
+        Best y = no_candidate();
+        if (lane < kPanelThreads / 32) { y.raw = s_raw[lane]; y.i = s_i[lane]; }
+        y = warp_best(y);
+        if (lane == 0) s_res = y;
+    }
+    __syncthreads();
+    return s_res;
+}
+
+__device__ __forceinline__ double as_double(unsigned long long raw) {
+    return __longlong_as_double((long long)raw);
+}
+
+}  // namespace
+}  // namespace skew

@@ -55,6 +55,8 @@ struct Ctrl {
     double vtop[2];           // panel: v[k+1] of step k (slot k & 1), before the exchange
     double pad1[4];
     double rowp[2][kMaxNb];   // panel: L[k+1, k0+1..k] of step k (slot k & 1)
+    double vnext[2];          // two-step panel: v[k+2] of pair step j (slot j & 1)
+    double rowq[2][kMaxNb];   // two-step panel: stored row k+2 of pair step j (slot j & 1)
 };
 
 // One per panel CTA and step parity: the CTA's best candidate row of the step and
@@ -208,6 +210,29 @@ int launch_skr2k(PairKind kind, const Skr2kArgs &a, cudaStream_t stream);
 size_t split_scratch_bytes(int64_t m);
 int launch_skr2k_split(PairKind kind, const Skr2kArgs &a, void *scratch, int *err, int sms,
                        cudaStream_t stream);
+
+// Two-step (Pfaffian-only) panel (twostep.cu): pairs at columns k = k0, k0+2, ... <
+// kend (and k + 1 < n).  V (ldv x (kend-k0)) receives l_j (column 2j) and y_j
+// (column 2j+1) of pair j for rows k+2 .. n-1; a[k/2] and piv[k+1] are written.
+struct TwoStepArgs {
+    double *X;
+    int64_t ldx;
+    double *V;
+    int64_t ldv;
+    double *a;
+    int32_t *piv;
+    Ctrl *ctrl;
+    ArgmaxPartial *part;
+    int n, k0, kend;
+};
+// Returns SKEW_ERR_CUDA if the rows do not fit the shared-memory organisation
+// (n - k0 - 1 > sms * kPanelThreads or kend - k0 > 96); callers check first.
+int launch_twostep_panel(const TwoStepArgs &a, int sms, cudaStream_t stream);
+bool twostep_fits(int64_t n, int nb, int sms);
+// log|Pf| = sum log|a_j|, sign = det(P) prod sign(-a_j); info as for the one-step path
+// but over the a_j (1 + the first even k with a[k/2] == 0).
+int launch_finish_twostep(int64_t n, const double *a, const int32_t *piv, const Ctrl *ctrl,
+                          double *logabs, int32_t *sign, int32_t *info, cudaStream_t stream);
 
 // Batched persistent factorization (batched.cu).
 size_t batched_workspace_bytes(int count, int max_n);
