@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-precision", action="store_true")
+    ap.add_argument("--skip-twostep", action="store_true",
+                    help="skip the Pfaffian-only (two-step and one-step) leg")
     ap.add_argument("--qdq-n", type=int, default=2048)
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-poisson", type=int, default=500)
@@ -483,6 +485,60 @@ def run_reference(args):
     return 0
 
 
+def run_twostep_leg(skew, inputs, torch, dev, A_host, steps: int, warmup: int):
+    """The Pfaffian-only forms on the same n x n matrix: skew_pfaffian_twostep (the
+    two-step elimination, pivot searches at even steps only) and skew_pfaffian (the
+    one-step factorization without L), each with the FP64 and the split-precision
+    trailing update; timed like the main leg, with the per-kernel split and the
+    agreement of their log|Pf| (the two eliminations pivot differently)."""
+    n = A_host.shape[0]
+    pristine = torch.from_numpy(A_host).to(dev)
+    work = skew.fortran_empty(n, n, dev)
+    stream = torch.cuda.Stream(device=dev)
+    flops = factorization_flops(n)
+    out = {"metric": "Pfaffian TFLOP/s (n^3/3 counted) by the two-step elimination",
+           "unit": "TFLOP/s", "nb": 64}
+    vals = {}
+    for algo in ("twostep", "one_step"):
+        for pname, prec in (("fp64", skew.PRECISION_FP64), ("split", skew.PRECISION_SPLIT_BF16)):
+            times = []
+            for i in range(warmup + steps):
+                work.copy_(pristine)
+                torch.cuda.synchronize()
+                if i == warmup:
+                    skew.profile_read()
+                    skew.profile_enable(True)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if algo == "twostep":
+                    la, sg, *_ = skew.pfaffian_twostep(work, nb=64, stream=stream, precision=prec)
+                else:
+                    la, sg, *_ = skew.pfaffian(work, nb=64, stream=stream, precision=prec)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if i >= warmup:
+                    times.append(e0.elapsed_time(e1))
+            prof = skew.profile_read()
+            skew.profile_enable(False)
+            ms = statistics.median(times)
+            vals[(algo, pname)] = (float(la.item()), int(sg.item()))
+            out.setdefault(algo, {})[pname] = {
+                "ms_per_step": ms, "value": flops / (ms / 1e3) / 1e12,
+                "kernels": {k: {"ms_per_step": v["ms"] / steps, "launches_per_step": v["launches"] / steps}
+                            for k, v in prof.items() if v["launches"]}}
+    ref = vals[("one_step", "fp64")]
+    out["value"] = out["twostep"]["fp64"]["value"]
+    out["log_abs_pf"] = {f"{a}_{p}": v[0] for (a, p), v in vals.items()}
+    out["max_rel_diff_vs_one_step_fp64"] = max(abs(v[0] - ref[0]) / abs(ref[0]) for v in vals.values())
+    out["signs_equal"] = all(v[1] == ref[1] for v in vals.values())
+    out["speedup_vs_one_step"] = {p: out["one_step"][p]["ms_per_step"] / out["twostep"][p]["ms_per_step"]
+                                  for p in ("fp64", "split")}
+    del pristine, work
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -601,6 +657,10 @@ def run_ours(args):
                                       t.cpu().numpy(), piv.cpu().numpy(), steps=2, warmup=1,
                                       n_qdq=args.qdq_n)
 
+    twostep = None
+    if not args.skip_twostep:
+        twostep = run_twostep_leg(skew, inputs, torch, dev, A_host, steps=2, warmup=1)
+
     batched = None
     if not args.skip_batched:
         batched = run_batched_leg(skew, inputs, torch, dev, steps=3, warmup=1,
@@ -633,6 +693,7 @@ def run_ours(args):
             "kernels": kernels,
             "e2e": e2e,
             "precision": precision,
+            "pfaffian_only": twostep,
             "batched": batched,
             "serving": serving,
             "cpu_baseline": cpu,
