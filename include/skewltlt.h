@@ -347,6 +347,22 @@ int skew_ltlt_batched(int count, const skew_problem *problems, double *logabs,
                       size_t workspace_bytes, void *stream);
 
 /*
+ * skew_pfaffian_batched -- the Pfaffians of `count` independent skew matrices by the
+ * two-step elimination of skew_pfaffian_twostep, each matrix factored in place by one
+ * CTA of a persistent kernel (largest orders first): panels of 16 columns (8 pairs)
+ * formed left-looking in shared memory, one skew rank-2k update per panel on FP64
+ * tensor cores.  Arguments as for skew_ltlt_batched, with these differences: max_n
+ * <= 512; problem j's `t` (n/2 doubles, required for n >= 2) receives the pivot-block
+ * entries a_i and its `piv` (n int32) the even-step exchanges; its `L` is not used;
+ * info[j] = 1 + the first even k with a_(k/2) = 0 (Pf = 0), -100 for a non-finite
+ * entry, -2 for a bad descriptor.
+ */
+int skew_pfaffian_batched(int count, const skew_problem *problems, double *logabs,
+                          int32_t *sign, int32_t *info, int max_n, void *workspace,
+                          size_t workspace_bytes, void *stream);
+
+
+/*
  * Serving form: a continuous-batching server of factorizations / Pfaffians.
  *
  * skew_server_submit queues a request (an order-n skew matrix in device memory) and

@@ -50,6 +50,7 @@ SIGNATURES = {
     "skew_workspace_bytes_ex": ([_i64, _i32, _i32, _i32], _sz),
     "skew_rank2k_ex": ([_i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _i32, _vp], _i32),
     "skew_ltlt_batched": ([_i32, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
+    "skew_pfaffian_batched": ([_i32, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
     "skew_pfaffian_twostep": ([_i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _vp, _sz, _vp], _i32),
     "skew_workspace_bytes_twostep": ([_i64, _i32, _i32], _sz),
     "skew_server_create": ([_sz, _i32, _i32, _vp], _i32),
@@ -361,6 +362,32 @@ def ltlt_batched(As, want_L: bool = False, stream=None, max_n: int | None = None
     _check("skew_ltlt_batched", st)
     return logabs, sign, info, ts, pivs, Ls
 
+
+
+def pfaffian_batched(As, stream=None, max_n: int | None = None, table=None, outs=None):
+    """Pfaffians of the column-major float64 CUDA tensors ``As`` (destroyed) by the
+    two-step elimination, one launch (orders <= 512).  Returns ``(logabs, sign,
+    info, as_, pivs)``: per-problem CUDA tensors and the lists of pivot-block entries
+    (n/2 each) and even-step pivots.  ``table``/``outs`` as for :func:`ltlt_batched`
+    (``outs = (as_, pivs)``)."""
+    import torch
+    count = len(As)
+    dev = As[0].device if count else torch.device("cuda")
+    if outs is None:
+        as_ = [torch.empty(max(A.shape[0] // 2, 1), dtype=torch.float64, device=dev) for A in As]
+        pivs = [torch.empty(max(A.shape[0], 1), dtype=torch.int32, device=dev) for A in As]
+    else:
+        as_, pivs = outs
+    if table is None:
+        table = problem_table(As, [None] * count, as_, pivs, dev)
+    logabs = torch.empty(count, dtype=torch.float64, device=dev)
+    sign = torch.empty(count, dtype=torch.int32, device=dev)
+    info = torch.empty(count, dtype=torch.int32, device=dev)
+    mx = max((A.shape[0] for A in As), default=0) if max_n is None else max_n
+    st = lib().skew_pfaffian_batched(count, _ptr(table) if count else None, _ptr(logabs),
+                                     _ptr(sign), _ptr(info), mx, None, 0, _stream_handle(stream))
+    _check("skew_pfaffian_batched", st)
+    return logabs, sign, info, as_, pivs
 
 
 class Server:

@@ -867,6 +867,39 @@ int skew_pfaffian_twostep(int64_t n, double *A, int64_t lda, double *logabs, int
                           st, precision);
 }
 
+int skew_pfaffian_batched(int count, const skew_problem *problems, double *logabs,
+                          int32_t *sign, int32_t *info, int max_n, void *workspace,
+                          size_t workspace_bytes, void *stream) {
+    if (count < 0) return -1;
+    if (problems == nullptr && count > 0) return -2;
+    if (max_n < 0 || max_n > 512) return -6;
+    const size_t need = batched_workspace_bytes(count, max_n);
+    if (workspace != nullptr && workspace_bytes < need) return -8;
+    if (count == 0) return SKEW_OK;
+    DeviceInfo di;
+    SKEW_TRY_STATUS(current_device_info(&di));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *ws = workspace;
+    bool own = false;
+    if (ws == nullptr) {
+        SKEW_TRY_STATUS(pool_alloc(&ws, need, st));
+        own = true;
+    }
+    int status;
+    {
+        ProfScope ps(kProfBatched, st, 0.0, 0.0);
+        status = launch_batched_twostep(count, problems, logabs, sign, info, max_n, ws, st, di.sms);
+    }
+    if (own) {
+        cudaError_t e = cudaFreeAsync(ws, st);
+        if (e != cudaSuccess && status == SKEW_OK) {
+            set_last_error(e);
+            status = SKEW_ERR_CUDA;
+        }
+    }
+    return status;
+}
+
 int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
                    int64_t ldl, double *t_host, int32_t *piv_host, double *logabs,
                    int32_t *sign, int32_t *info, int nb) {

@@ -537,6 +537,245 @@ __device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_
     __syncthreads();
 }
 
+// ------------------------------------------------------------------------------------
+// Pfaffian-only batched variant: the two-step elimination (only the even-step Gauss
+// transforms; each pair of columns removed by the Schur complement of its 2 x 2 skew
+// pivot block; notes to the two-step right-looking algorithm, Section 4.1), blocked
+// inside one CTA: panels of kBlkNb columns (kBlkNb/2 pairs) formed left-looking from
+// the panel's vectors kept in shared memory, then one skew rank-2k update
+// X[k1:, k1:] += sum_j (l_j y_j^T - y_j l_j^T) on FP64 DMMA.  Half the pivot searches
+// (and CTA barriers) of factor_one_blocked and no W.  P.t receives the n/2 pivot-block
+// entries a_j, P.piv the even-step exchanges (identity elsewhere); P.L is not used.
+// smem: Vp[kBlkNb][nmax] (c = 2q: l_q, 2q+1: y_q), sv[nmax].
+// ------------------------------------------------------------------------------------
+__device__ void pfaff_one_twostep(const skew_problem &P, double *logabs, int32_t *sign,
+                                  int32_t *info, double *smem, int nmax, BlkShared &sh,
+                                  BatchShared &fin) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+    const int n = (int)P.n;
+    double *X = P.A;
+    const int64_t ldx = P.lda;
+    double *aout = P.t;
+    int32_t *piv = P.piv;
+    double *Vp = smem;                                  // Vp[c * nmax + i]
+    double *sv = smem + (size_t)kBlkNb * nmax;
+
+    for (int i = tid; i < n; i += nthr) piv[i] = i;
+    bool nonfinite = false;
+    __syncthreads();
+
+    for (int k0 = 0; k0 + 1 < n;) {
+        int np = 0;
+        for (int k = k0; k < k0 + kBlkNb && k + 1 < n; k += 2) ++np;
+        for (int j = 0; j < np; ++j) {
+            const int k = k0 + 2 * j, nc = 2 * j, p = k + 1;
+            // v = X[:, k] + sum_c Vp[c][i] h[c]:  h[2q] = y_q[k], h[2q+1] = -l_q[k]
+            for (int c = tid; c < nc; c += nthr)
+                sh.h[c] = (c & 1) ? -Vp[(size_t)(c - 1) * nmax + k] : Vp[(size_t)(c + 1) * nmax + k];
+            __syncthreads();
+            const double *colk = X + (int64_t)k * ldx;
+            Cand cd;
+            cd.raw = 0ull;
+            cd.i = INT_MAX;
+            bool bad = false;
+            for (int i = p + tid; i < n; i += nthr) {
+                double v = colk[i];
+                for (int c = 0; c < nc; ++c) v += Vp[(size_t)c * nmax + i] * sh.h[c];
+                sv[i] = v;
+                const unsigned long long raw = (unsigned long long)__double_as_longlong(v);
+                if ((raw & kExp) == kExp) { bad = true; continue; }
+                if (cand_better(raw, i, cd.raw, cd.i)) { cd.raw = raw; cd.i = i; }
+            }
+            bool any_bad;
+            const Cand best = blk_cand(cd, bad, sh, any_bad);
+            nonfinite |= any_bad;
+            const int r = (best.i == INT_MAX) ? p : best.i;
+            if (r != p) {
+                // exchange of indices p and r in X[p:, p:] (lower storage), in the panel's
+                // vectors and in v
+                double *colp = X + (int64_t)p * ldx;
+                for (int i = p + 1 + tid; i < n; i += nthr) {
+                    if (i < r) {
+                        double *xri = X + (int64_t)i * ldx + r;
+                        const double tmp = colp[i];
+                        colp[i] = -*xri;
+                        *xri = -tmp;
+                    } else if (i == r) {
+                        colp[i] = -colp[i];
+                    } else {
+                        double *colr = X + (int64_t)r * ldx;
+                        const double tmp = colp[i];
+                        colp[i] = colr[i];
+                        colr[i] = tmp;
+                    }
+                }
+                for (int c = tid; c < nc; c += nthr) {
+                    const double tmp = Vp[(size_t)c * nmax + p];
+                    Vp[(size_t)c * nmax + p] = Vp[(size_t)c * nmax + r];
+                    Vp[(size_t)c * nmax + r] = tmp;
+                }
+                if (tid == 0) {
+                    const double tmp = sv[p];
+                    sv[p] = sv[r];
+                    sv[r] = tmp;
+                }
+            }
+            __syncthreads();
+            const double a = sv[p];
+            if (tid == 0) {
+                aout[k / 2] = a;
+                piv[p] = r;
+            }
+            // y = X[:, k+1] + sum_c Vp[c][i] h[c] with h from the new row k+1;  l = v / a
+            for (int c = tid; c < nc; c += nthr)
+                sh.t[c] = (c & 1) ? -Vp[(size_t)(c - 1) * nmax + p] : Vp[(size_t)(c + 1) * nmax + p];
+            __syncthreads();
+            const double *colp = X + (int64_t)p * ldx;
+            for (int i = p + 1 + tid; i < n; i += nthr) {
+                double y = colp[i];
+                for (int c = 0; c < nc; ++c) y += Vp[(size_t)c * nmax + i] * sh.t[c];
+                Vp[(size_t)nc * nmax + i] = (a != 0.0) ? sv[i] / a : 0.0;
+                Vp[(size_t)(nc + 1) * nmax + i] = y;
+            }
+            __syncthreads();
+        }
+        const int k1 = k0 + 2 * np;
+        const int m = n - k1;
+        if (m >= 2) {
+            // C = X[k1:, k1:] += sum_q (l_q y_q^T - y_q l_q^T): U = [l | -y], V = [y | l]
+            const int K = 2 * np;
+            const int K4 = (K + 3) / 4 * 4;
+            const int nt = (m + 31) / 32;
+            const int ntiles = nt * (nt + 1) / 2;
+            const int g = lane >> 2, tg = lane & 3;
+            for (int tile = warp; tile < ntiles; tile += nwarps) {
+                int bi = 0;
+                while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
+                const int bj = tile - bi * (bi + 1) / 2;
+                double acc[4][4][2];
+#pragma unroll
+                for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+                    for (int ni = 0; ni < 4; ++ni) acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
+                for (int kb = 0; kb < K4; kb += 4) {
+                    const int kc = kb + tg;
+                    double af[4], bf[4];
+#pragma unroll
+                    for (int mi = 0; mi < 4; ++mi) {
+                        const int li = bi * 32 + mi * 8 + g;
+                        const int i = k1 + li;
+                        double u = 0.0;
+                        if (li < m && kc < K)
+                            u = kc < np ? Vp[(size_t)(2 * kc) * nmax + i]
+                                        : -Vp[(size_t)(2 * (kc - np) + 1) * nmax + i];
+                        af[mi] = u;
+                    }
+#pragma unroll
+                    for (int ni = 0; ni < 4; ++ni) {
+                        const int lj = bj * 32 + ni * 8 + g;
+                        const int j = k1 + lj;
+                        double v = 0.0;
+                        if (lj < m && kc < K)
+                            v = kc < np ? Vp[(size_t)(2 * kc + 1) * nmax + j]
+                                        : Vp[(size_t)(2 * (kc - np)) * nmax + j];
+                        bf[ni] = v;
+                    }
+#pragma unroll
+                    for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+                        for (int ni = 0; ni < 4; ++ni)
+                            dmma884(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
+                }
+#pragma unroll
+                for (int mi = 0; mi < 4; ++mi) {
+                    const int li = bi * 32 + mi * 8 + g;
+#pragma unroll
+                    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+                        for (int cc = 0; cc < 2; ++cc) {
+                            const int lj = bj * 32 + ni * 8 + 2 * tg + cc;
+                            if (li < m && lj < m && li > lj) {
+                                double *dst = X + (int64_t)(k1 + lj) * ldx + (k1 + li);
+                                *dst = *dst + acc[mi][ni][cc];
+                            }
+                        }
+                }
+            }
+        }
+        __syncthreads();
+        k0 = k1;
+    }
+
+    // ---- Pf = det(P) prod_j (-a_j), fixed reduction order
+    double sum = 0.0;
+    int par = 0, first_zero = INT_MAX;
+    const int half = n / 2;
+    for (int j = tid; j < half; j += nthr) {
+        const double v = -aout[j];
+        if (v == 0.0) {
+            if (j < first_zero) first_zero = j;
+        } else {
+            if (v < 0.0) par ^= 1;
+            sum += log(fabs(v));
+        }
+    }
+    for (int i = tid; i < n; i += nthr)
+        if (piv[i] != i) par ^= 1;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        sum += __shfl_down_sync(0xffffffffu, sum, off);
+        par ^= __shfl_down_sync(0xffffffffu, par, off);
+        first_zero = min(first_zero, __shfl_down_sync(0xffffffffu, first_zero, off));
+    }
+    if (lane == 0) {
+        fin.w_sum[warp] = sum;
+        fin.w_par[warp] = par;
+        fin.w_i[warp] = first_zero;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double sm = 0.0;
+        int pr = 0, fz = INT_MAX;
+        for (int w = 0; w < nwarps; ++w) {
+            sm += fin.w_sum[w];
+            pr ^= fin.w_par[w];
+            fz = min(fz, fin.w_i[w]);
+        }
+        const bool pf_zero = (n & 1) || fz != INT_MAX;
+        if (logabs) *logabs = pf_zero ? -INFINITY : sm;
+        if (sign) *sign = pf_zero ? 0 : (pr ? -1 : 1);
+        if (info) *info = nonfinite ? SKEW_ERR_NONFINITE : (fz == INT_MAX ? 0 : 2 * fz + 1);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBlkThreads, 2)
+batched_twostep_kernel(int count, const skew_problem *problems, const int32_t *order,
+                       unsigned int *counter, double *logabs, int32_t *sign, int32_t *info,
+                       int max_n) {
+    extern __shared__ double s_blk[];
+    __shared__ BlkShared sh;
+    __shared__ BatchShared fin;
+    for (;;) {
+        if (threadIdx.x == 0) fin.item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int item = fin.item;
+        __syncthreads();
+        if (item >= count) return;
+        const int b = order[item];
+        const skew_problem P = problems[b];
+        const int n = (int)P.n;
+        if (n < 0 || n > max_n || (n > 0 && P.A == nullptr) || P.lda < (n > 1 ? n : 1) ||
+            (n > 1 && P.t == nullptr) || (n > 0 && P.piv == nullptr)) {
+            if (threadIdx.x == 0 && info) info[b] = -2;
+            continue;
+        }
+        pfaff_one_twostep(P, logabs ? logabs + b : nullptr, sign ? sign + b : nullptr,
+                          info ? info + b : nullptr, s_blk, max_n > 1 ? max_n : 1, sh, fin);
+    }
+}
+
 __global__ void __launch_bounds__(kBlkThreads, 2)
 batched_blocked_kernel(int count, const skew_problem *problems, const int32_t *order,
                        unsigned int *counter, double *logabs, int32_t *sign, int32_t *info,
@@ -621,6 +860,42 @@ order_kernel(int count, const skew_problem *problems, int max_n, int32_t *order,
 }
 
 }  // namespace
+
+int launch_batched_twostep(int count, const skew_problem *problems, double *logabs,
+                           int32_t *sign, int32_t *info, int max_n, void *ws,
+                           cudaStream_t stream, int sms) {
+    if (max_n > kBlkMaxN) return SKEW_ERR_CUDA;            // callers check
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    char *base = static_cast<char *>(ws);
+    unsigned int *counter = reinterpret_cast<unsigned int *>(base);
+    int32_t *order = reinterpret_cast<int32_t *>(base + al(sizeof(unsigned int)));
+    unsigned int *hist = reinterpret_cast<unsigned int *>(
+        base + al(sizeof(unsigned int)) + al(sizeof(int32_t) * (size_t)(count > 0 ? count : 1)));
+    order_kernel<<<1, 1024, 0, stream>>>(count, problems, max_n, order, counter, hist);
+    note_launches(1);
+    SKEW_TRY_STATUS(check_launch());
+    const size_t nm = (size_t)(max_n > 1 ? max_n : 1);
+    const size_t smem = sizeof(double) * nm * (kBlkNb + 1);
+    cudaError_t e = cudaFuncSetAttribute((const void *)batched_twostep_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        set_last_error(e);
+        return SKEW_ERR_CUDA;
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_twostep_kernel,
+                                                      kBlkThreads, smem);
+    if (e != cudaSuccess || per_sm < 1) {
+        if (e != cudaSuccess) set_last_error(e);
+        return SKEW_ERR_CUDA;
+    }
+    int grid = sms * per_sm;
+    if (grid > count) grid = count;
+    batched_twostep_kernel<<<grid, kBlkThreads, smem, stream>>>(count, problems, order, counter,
+                                                                logabs, sign, info, max_n);
+    note_launches(1);
+    return check_launch();
+}
 
 size_t batched_workspace_bytes(int count, int max_n) {
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };

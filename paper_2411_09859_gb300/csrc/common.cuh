@@ -238,6 +238,10 @@ int launch_finish_twostep(int64_t n, const double *a, const int32_t *piv, const 
 size_t batched_workspace_bytes(int count, int max_n);
 int launch_batched(int count, const skew_problem *problems, double *logabs, int32_t *sign,
                    int32_t *info, int max_n, void *ws, cudaStream_t stream, int sms);
+// Pfaffian-only batched variant (two-step elimination), max_n <= 512.
+int launch_batched_twostep(int count, const skew_problem *problems, double *logabs,
+                           int32_t *sign, int32_t *info, int max_n, void *ws,
+                           cudaStream_t stream, int sms);
 
 // Self-test of the bounded waits: `blocks` CTAs enter a grid barrier that expects one
 // more CTA than launched, so it can only end by its time limit.

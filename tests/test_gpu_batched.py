@@ -135,3 +135,64 @@ def test_blocked_kernel_zero_pivots_and_ties():
     la, sg, info, ts, pivs, Ls = run_batch([D, I], True)
     check_against_oracle(D, la[0], sg[0], info[0], ts[0], pivs[0], Ls[0])
     check_against_oracle(I, la[1], sg[1], info[1], ts[1], pivs[1], Ls[1])
+
+
+# ------------------------------------------------ Pfaffian-only (two-step) batched form
+def run_pf_batch(mats):
+    As = [dev(A) for A in mats]
+    la, sg, info, as_, pivs = skew.pfaffian_batched(As)
+    torch.cuda.synchronize()
+    return (la.cpu().numpy(), sg.cpu().numpy(), info.cpu().numpy(),
+            [a.cpu().numpy() for a in as_], [p.cpu().numpy() for p in pivs])
+
+
+def check_twostep(A, la, sg, info, a, piv):
+    n = A.shape[0]
+    la0, sg0, a0, p0, i0 = oracle.pfaffian_twostep(A)
+    assert np.array_equal(piv[:n], p0)
+    assert info == i0 and sg == sg0
+    if n >= 2:
+        assert np.max(np.abs(a[: n // 2] - a0)) <= TOL_C * n * EPS * max(1e-300, np.max(np.abs(a0)))
+    if sg0 != 0:
+        assert abs(la - la0) <= 1e-10 * max(1.0, abs(la0))
+
+
+def test_pfaffian_batched_mixed_orders_against_oracle():
+    rng = np.random.default_rng(77)
+    sizes = [0, 1, 2, 3, 5, 16, 17, 31, 33, 64, 100, 129, 255, 256, 300, 511, 512] + \
+        [int(x) for x in rng.integers(2, 257, size=40)]
+    mats = [inputs.skew_gaussian(n, 2000 + i) for i, n in enumerate(sizes)]
+    la, sg, info, as_, pivs = run_pf_batch(mats)
+    for b, A in enumerate(mats):
+        if A.shape[0] == 0:
+            assert sg[b] == 1 and la[b] == 0.0
+            continue
+        check_twostep(A, la[b], sg[b], info[b], as_[b], pivs[b])
+
+
+def test_pfaffian_batched_equals_single_two_step_and_one_step():
+    mats = [inputs.skew_gaussian(n, 3100 + n) for n in (40, 96, 200, 256)]
+    la, sg, info, as_, pivs = run_pf_batch(mats)
+    for b, A in enumerate(mats):
+        l1, s1, a1, p1, i1 = skew.pfaffian_twostep(dev(A), nb=16)
+        l2, s2, *_ = skew.pfaffian(dev(A))
+        torch.cuda.synchronize()
+        assert np.array_equal(pivs[b], p1.cpu().numpy())
+        assert int(s1.item()) == sg[b] == int(s2.item())
+        assert abs(la[b] - float(l1.item())) <= 1e-12 * max(1.0, abs(la[b]))
+        assert abs(la[b] - float(l2.item())) <= 1e-10 * max(1.0, abs(la[b]))
+
+
+def test_pfaffian_batched_zero_pivots_nonfinite_and_bad_descriptor():
+    D = inputs.block_diag_skew([2.0, -1.0, 4.0])
+    Z = np.zeros((6, 6))
+    B = inputs.skew_gaussian(20, 4)
+    B[13, 2] = np.nan
+    la, sg, info, as_, pivs = run_pf_batch([D, Z, B])
+    assert sg[0] == -1 and math.isclose(la[0], math.log(8.0), rel_tol=1e-15)
+    assert np.array_equal(as_[0][:3], [-2.0, 1.0, -4.0])
+    assert sg[1] == 0 and info[1] == 1
+    assert info[2] == -100
+    As = [dev(inputs.skew_gaussian(8, 1))]
+    with pytest.raises(skew.SkewError):
+        skew.pfaffian_batched(As, max_n=513)
