@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-precision", action="store_true")
+    ap.add_argument("--qdq-full-n", type=int, default=16384,
+                    help="order of the device-generated QDQ^T check (0: skip)")
     ap.add_argument("--skip-twostep", action="store_true",
                     help="skip the Pfaffian-only (two-step and one-step) leg")
     ap.add_argument("--qdq-n", type=int, default=2048)
@@ -288,7 +290,7 @@ def run_batched_leg(skew, inputs, torch, dev, steps: int, warmup: int, plain_cou
 
 # ----------------------------------------------------------------------------- precision
 def run_precision_leg(skew, inputs, torch, dev, A_host, nb_fp64, fp64_ms, fp64_t, fp64_piv,
-                      steps: int, warmup: int, n_qdq: int):
+                      steps: int, warmup: int, n_qdq: int, n_full: int = 0):
     """The precision form: the same n = 16384 matrix with the trailing update run as
     split-precision bf16 tensor-core products (panel, pivots, division, t and
     log|Pf| in FP64), timed like the FP64 run, compared with it (pivots, log|Pf|);
@@ -353,6 +355,35 @@ def run_precision_leg(skew, inputs, torch, dev, A_host, nb_fp64, fp64_ms, fp64_t
                      "rel_err_vs_closed_form": abs(la - closed) / abs(closed),
                      "rel_err_vs_oracle": abs(la - la_o) / abs(la_o),
                      "pivots_equal_oracle": bool(np.array_equal(pq.cpu().numpy(), p0))}
+    # the precision workload at full order: QDQ^T generated on the device
+    full = None
+    if n_full > 0:
+        tg0 = time.perf_counter()
+        Af, s_full, detQ = inputs.qdq_skew_device(n_full, inputs.SEED_PRECISION, smax=1e6,
+                                                  device=dev)
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - tg0
+        closed_f = float(np.sum(np.log(s_full)))
+        full = {"n": n_full, "closed_form_log_abs_pf": closed_f, "closed_form_sign": detQ,
+                "generation_s": gen_s,
+                "generator": "device QR of a seeded Gaussian (torch), sign(diag R) correction; "
+                             "Pf = det(Q) prod s"}
+        work_f = skew.fortran_empty(n_full, n_full, dev)
+        for name, prec in (("fp64_dmma", skew.PRECISION_FP64), ("split_bf16", split)):
+            for algo in ("one_step", "twostep"):
+                work_f.copy_(Af)
+                torch.cuda.synchronize()
+                if algo == "one_step":
+                    la, sg, *_ = skew.pfaffian(work_f, nb=64, precision=prec)
+                else:
+                    la, sg, *_ = skew.pfaffian_twostep(work_f, nb=64, precision=prec)
+                torch.cuda.synchronize()
+                la = float(la.item())
+                full[f"{name}_{algo}"] = {"log_abs_pf": la, "sign": int(sg.item()),
+                                          "sign_ok": int(sg.item()) == detQ,
+                                          "rel_err_vs_closed_form": abs(la - closed_f) / abs(closed_f)}
+        del Af, work_f
+        torch.cuda.empty_cache()
     flops = factorization_flops(n)
     return {"metric": "skew LTLt TFLOP/s (n^3/3) with the split-precision trailing update",
             "value": flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
@@ -362,10 +393,12 @@ def run_precision_leg(skew, inputs, torch, dev, A_host, nb_fp64, fp64_ms, fp64_t
                             "log_abs_pf_fp64": la_f, "log_abs_pf_split": la_s,
                             "rel_diff": abs(la_s - la_f) / abs(la_f), "sign_equal": int(sg_f.item()) == int(sg_s.item()),
                             "max_rel_t_diff": float(np.max(np.abs(t_s - fp64_t)) / np.max(np.abs(fp64_t)))},
+            "qdq_full_order": full,
             "qdq": {"n": n_qdq, "closed_form_log_abs_pf": closed, "oracle_log_abs_pf": la_o,
                     "oracle_rel_err_vs_closed_form": abs(la_o - closed) / abs(closed), **acc,
-                    "note": "QDQ^T workload run at a reduced order: its O(n^3) host generation "
-                            "at n = 16384 would dominate the run"}}
+                    "note": "QDQ^T at a reduced order against the CPU oracle (host generation); "
+                            "qdq_full_order: the same workload at full order, generated on the "
+                            "device, against its closed form"}}
 
 
 # ----------------------------------------------------------------------------- serving
@@ -682,7 +715,7 @@ def run_ours(args):
     if not args.skip_precision:
         precision = run_precision_leg(skew, inputs, torch, dev, A_host, nb, ms / K,
                                       t.cpu().numpy(), piv.cpu().numpy(), steps=2, warmup=1,
-                                      n_qdq=args.qdq_n)
+                                      n_qdq=args.qdq_n, n_full=args.qdq_full_n)
 
     twostep = None
     if not args.skip_twostep:

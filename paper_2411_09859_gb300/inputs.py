@@ -87,6 +87,43 @@ def qdq_skew(n: int, seed: int, smax: float = 1e6):
     return np.asfortranarray((M - M.T) / 2.0), s
 
 
+def qdq_skew_device(n: int, seed: int, smax: float = 1e6, device="cuda"):
+    """A = Q D Q^T generated on the device, for orders whose host generation would take
+    minutes (n = 16384).  G: n x n standard normal from a torch generator seeded with
+    `seed` (not the numpy stream of `qdq_skew`); Q: the Householder QR of G with the
+    sign(diag R) correction (Haar); D = block_diag_skew(log_spaced_s(n, smax)).
+    A = U V^T - V U^T with U = Q[:, 0::2] * s and V = Q[:, 1::2] (= Q D Q^T, exactly
+    skew).  det(Q) = (-1)^(number of nonzero reflectors) * prod sign(R_ii).
+
+    Returns (A, s, detQ): A a column-major float64 CUDA tensor, s (numpy), detQ in
+    {-1, +1}; Pf(A) = detQ * prod(s)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    G = torch.randn((n, n), generator=gen, dtype=torch.float64, device=device)
+    H, tau = torch.geqrf(G)
+    del G
+    dR = torch.diagonal(H).clone()
+    Q = torch.linalg.householder_product(H, tau)
+    sgn = torch.where(dR < 0, -1.0, 1.0).to(torch.float64)
+    Q *= sgn.unsqueeze(0)
+    nneg = int((dR < 0).sum().item())
+    nref = int((tau != 0).sum().item())
+    detQ = -1 if (nneg + nref) % 2 else 1
+    del H, tau
+    s = log_spaced_s(n, smax)
+    st = torch.from_numpy(s).to(device)
+    U = Q[:, 0::2] * st.unsqueeze(0)
+    V = Q[:, 1::2].contiguous()
+    del Q
+    M = U @ V.t()
+    del U, V
+    A = torch.empty((n, n), dtype=torch.float64, device=device).t()   # column-major
+    A.copy_(M - M.t())
+    del M
+    return A, s, detQ
+
+
 def batched_sizes(count: int = 4096, seed: int = SEED_BATCH_SIZES, lo: int = 16,
                   hi: int = 256) -> np.ndarray:
     """count even orders drawn uniformly from {lo, lo+2, ..., hi}."""

@@ -275,3 +275,16 @@ def test_generator_is_skew_and_seeded():
     sz = inputs.batched_sizes(1000)
     assert sz.min() >= 16 and sz.max() <= 256 and np.all(sz % 2 == 0)
     assert full_skew_from_lower(A).tolist() == A.tolist()
+
+
+def test_device_qdq_generator_closed_form_on_cpu(orc):
+    """The device QDQ^T generator (used at n = 16384), run on the CPU: exactly skew,
+    Pf = det(Q) prod s with det(Q) read off the Householder reflectors."""
+    torch = pytest.importorskip("torch")
+    for n, seed in ((12, 3), (40, 5), (64, 9)):
+        A, s, detQ = inputs.qdq_skew_device(n, seed, smax=1e3, device="cpu")
+        A = A.numpy()
+        assert np.array_equal(A, -A.T)
+        la, sg = orc.pfaffian(np.asfortranarray(A))
+        assert sg == detQ
+        assert math.isclose(la, float(np.sum(np.log(s))), rel_tol=1e-10)
