@@ -109,8 +109,17 @@ int skew_profile_read(skew_kernel_stat *stats /* SKEW_KIND_COUNT entries */);
  * usable afterwards. */
 int skew_selftest_bounded_wait(double timeout_s, int32_t *status);
 
-/* Panel width used when `nb` is 0 for a matrix of order n. */
+/* Panel width used when `nb` is 0 for a matrix of order n: from the table installed
+ * by skew_set_nb_table, else 16 (n <= 256), 32 (n <= 2048), 64. */
 int skew_default_nb(int64_t n);
+
+/* Installs a panel-width table (typically an autotuner's measurements on this device):
+ * orders n <= n_upper[i] (the first such i; n_upper strictly increasing) take nb[i]
+ * (1 .. 256), larger orders the last entry.  count = 0 restores the built-in rule.
+ * The paper has no counterpart (its block size is a parameter of the C++ routine,
+ * Section 5.2); here it only chooses the default of `nb = 0`.  Thread safe.
+ * Returns 0, or -1 / -2 / -3 for a bad count / n_upper / nb. */
+int skew_set_nb_table(int count, const int64_t *n_upper, const int32_t *nb);
 
 /*
  * Device workspace, in bytes, that skew_ltlt / skew_pfaffian need for order n and

@@ -36,6 +36,7 @@ SIGNATURES = {
     "skew_profile_enable": ([_i32], _i32),
     "skew_profile_read": ([_vp], _i32),
     "skew_default_nb": ([_i64], _i32),
+    "skew_set_nb_table": ([_i32, _vp, _vp], _i32),
     "skew_workspace_bytes": ([_i64, _i32, _i32], _sz),
     "skew_ltlt": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
     "skew_pfaffian": ([_i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
@@ -95,8 +96,22 @@ def lib():
                 fn = getattr(L, name)
                 fn.argtypes = args
                 fn.restype = res
+            _install_saved_nb_table(L)
             _lib = L
         return _lib
+
+
+def _install_saved_nb_table(L):
+    """Install the autotuner's saved panel-width table (nb_table.json), if present."""
+    import json
+    path = os.path.join(_HERE, "nb_table.json")
+    if not os.path.exists(path):
+        return
+    with open(path) as f:
+        table = json.load(f)["table"]
+    nu = (ctypes.c_int64 * max(len(table), 1))(*[int(a) for a, _ in table])
+    nbs = (ctypes.c_int32 * max(len(table), 1))(*[int(b) for _, b in table])
+    L.skew_set_nb_table(len(table), ctypes.cast(nu, ctypes.c_void_p), ctypes.cast(nbs, ctypes.c_void_p))
 
 
 def _check(fn: str, status: int):
@@ -162,6 +177,16 @@ def kernel_launches() -> int:
 
 def default_nb(n: int) -> int:
     return int(lib().skew_default_nb(n))
+
+
+def set_nb_table(table):
+    """Install ``[(n_upper, nb), ...]`` (increasing n_upper) as the default panel widths;
+    an empty list restores the built-in rule."""
+    count = len(table)
+    nu = (ctypes.c_int64 * max(count, 1))(*[int(a) for a, _ in table])
+    nbs = (ctypes.c_int32 * max(count, 1))(*[int(b) for _, b in table])
+    _check("skew_set_nb_table", lib().skew_set_nb_table(count, ctypes.cast(nu, ctypes.c_void_p),
+                                                         ctypes.cast(nbs, ctypes.c_void_p)))
 
 
 def workspace_bytes(n: int, nb: int = 0, with_L: bool = True) -> int:

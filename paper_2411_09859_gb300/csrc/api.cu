@@ -492,7 +492,37 @@ const char *skew_last_error(void) { return g_last_error; }
 
 uint64_t skew_kernel_launches(void) { return g_launches.load(); }
 
+// Panel-width table installed by skew_set_nb_table (an autotuner's result), else the
+// built-in rule.  Guarded by a mutex: installs are rare, reads take a snapshot.
+namespace {
+std::mutex g_nb_mutex;
+std::vector<std::pair<int64_t, int>> g_nb_table;
+}  // namespace
+
+int skew_set_nb_table(int count, const int64_t *n_upper, const int32_t *nb) {
+    if (count < 0) return -1;
+    if (count > 0 && (n_upper == nullptr)) return -2;
+    if (count > 0 && (nb == nullptr)) return -3;
+    std::vector<std::pair<int64_t, int>> t;
+    for (int i = 0; i < count; ++i) {
+        if (nb[i] < 1 || nb[i] > kMaxNb) return -3;
+        if (i > 0 && n_upper[i] <= n_upper[i - 1]) return -2;
+        t.emplace_back(n_upper[i], nb[i]);
+    }
+    std::lock_guard<std::mutex> lock(g_nb_mutex);
+    g_nb_table.swap(t);
+    return SKEW_OK;
+}
+
 int skew_default_nb(int64_t n) {
+    {
+        std::lock_guard<std::mutex> lock(g_nb_mutex);
+        if (!g_nb_table.empty()) {
+            for (const auto &e : g_nb_table)
+                if (n <= e.first) return e.second;
+            return g_nb_table.back().second;
+        }
+    }
     if (n <= 256) return 16;
     if (n <= 2048) return 32;
     return 64;

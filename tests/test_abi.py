@@ -88,3 +88,34 @@ def test_oracle_never_touches_product():
         if path.endswith((".py", ".c")):
             text = open(path).read()
             assert "paper_2411_09859_gb300" not in text and "skewltlt" not in text, path
+
+
+def test_nb_table_install_and_reset():
+    """The panel-width table of the autotuner (host-only functions, no device work)."""
+    import paper_2411_09859_gb300 as skew
+    lib = skew.lib()
+    before = [skew.default_nb(n) for n in (100, 1000, 5000, 20000)]
+    try:
+        skew.set_nb_table([(1000, 24), (8000, 48), (16384, 96)])
+        assert [skew.default_nb(n) for n in (100, 1000, 1001, 8000, 9000, 16384, 50000)] == \
+            [24, 24, 48, 48, 96, 96, 96]
+        with pytest.raises(skew.SkewError):
+            skew.set_nb_table([(1000, 24), (900, 48)])       # not increasing
+        with pytest.raises(skew.SkewError):
+            skew.set_nb_table([(1000, 0)])                   # bad width
+        skew.set_nb_table([])
+        assert [skew.default_nb(n) for n in (100, 1000, 5000)] == [16, 32, 64]
+    finally:
+        from paper_2411_09859_gb300 import autotune
+        if not autotune.load():
+            skew.set_nb_table([])
+    assert [skew.default_nb(n) for n in (100, 1000, 5000, 20000)] == before
+    assert lib.skew_set_nb_table(-1, None, None) == -1
+
+
+def test_autotune_pick_rule():
+    from paper_2411_09859_gb300 import autotune
+    assert autotune.pick({"32": 10.0, "64": 9.99, "96": 9.98}) == 32      # all within 0.5 %
+    assert autotune.pick({"32": 10.0, "64": 9.0, "96": 8.99}) == 64
+    assert autotune.table_from_ms({"4096": {"32": 1.0, "64": 2.0}, "512": {"16": 3.0, "32": 1.0}}) == \
+        [(512, 32), (4096, 32)]
