@@ -359,8 +359,12 @@ def problem_table(As, Ls, ts, pivs, device):
     return host.to(device)
 
 
+def batched_workspace_bytes(count: int, max_n: int) -> int:
+    return int(lib().skew_batched_workspace_bytes(count, max_n))
+
+
 def ltlt_batched(As, want_L: bool = False, stream=None, max_n: int | None = None,
-                 table=None, outs=None):
+                 table=None, outs=None, workspace=None):
     """Factor every column-major float64 CUDA tensor of the list ``As`` (destroyed) in
     one batched launch.  Returns ``(logabs, sign, info, ts, pivs, Ls)``: per-problem
     CUDA tensors (logabs float64 (count,), sign/info int32 (count,)) and lists of the
@@ -382,14 +386,16 @@ def ltlt_batched(As, want_L: bool = False, stream=None, max_n: int | None = None
     sign = torch.empty(count, dtype=torch.int32, device=dev)
     info = torch.empty(count, dtype=torch.int32, device=dev)
     mx = max((A.shape[0] for A in As), default=0) if max_n is None else max_n
+    ws, wsb = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
     st = lib().skew_ltlt_batched(count, _ptr(table) if count else None, _ptr(logabs),
-                                 _ptr(sign), _ptr(info), mx, None, 0, _stream_handle(stream))
+                                 _ptr(sign), _ptr(info), mx, ws, wsb, _stream_handle(stream))
     _check("skew_ltlt_batched", st)
     return logabs, sign, info, ts, pivs, Ls
 
 
 
-def pfaffian_batched(As, stream=None, max_n: int | None = None, table=None, outs=None):
+def pfaffian_batched(As, stream=None, max_n: int | None = None, table=None, outs=None,
+                     workspace=None, results=None):
     """Pfaffians of the column-major float64 CUDA tensors ``As`` (destroyed) by the
     two-step elimination, one launch (orders <= 512).  Returns ``(logabs, sign,
     info, as_, pivs)``: per-problem CUDA tensors and the lists of pivot-block entries
@@ -405,12 +411,16 @@ def pfaffian_batched(As, stream=None, max_n: int | None = None, table=None, outs
         as_, pivs = outs
     if table is None:
         table = problem_table(As, [None] * count, as_, pivs, dev)
-    logabs = torch.empty(count, dtype=torch.float64, device=dev)
-    sign = torch.empty(count, dtype=torch.int32, device=dev)
-    info = torch.empty(count, dtype=torch.int32, device=dev)
+    if results is None:
+        logabs = torch.empty(count, dtype=torch.float64, device=dev)
+        sign = torch.empty(count, dtype=torch.int32, device=dev)
+        info = torch.empty(count, dtype=torch.int32, device=dev)
+    else:
+        logabs, sign, info = results
     mx = max((A.shape[0] for A in As), default=0) if max_n is None else max_n
+    ws, wsb = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
     st = lib().skew_pfaffian_batched(count, _ptr(table) if count else None, _ptr(logabs),
-                                     _ptr(sign), _ptr(info), mx, None, 0, _stream_handle(stream))
+                                     _ptr(sign), _ptr(info), mx, ws, wsb, _stream_handle(stream))
     _check("skew_pfaffian_batched", st)
     return logabs, sign, info, as_, pivs
 
