@@ -79,6 +79,33 @@ __device__ Best block_best(Best x) {
     return s_res;
 }
 
+// A panel CTA's step record {val, idx, tag} (the first 16 bytes of its ArgmaxPartial)
+// is written and read as ONE 128-bit access, so a reader that sees the step's tag has
+// that step's candidate in the same load (no second round trip).
+__device__ __forceinline__ void record_poll(const ArgmaxPartial *p, unsigned long long &val,
+                                            unsigned int &idx, unsigned int &tag) {
+    unsigned long long lo, hi;
+    asm volatile(
+        "{\n\t.reg .b128 t;\n\tld.relaxed.gpu.global.b128 t, [%2];\n\t"
+        "mov.b128 {%0, %1}, t;\n\t}"
+        : "=l"(lo), "=l"(hi)
+        : "l"(p)
+        : "memory");
+    val = lo;
+    idx = (unsigned int)(hi & 0xffffffffull);
+    tag = (unsigned int)(hi >> 32);
+}
+__device__ __forceinline__ void record_release(ArgmaxPartial *p, unsigned long long val, int idx,
+                                               unsigned int tag) {
+    const unsigned long long hi =
+        ((unsigned long long)tag << 32) | (unsigned long long)(unsigned int)idx;
+    asm volatile(
+        "{\n\t.reg .b128 t;\n\tmov.b128 t, {%1, %2};\n\t"
+        "st.release.gpu.global.b128 [%0], t;\n\t}" ::"l"(p),
+        "l"(val), "l"(hi)
+        : "memory");
+}
+
 __device__ __forceinline__ double as_double(unsigned long long raw) {
     return __longlong_as_double((long long)raw);
 }

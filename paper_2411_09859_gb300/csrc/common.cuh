@@ -61,10 +61,11 @@ struct Ctrl {
 
 // One per panel CTA and step parity: the CTA's best candidate row of the step and
 // that row's L values in the panel columns formed so far.
-struct ArgmaxPartial {
+struct __align__(16) ArgmaxPartial {
     double val;               // signed v at the CTA's best row
     int idx;                  // that row (INT32_MAX if none)
-    unsigned int tag;         // shared-memory panel: step tag released after the rest
+    unsigned int tag;         // shared-memory panels: step tag; val, idx, tag are written
+                              // and read together as one 128-bit access
     double row[kMaxNb];       // L[idx, k0+1 .. k]
 };
 constexpr int64_t kMaxOrder = int64_t(1) << 22;   // keeps every tile count below 2^31

@@ -300,14 +300,10 @@ panel_smem_kernel(PanelArgs a) {
             for (int q = tid; q < nq; q += blockDim.x)
                 ctrl->rowp[k & 1][q] = s_L[q * kPanelThreads + ot];
         }
-        if (tid == 0) {
-            sp->val = as_double(best.raw);
-            sp->idx = best.i;
-        }
         __syncthreads();
         // release: the CTA's writes above (ordered before by the barrier) become
-        // visible to any CTA that acquires the tag
-        if (tid == 0) st_release_u32_gpu(&sp->tag, base + (unsigned int)(k - k0) + 1u);
+        // visible to any CTA that sees the tag; candidate and tag in one 128-bit store
+        if (tid == 0) record_release(sp, best.raw, best.i, base + (unsigned int)(k - k0) + 1u);
     };
 
     // ---------------- step k0: v = X[k0+1:, k0]
@@ -342,12 +338,21 @@ panel_smem_kernel(PanelArgs a) {
             unsigned int polls = 0;
             // relaxed loads, all in flight at once (acquire loads would serialise);
             // the fence after the loop turns the observed tags into an acquire
+            unsigned long long pv[kPer];
+            unsigned int pi[kPer];
             while (pending != 0u) {
 #pragma unroll
                 for (int j = 0; j < kPer; ++j)
-                    if ((pending >> j) & 1u)
-                        if (ld_relaxed_u32(&slot(k, tid + 32 * j)->tag) == want)
+                    if ((pending >> j) & 1u) {
+                        unsigned long long rv;
+                        unsigned int ri, rt;
+                        record_poll(slot(k, tid + 32 * j), rv, ri, rt);
+                        if (rt == want) {
                             pending &= ~(1u << j);
+                            pv[j] = rv;
+                            pi[j] = ri;
+                        }
+                    }
                 if (pending == 0u) break;
                 // the error word and the clock are looked at every 16th pass only, so
                 // that a pass is one round of loads
@@ -368,12 +373,10 @@ panel_smem_kernel(PanelArgs a) {
 #pragma unroll
                 for (int j = 0; j < kPer; ++j) {
                     const int c = tid + 32 * j;
-                    if (c < G) {
-                        const ArgmaxPartial *sp = slot(k, c);
-                        const unsigned long long pr =
-                            (unsigned long long)__double_as_longlong(__ldcg(&sp->val));
-                        const int pi = __ldcg(&sp->idx);
-                        if (better(pr, pi, b.raw, b.i)) { b.raw = pr; b.i = pi; b.c = c; }
+                    if (c < G && better(pv[j], (int)pi[j], b.raw, b.i)) {
+                        b.raw = pv[j];
+                        b.i = (int)pi[j];
+                        b.c = c;
                     }
                 }
             }

@@ -98,12 +98,8 @@ twostep_panel_kernel(TwoStepArgs A) {
                 ctrl->rowq[j & 1][c] = s_S[c * kPanelThreads + ot];
             if (tid == ot) ctrl->vnext[j & 1] = v;
         }
-        if (tid == 0) {
-            sp->val = as_double(best.raw);
-            sp->idx = best.i;
-        }
         __syncthreads();
-        if (tid == 0) st_release_gpu(&sp->tag, base + (unsigned int)j + 1u);
+        if (tid == 0) record_release(sp, best.raw, best.i, base + (unsigned int)j + 1u);
     };
 
     // ---------------- pair step 0: v = X[k0+1:, k0]
@@ -136,12 +132,21 @@ twostep_panel_kernel(TwoStepArgs A) {
             int fail = 0;
             uint64_t t0 = 0;
             unsigned int polls = 0;
+            unsigned long long pv[kPer];
+            unsigned int pi[kPer];
             while (pending != 0u) {
 #pragma unroll
                 for (int q = 0; q < kPer; ++q)
-                    if ((pending >> q) & 1u)
-                        if (ld_relaxed_u32(&slot(j, tid + 32 * q)->tag) == want)
+                    if ((pending >> q) & 1u) {
+                        unsigned long long rv;
+                        unsigned int ri, rt;
+                        record_poll(slot(j, tid + 32 * q), rv, ri, rt);
+                        if (rt == want) {
                             pending &= ~(1u << q);
+                            pv[q] = rv;
+                            pi[q] = ri;
+                        }
+                    }
                 if (pending == 0u) break;
                 if ((++polls & 15u) == 0u) {
                     if (ld_volatile_i32(&ctrl->err) != 0) { fail = 1; break; }
@@ -160,12 +165,10 @@ twostep_panel_kernel(TwoStepArgs A) {
 #pragma unroll
                 for (int q = 0; q < kPer; ++q) {
                     const int c = tid + 32 * q;
-                    if (c < G) {
-                        const ArgmaxPartial *sp = slot(j, c);
-                        const unsigned long long pr =
-                            (unsigned long long)__double_as_longlong(__ldcg(&sp->val));
-                        const int pi = __ldcg(&sp->idx);
-                        if (better(pr, pi, b.raw, b.i)) { b.raw = pr; b.i = pi; b.c = c; }
+                    if (c < G && better(pv[q], (int)pi[q], b.raw, b.i)) {
+                        b.raw = pv[q];
+                        b.i = (int)pi[q];
+                        b.c = c;
                     }
                 }
             }
