@@ -121,6 +121,16 @@ int skew_default_nb(int64_t n);
  * Returns 0, or -1 / -2 / -3 for a bad count / n_upper / nb. */
 int skew_set_nb_table(int count, const int64_t *n_upper, const int32_t *nb);
 
+/* Panel width (8, 16 or 32) of the CTA-local batched kernels (skew_ltlt_batched for
+ * orders <= 512, skew_pfaffian_batched) per order bucket: a matrix of order
+ * n <= n_upper[i] (first such i; strictly increasing, count <= 8) takes nb[i], larger
+ * ones the last entry; count = 0 restores 16 for every order.  Typically the batched
+ * autotuner's result.  No counterpart in the paper.  Thread safe; returns 0, or -1 /
+ * -2 / -3 for a bad count / n_upper / nb.  skew_get_batched_nb(n) reports the width an
+ * order takes. */
+int skew_set_batched_nb_table(int count, const int32_t *n_upper, const int32_t *nb);
+int skew_get_batched_nb(int n);
+
 /*
  * Device workspace, in bytes, that skew_ltlt / skew_pfaffian need for order n and
  * panel width nb (0 = default).  `with_L` = 0 gives the figure for skew_pfaffian,

@@ -37,6 +37,8 @@ SIGNATURES = {
     "skew_profile_read": ([_vp], _i32),
     "skew_default_nb": ([_i64], _i32),
     "skew_set_nb_table": ([_i32, _vp, _vp], _i32),
+    "skew_set_batched_nb_table": ([_i32, _vp, _vp], _i32),
+    "skew_get_batched_nb": ([_i32], _i32),
     "skew_workspace_bytes": ([_i64, _i32, _i32], _sz),
     "skew_ltlt": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
     "skew_pfaffian": ([_i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
@@ -108,10 +110,15 @@ def _install_saved_nb_table(L):
     if not os.path.exists(path):
         return
     with open(path) as f:
-        table = json.load(f)["table"]
+        saved = json.load(f)
+    table = saved.get("table", [])
     nu = (ctypes.c_int64 * max(len(table), 1))(*[int(a) for a, _ in table])
     nbs = (ctypes.c_int32 * max(len(table), 1))(*[int(b) for _, b in table])
     L.skew_set_nb_table(len(table), ctypes.cast(nu, ctypes.c_void_p), ctypes.cast(nbs, ctypes.c_void_p))
+    bt = saved.get("batched_table", [])
+    bu = (ctypes.c_int32 * max(len(bt), 1))(*[int(a) for a, _ in bt])
+    bn = (ctypes.c_int32 * max(len(bt), 1))(*[int(b) for _, b in bt])
+    L.skew_set_batched_nb_table(len(bt), ctypes.cast(bu, ctypes.c_void_p), ctypes.cast(bn, ctypes.c_void_p))
 
 
 def _check(fn: str, status: int):
@@ -177,6 +184,21 @@ def kernel_launches() -> int:
 
 def default_nb(n: int) -> int:
     return int(lib().skew_default_nb(n))
+
+
+def set_batched_nb_table(table):
+    """Install ``[(n_upper, nb), ...]`` (nb in 8, 16, 32) as the batched kernels' panel
+    width per order bucket; an empty list restores 16."""
+    count = len(table)
+    nu = (ctypes.c_int32 * max(count, 1))(*[int(a) for a, _ in table])
+    nbs = (ctypes.c_int32 * max(count, 1))(*[int(b) for _, b in table])
+    _check("skew_set_batched_nb_table",
+           lib().skew_set_batched_nb_table(count, ctypes.cast(nu, ctypes.c_void_p),
+                                           ctypes.cast(nbs, ctypes.c_void_p)))
+
+
+def batched_nb(n: int) -> int:
+    return int(lib().skew_get_batched_nb(n))
 
 
 def set_nb_table(table):

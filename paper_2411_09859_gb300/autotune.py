@@ -1,6 +1,7 @@
 """Panel-width autotuner: times the factorization on this device for candidate panel
 widths at a set of orders, and installs the fastest width per order range as the
-library's default (skew_set_nb_table).  The result is saved as JSON beside this file
+library's default (skew_set_nb_table); likewise the batched kernels' panel width per
+order bucket (skew_set_batched_nb_table), timed on batches of that bucket.  The result is saved as JSON beside this file
 (``nb_table.json``) and installed again by the package at import.
 
     python -m paper_2411_09859_gb300.autotune [--sizes 512,2048,4096,8192,16384]
@@ -68,6 +69,96 @@ def tune(sizes=(512, 2048, 4096, 8192, 16384), candidates=(32, 48, 64, 96), reps
             "ms": {str(n): {str(b): v for b, v in d.items()} for n, d in ms.items()}}
 
 
+BUCKETS = (64, 128, 256, 512)      # order buckets of the batched kernels
+BATCHED_NB = (8, 16, 32)
+
+
+def _batch(sizes, seed_base: int):
+    """Device buffers of one batch of iid skew matrices of the given orders."""
+    import numpy as np
+    import torch
+
+    from . import _native as nat
+    from . import inputs
+    mats = [inputs.skew_gaussian(int(n), seed_base + i) for i, n in enumerate(sizes)]
+    offs = np.concatenate([[0], np.cumsum(np.asarray(sizes, dtype=np.int64) ** 2)])
+    flat = np.empty(int(offs[-1]))
+    for i, A in enumerate(mats):
+        flat[offs[i]:offs[i + 1]] = A.ravel(order="F")
+    pristine = torch.from_numpy(flat).cuda()
+    work = torch.empty_like(pristine)
+    views = [work[int(offs[i]):int(offs[i + 1])].view(int(n), int(n)).t()
+             for i, n in enumerate(sizes)]
+    ts = [torch.empty(max(int(n) - 1, 1), dtype=torch.float64, device="cuda") for n in sizes]
+    pivs = [torch.empty(max(int(n), 1), dtype=torch.int32, device="cuda") for n in sizes]
+    table = nat.problem_table(views, [None] * len(views), ts, pivs, "cuda")
+    return pristine, work, views, ts, pivs, table
+
+
+def measure_batched_mix(sizes, table_nb, reps: int = 2, batch=None) -> float:
+    """Median milliseconds of skew_ltlt_batched plus skew_pfaffian_batched on one batch
+    of the given orders, with the bucket table `table_nb` installed."""
+    import torch
+
+    from . import _native as nat
+    pristine, work, views, ts, pivs, table = batch or _batch(sizes, 50000)
+    mx = int(max(sizes))
+    nat.set_batched_nb_table(table_nb)
+    stream = torch.cuda.Stream()
+    total = 0.0
+    for fn in (lambda: nat.ltlt_batched(views, stream=stream, max_n=mx, table=table,
+                                        outs=(ts, pivs, [None] * len(views))),
+               lambda: nat.pfaffian_batched(views, stream=stream, max_n=mx, table=table,
+                                            outs=(ts, pivs))):
+        times = []
+        for i in range(reps + 1):
+            work.copy_(pristine)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i > 0:
+                times.append(e0.elapsed_time(e1))
+        total += statistics.median(times)
+    return total
+
+
+def tune_batched(sizes=None, buckets=BUCKETS, candidates=BATCHED_NB, reps: int = 2):
+    """The batched kernels' width per order bucket, chosen on a workload mix (default:
+    the batched workload, 4096 orders even in [16, 256]): every combination of widths
+    over the buckets the mix populates is timed (both batched kernels, summed) and the
+    fastest kept; a bucket the mix does not reach takes the fastest width on a batch of
+    its own orders."""
+    import itertools
+
+    from . import inputs
+    if sizes is None:
+        sizes = inputs.batched_sizes(4096)
+    sizes = [int(n) for n in sizes]
+    batch = _batch(sizes, 50000)
+    lows = [16] + [b + 2 for b in buckets[:-1]]
+    used = [hi for lo, hi in zip(lows, buckets) if any(lo <= n <= hi for n in sizes)]
+    mix_ms = {}
+    for combo in itertools.product(candidates, repeat=len(used)):
+        tab = [(hi, nb) for hi, nb in zip(used, combo)]
+        mix_ms[combo] = measure_batched_mix(sizes, tab, reps, batch)
+    best = dict(zip(used, min(mix_ms, key=mix_ms.get)))
+    del batch
+    extra = {}
+    for lo, hi in zip(lows, buckets):
+        if hi in best:
+            continue
+        own = [lo + 2 * ((hi - lo) // 4)] * 256
+        extra[hi] = {nb: measure_batched_mix(own, [(hi, nb)], reps) for nb in candidates}
+        best[hi] = pick(extra[hi])
+    return {"batched_table": [(hi, best[hi]) for hi in buckets],
+            "batched_mix_ms": {",".join(map(str, k)): v for k, v in mix_ms.items()},
+            "batched_mix_buckets": used,
+            "batched_own_ms": {str(h): {str(b): v for b, v in d.items()} for h, d in extra.items()}}
+
+
 def save(result, path: str = TABLE_PATH):
     import torch
     out = dict(result)
@@ -77,13 +168,14 @@ def save(result, path: str = TABLE_PATH):
 
 
 def load(path: str = TABLE_PATH) -> bool:
-    """Install a saved table if there is one; returns whether it did."""
+    """Install saved tables if there are any; returns whether it did."""
     if not os.path.exists(path):
         return False
     with open(path) as f:
-        table = [tuple(e) for e in json.load(f)["table"]]
+        saved = json.load(f)
     from . import _native as nat
-    nat.set_nb_table(table)
+    nat.set_nb_table([tuple(e) for e in saved.get("table", [])])
+    nat.set_batched_nb_table([tuple(e) for e in saved.get("batched_table", [])])
     return True
 
 
@@ -93,11 +185,20 @@ def main():
     ap.add_argument("--candidates", default="32,48,64,96")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--no-save", action="store_true")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="tune only the batched kernels' widths (keep the saved panel table)")
     args = ap.parse_args()
-    res = tune([int(x) for x in args.sizes.split(",")], [int(x) for x in args.candidates.split(",")],
-               args.reps)
     from . import _native as nat
-    nat.set_nb_table(res["table"])
+    res = {}
+    if os.path.exists(TABLE_PATH):
+        with open(TABLE_PATH) as f:
+            res = json.load(f)
+    if not args.batched_only:
+        res.update(tune([int(x) for x in args.sizes.split(",")],
+                        [int(x) for x in args.candidates.split(",")], args.reps))
+        nat.set_nb_table(res["table"])
+    res.update(tune_batched(reps=args.reps))
+    nat.set_batched_nb_table(res["batched_table"])
     if not args.no_save:
         save(res)
     print(json.dumps(res))

@@ -482,6 +482,18 @@ int factor_twostep(int64_t n, double *A, int64_t lda, double *a, int32_t *piv, i
 }  // namespace
 }  // namespace skew
 
+namespace skew {
+namespace {
+std::mutex g_bnb_mutex;
+BatchedNb g_bnb = {0, {0}, {0}};
+}  // namespace
+
+BatchedNb batched_nb_table() {
+    std::lock_guard<std::mutex> lock(g_bnb_mutex);
+    return g_bnb;
+}
+}  // namespace skew
+
 using namespace skew;
 
 extern "C" {
@@ -512,6 +524,26 @@ int skew_set_nb_table(int count, const int64_t *n_upper, const int32_t *nb) {
     std::lock_guard<std::mutex> lock(g_nb_mutex);
     g_nb_table.swap(t);
     return SKEW_OK;
+}
+
+int skew_set_batched_nb_table(int count, const int32_t *n_upper, const int32_t *nb) {
+    if (count < 0 || count > 8) return -1;
+    if (count > 0 && n_upper == nullptr) return -2;
+    if (count > 0 && nb == nullptr) return -3;
+    BatchedNb t = {count, {0}, {0}};
+    for (int i = 0; i < count; ++i) {
+        if (nb[i] != 8 && nb[i] != 16 && nb[i] != 32) return -3;
+        if (n_upper[i] < 1 || (i > 0 && n_upper[i] <= n_upper[i - 1])) return -2;
+        t.n_upper[i] = n_upper[i];
+        t.nb[i] = nb[i];
+    }
+    std::lock_guard<std::mutex> lock(g_bnb_mutex);
+    g_bnb = t;
+    return SKEW_OK;
+}
+
+int skew_get_batched_nb(int n) {
+    return batched_nb_for(batched_nb_table(), n);
 }
 
 int skew_default_nb(int64_t n) {

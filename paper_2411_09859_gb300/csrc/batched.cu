@@ -224,14 +224,14 @@ __device__ void factor_one(const skew_problem &P, double *logabs, int32_t *sign,
 // ------------------------------------------------------------------------------------
 // Blocked variant for n <= kBlkMaxN: the blocked right-looking algorithm of
 // Section 4.2 (Variant 1) with the pivoted left-looking panel of Section 5.2, inside
-// one CTA.  Panels of kBlkNb columns: each step forms v = X[k+1:, k] - Lp h from the
+// one CTA.  Panels of NB columns: each step forms v = X[k+1:, k] - Lp h from the
 // panel's L columns kept in shared memory (h = T L[k, :]^T), takes the pivot, exchanges
 // k+1 and r in place, and scales.  The trailing update is one skew rank-2k update
 // with the pairs (a_j, w_j), W = A S (Section 2.2 theorem), plus the pair of the last
 // Gauss transform, on FP64 DMMA (mma.sync.m8n8k4.f64): n^3/3 flops per matrix.
 // ------------------------------------------------------------------------------------
 constexpr int kBlkThreads = 256;
-constexpr int kBlkNb = 16;
+constexpr int kBlkNbMax = 32;     // panel widths 8, 16, 32 per size bucket (BatchedNb)
 constexpr int kBlkMaxN = 512;
 
 __device__ __forceinline__ void dmma884(double &c0, double &c1, double a, double b) {
@@ -241,8 +241,8 @@ __device__ __forceinline__ void dmma884(double &c0, double &c1, double a, double
 }
 
 struct BlkShared {
-    double h[kBlkNb + 1];
-    double t[kBlkNb + 1];
+    double h[kBlkNbMax + 1];
+    double t[kBlkNbMax + 1];
     unsigned long long w_raw[kBlkThreads / 32];
     int w_i[kBlkThreads / 32];
     int w_bad[kBlkThreads / 32];
@@ -275,8 +275,9 @@ __device__ Cand blk_cand(Cand x, bool bad, BlkShared &sh, bool &any_bad) {
     return r;
 }
 
-// smem: Lp[kBlkNb][nmax] (panel L columns), Ws[kBlkNb/2+1][nmax] (odd W columns),
+// smem: Lp[NB][nmax] (panel L columns), Ws[NB/2+1][nmax] (odd W columns),
 // sv[nmax] (v of the current step)
+template <int NB>
 __device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_t *sign,
                                    int32_t *info, double *smem, int nmax, BlkShared &sh,
                                    BatchShared &fin) {
@@ -290,8 +291,8 @@ __device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_
     double *t = P.t;
     int32_t *piv = P.piv;
     double *Lp = smem;                                  // Lp[q * nmax + i]
-    double *Ws = smem + (size_t)kBlkNb * nmax;          // Ws[pp * nmax + i]
-    double *sv = Ws + (size_t)(kBlkNb / 2 + 1) * nmax;
+    double *Ws = smem + (size_t)NB * nmax;              // Ws[pp * nmax + i]
+    double *sv = Ws + (size_t)(NB / 2 + 1) * nmax;
 
     for (int i = tid; i < n; i += nthr) piv[i] = i;
     if (L != nullptr)
@@ -315,7 +316,7 @@ __device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_
     };
 
     for (int k0 = 0; k0 + 1 < n;) {
-        const int kend = (k0 + kBlkNb < n - 1) ? k0 + kBlkNb : n - 1;
+        const int kend = (k0 + NB < n - 1) ? k0 + NB : n - 1;
         const int b = kend - k0;
         // ---------------- the panel
         for (int k = k0; k < kend; ++k) {
@@ -541,13 +542,14 @@ __device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_
 // Pfaffian-only batched variant: the two-step elimination (only the even-step Gauss
 // transforms; each pair of columns removed by the Schur complement of its 2 x 2 skew
 // pivot block; notes to the two-step right-looking algorithm, Section 4.1), blocked
-// inside one CTA: panels of kBlkNb columns (kBlkNb/2 pairs) formed left-looking from
+// inside one CTA: panels of NB columns (NB/2 pairs) formed left-looking from
 // the panel's vectors kept in shared memory, then one skew rank-2k update
 // X[k1:, k1:] += sum_j (l_j y_j^T - y_j l_j^T) on FP64 DMMA.  Half the pivot searches
 // (and CTA barriers) of factor_one_blocked and no W.  P.t receives the n/2 pivot-block
 // entries a_j, P.piv the even-step exchanges (identity elsewhere); P.L is not used.
-// smem: Vp[kBlkNb][nmax] (c = 2q: l_q, 2q+1: y_q), sv[nmax].
+// smem: Vp[NB][nmax] (c = 2q: l_q, 2q+1: y_q), sv[nmax].
 // ------------------------------------------------------------------------------------
+template <int NB>
 __device__ void pfaff_one_twostep(const skew_problem &P, double *logabs, int32_t *sign,
                                   int32_t *info, double *smem, int nmax, BlkShared &sh,
                                   BatchShared &fin) {
@@ -559,7 +561,7 @@ __device__ void pfaff_one_twostep(const skew_problem &P, double *logabs, int32_t
     double *aout = P.t;
     int32_t *piv = P.piv;
     double *Vp = smem;                                  // Vp[c * nmax + i]
-    double *sv = smem + (size_t)kBlkNb * nmax;
+    double *sv = smem + (size_t)NB * nmax;
 
     for (int i = tid; i < n; i += nthr) piv[i] = i;
     bool nonfinite = false;
@@ -567,7 +569,7 @@ __device__ void pfaff_one_twostep(const skew_problem &P, double *logabs, int32_t
 
     for (int k0 = 0; k0 + 1 < n;) {
         int np = 0;
-        for (int k = k0; k < k0 + kBlkNb && k + 1 < n; k += 2) ++np;
+        for (int k = k0; k < k0 + NB && k + 1 < n; k += 2) ++np;
         for (int j = 0; j < np; ++j) {
             const int k = k0 + 2 * j, nc = 2 * j, p = k + 1;
             // v = X[:, k] + sum_c Vp[c][i] h[c]:  h[2q] = y_q[k], h[2q+1] = -l_q[k]
@@ -753,7 +755,7 @@ __device__ void pfaff_one_twostep(const skew_problem &P, double *logabs, int32_t
 __global__ void __launch_bounds__(kBlkThreads, 2)
 batched_twostep_kernel(int count, const skew_problem *problems, const int32_t *order,
                        unsigned int *counter, double *logabs, int32_t *sign, int32_t *info,
-                       int max_n) {
+                       int max_n, BatchedNb tab) {
     extern __shared__ double s_blk[];
     __shared__ BlkShared sh;
     __shared__ BatchShared fin;
@@ -771,15 +773,21 @@ batched_twostep_kernel(int count, const skew_problem *problems, const int32_t *o
             if (threadIdx.x == 0 && info) info[b] = -2;
             continue;
         }
-        pfaff_one_twostep(P, logabs ? logabs + b : nullptr, sign ? sign + b : nullptr,
-                          info ? info + b : nullptr, s_blk, max_n > 1 ? max_n : 1, sh, fin);
+        double *la = logabs ? logabs + b : nullptr;
+        int32_t *sg = sign ? sign + b : nullptr, *inf = info ? info + b : nullptr;
+        const int nm = max_n > 1 ? max_n : 1;
+        switch (batched_nb_for(tab, n)) {
+            case 8: pfaff_one_twostep<8>(P, la, sg, inf, s_blk, nm, sh, fin); break;
+            case 32: pfaff_one_twostep<32>(P, la, sg, inf, s_blk, nm, sh, fin); break;
+            default: pfaff_one_twostep<16>(P, la, sg, inf, s_blk, nm, sh, fin); break;
+        }
     }
 }
 
 __global__ void __launch_bounds__(kBlkThreads, 2)
 batched_blocked_kernel(int count, const skew_problem *problems, const int32_t *order,
                        unsigned int *counter, double *logabs, int32_t *sign, int32_t *info,
-                       int max_n) {
+                       int max_n, BatchedNb tab) {
     extern __shared__ double s_blk[];
     __shared__ BlkShared sh;
     __shared__ BatchShared fin;
@@ -798,8 +806,14 @@ batched_blocked_kernel(int count, const skew_problem *problems, const int32_t *o
             if (threadIdx.x == 0 && info) info[b] = -2;
             continue;
         }
-        factor_one_blocked(P, logabs ? logabs + b : nullptr, sign ? sign + b : nullptr,
-                           info ? info + b : nullptr, s_blk, max_n > 1 ? max_n : 1, sh, fin);
+        double *la = logabs ? logabs + b : nullptr;
+        int32_t *sg = sign ? sign + b : nullptr, *inf = info ? info + b : nullptr;
+        const int nm = max_n > 1 ? max_n : 1;
+        switch (batched_nb_for(tab, n)) {
+            case 8: factor_one_blocked<8>(P, la, sg, inf, s_blk, nm, sh, fin); break;
+            case 32: factor_one_blocked<32>(P, la, sg, inf, s_blk, nm, sh, fin); break;
+            default: factor_one_blocked<16>(P, la, sg, inf, s_blk, nm, sh, fin); break;
+        }
     }
 }
 
@@ -859,6 +873,17 @@ order_kernel(int count, const skew_problem *problems, int max_n, int32_t *order,
     }
 }
 
+// the widest panel any order <= max_n takes (shared memory is sized for it)
+int widest_nb(const BatchedNb &t, int max_n) {
+    if (t.count == 0) return 16;
+    int w = 0;
+    for (int i = 0; i < t.count; ++i) {
+        w = t.nb[i] > w ? t.nb[i] : w;
+        if (t.n_upper[i] >= max_n) break;
+    }
+    return w;
+}
+
 }  // namespace
 
 int launch_batched_twostep(int count, const skew_problem *problems, double *logabs,
@@ -875,7 +900,8 @@ int launch_batched_twostep(int count, const skew_problem *problems, double *loga
     note_launches(1);
     SKEW_TRY_STATUS(check_launch());
     const size_t nm = (size_t)(max_n > 1 ? max_n : 1);
-    const size_t smem = sizeof(double) * nm * (kBlkNb + 1);
+    const BatchedNb tab = batched_nb_table();
+    const size_t smem = sizeof(double) * nm * (widest_nb(tab, max_n) + 1);
     cudaError_t e = cudaFuncSetAttribute((const void *)batched_twostep_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
@@ -892,7 +918,7 @@ int launch_batched_twostep(int count, const skew_problem *problems, double *loga
     int grid = sms * per_sm;
     if (grid > count) grid = count;
     batched_twostep_kernel<<<grid, kBlkThreads, smem, stream>>>(count, problems, order, counter,
-                                                                logabs, sign, info, max_n);
+                                                                logabs, sign, info, max_n, tab);
     note_launches(1);
     return check_launch();
 }
@@ -917,7 +943,9 @@ int launch_batched(int count, const skew_problem *problems, double *logabs, int3
     if (max_n <= kBlkMaxN) {
         // blocked variant: Lp, Ws and sv in shared memory
         const size_t nm = (size_t)(max_n > 1 ? max_n : 1);
-        const size_t bsmem = sizeof(double) * nm * (kBlkNb + (kBlkNb / 2 + 1) + 1);
+        const BatchedNb tab = batched_nb_table();
+        const int wnb = widest_nb(tab, max_n);
+        const size_t bsmem = sizeof(double) * nm * (wnb + (wnb / 2 + 1) + 1);
         cudaError_t e = cudaFuncSetAttribute((const void *)batched_blocked_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)bsmem);
@@ -935,7 +963,7 @@ int launch_batched(int count, const skew_problem *problems, double *logabs, int3
         int grid = sms * per_sm;
         if (grid > count) grid = count;
         batched_blocked_kernel<<<grid, kBlkThreads, bsmem, stream>>>(
-            count, problems, order, counter, logabs, sign, info, max_n);
+            count, problems, order, counter, logabs, sign, info, max_n, tab);
         note_launches(1);
         return check_launch();
     }

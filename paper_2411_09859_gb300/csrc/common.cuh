@@ -235,6 +235,20 @@ bool twostep_fits(int64_t n, int nb, int sms);
 int launch_finish_twostep(int64_t n, const double *a, const int32_t *piv, const Ctrl *ctrl,
                           double *logabs, int32_t *sign, int32_t *info, cudaStream_t stream);
 
+// Panel width of the CTA-local batched kernels per order bucket: n <= n_upper[i] takes
+// nb[i] (8, 16 or 32; first match), larger orders the last entry; count 0: 16.
+struct BatchedNb {
+    int count;
+    int n_upper[8];
+    int nb[8];
+};
+__host__ __device__ inline int batched_nb_for(const BatchedNb &t, int n) {
+    for (int i = 0; i < t.count; ++i)
+        if (n <= t.n_upper[i]) return t.nb[i];
+    return t.count > 0 ? t.nb[t.count - 1] : 16;
+}
+BatchedNb batched_nb_table();     // the table installed by skew_set_batched_nb_table
+
 // Batched persistent factorization (batched.cu).
 size_t batched_workspace_bytes(int count, int max_n);
 int launch_batched(int count, const skew_problem *problems, double *logabs, int32_t *sign,

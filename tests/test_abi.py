@@ -119,3 +119,18 @@ def test_autotune_pick_rule():
     assert autotune.pick({"32": 10.0, "64": 9.0, "96": 8.99}) == 64
     assert autotune.table_from_ms({"4096": {"32": 1.0, "64": 2.0}, "512": {"16": 3.0, "32": 1.0}}) == \
         [(512, 32), (4096, 32)]
+
+
+def test_batched_nb_table():
+    import paper_2411_09859_gb300 as skew
+    from paper_2411_09859_gb300 import autotune
+    try:
+        skew.set_batched_nb_table([(64, 8), (256, 16), (512, 32)])
+        assert [skew.batched_nb(n) for n in (10, 64, 65, 256, 300, 600)] == [8, 8, 16, 16, 32, 32]
+        with pytest.raises(skew.SkewError):
+            skew.set_batched_nb_table([(64, 12)])
+        skew.set_batched_nb_table([])
+        assert skew.batched_nb(100) == 16
+    finally:
+        if not autotune.load():
+            skew.set_batched_nb_table([])
