@@ -109,6 +109,13 @@ int skew_profile_read(skew_kernel_stat *stats /* SKEW_KIND_COUNT entries */);
  * usable afterwards. */
 int skew_selftest_bounded_wait(double timeout_s, int32_t *status);
 
+/* The same check for the bounded mbarrier wait of the tensor-core (tcgen05) kernels: one
+ * thread waits for the completion of an mbarrier phase that no thread ever arrives on;
+ * after timeout_s seconds (0 < timeout_s <= 10) the wait gives up and records
+ * SKEW_ERR_TIMEOUT in *status.  Synchronous; the device stays usable afterwards.
+ * Returns 0, -1 / -2 for a bad argument, or a host-side status. */
+int skew_selftest_mbarrier_wait(double timeout_s, int32_t *status);
+
 /* Panel width used when `nb` is 0 for a matrix of order n: from the table installed
  * by skew_set_nb_table, else 16 (n <= 256), 32 (n <= 2048), 64. */
 int skew_default_nb(int64_t n);

@@ -33,6 +33,7 @@ SIGNATURES = {
     "skew_kernel_launches": ([], ctypes.c_uint64),
     "skew_trim_memory": ([], _i32),
     "skew_selftest_bounded_wait": ([_dbl, _vp], _i32),
+    "skew_selftest_mbarrier_wait": ([_dbl, _vp], _i32),
     "skew_profile_enable": ([_i32], _i32),
     "skew_profile_read": ([_vp], _i32),
     "skew_default_nb": ([_i64], _i32),

@@ -630,6 +630,32 @@ int skew_selftest_bounded_wait(double timeout_s, int32_t *status) {
     return rc;
 }
 
+int skew_selftest_mbarrier_wait(double timeout_s, int32_t *status) {
+    if (!(timeout_s > 0.0 && timeout_s <= 10.0)) return -1;
+    if (status == nullptr) return -2;
+    DeviceInfo di;
+    SKEW_TRY_STATUS(current_device_info(&di));
+    cudaStream_t st;
+    SKEW_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    void *p = nullptr;
+    int rc = pool_alloc(&p, sizeof(int), st);
+    if (rc == SKEW_OK) {
+        int *err = static_cast<int *>(p);
+        cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+        if (e != cudaSuccess) { set_last_error(e); rc = SKEW_ERR_CUDA; }
+        if (rc == SKEW_OK) rc = launch_selftest_mbar(err, (uint64_t)(timeout_s * 1e9), st);
+        if (rc == SKEW_OK) {
+            e = cudaMemcpyAsync(status, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) { set_last_error(e); rc = SKEW_ERR_CUDA; }
+        }
+        cudaFreeAsync(p, st);
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess && rc == SKEW_OK) { set_last_error(e); rc = SKEW_ERR_CUDA; }
+    cudaStreamDestroy(st);
+    return rc;
+}
+
 int skew_trim_memory(void) {
     int dev;
     SKEW_TRY(cudaGetDevice(&dev));

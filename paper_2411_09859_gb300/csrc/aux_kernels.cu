@@ -2,6 +2,7 @@
 #include <climits>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace skew {
 namespace {
@@ -111,7 +112,28 @@ __global__ void selftest_wait_kernel(Ctrl *ctrl, unsigned int expected, uint64_t
     grid_barrier(ctrl, expected, gen, timeout_ns);
 }
 
+// An mbarrier that no thread ever arrives on, waited for with the bounded wait of the
+// tensor-core kernels: the wait gives up after timeout_ns and records the timeout.
+__global__ void selftest_mbar_kernel(int *err, uint64_t timeout_ns) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        abort_flag = 0;
+        tc::fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) tc::mbar_wait_bounded(&bar, 0, &abort_flag, err, SKEW_ERR_TIMEOUT, timeout_ns);
+    __syncthreads();
+}
+
 }  // namespace
+
+int launch_selftest_mbar(int *err, uint64_t timeout_ns, cudaStream_t stream) {
+    selftest_mbar_kernel<<<1, 32, 0, stream>>>(err, timeout_ns);
+    note_launches(1);
+    return check_launch();
+}
 
 int launch_selftest_wait(Ctrl *ctrl, int blocks, uint64_t timeout_ns, cudaStream_t stream) {
     selftest_wait_kernel<<<blocks, 32, 0, stream>>>(ctrl, (unsigned int)blocks + 1u, timeout_ns);

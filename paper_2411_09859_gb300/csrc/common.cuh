@@ -261,6 +261,8 @@ int launch_batched_twostep(int count, const skew_problem *problems, double *loga
 // Self-test of the bounded waits: `blocks` CTAs enter a grid barrier that expects one
 // more CTA than launched, so it can only end by its time limit.
 int launch_selftest_wait(Ctrl *ctrl, int blocks, uint64_t timeout_ns, cudaStream_t stream);
+// Self-test of the bounded mbarrier wait of the tensor-core kernels (no arrival ever).
+int launch_selftest_mbar(int *err, uint64_t timeout_ns, cudaStream_t stream);
 
 // log|Pf|, sign (either may be null), and the final info word (may be null).
 int launch_finish(int64_t n, const double *t, const int32_t *piv, const Ctrl *ctrl,

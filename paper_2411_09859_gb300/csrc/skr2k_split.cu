@@ -250,17 +250,7 @@ static_assert(sizeof(SplitShared) <= 256, "barrier block");
 // *err when err is given) or when another role has given up.
 __device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, SplitShared *sh,
                                            int *err) {
-    if (tc::mbar_test(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (!tc::mbar_wait_for(bar, parity, 20000u)) {
-        if (ld_volatile_i32(&sh->abort)) return false;
-        if (global_ns() - t0 > kSplitTimeoutNs) {
-            *reinterpret_cast<volatile int *>(&sh->abort) = 1;
-            if (err) atomicCAS(err, 0, SKEW_ERR_TIMEOUT);
-            return false;
-        }
-    }
-    return true;
+    return tc::mbar_wait_bounded(bar, parity, &sh->abort, err, SKEW_ERR_TIMEOUT, kSplitTimeoutNs);
 }
 
 // The 8 entries C[i, j0 .. j0+7] of the strictly lower part that a thread updates

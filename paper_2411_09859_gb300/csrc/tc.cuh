@@ -60,6 +60,28 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Bounded wait for the phase of the given parity.  Returns false when the wait gives
+// up: after timeout_ns (then *abort is set and SKEW-style status `code` is recorded in
+// *err when err is given) or as soon as another thread has set *abort.  A waiting
+// thread is suspended in the barrier unit between polls (up to 20 us per poll).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *abort,
+                                                  int *err, int code, uint64_t timeout_ns) {
+    if (mbar_test(bar, parity)) return true;
+    uint64_t t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    while (!mbar_wait_for(bar, parity, 20000u)) {
+        if (*reinterpret_cast<volatile int *>(abort)) return false;
+        uint64_t now;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+        if (now - t0 > timeout_ns) {
+            *reinterpret_cast<volatile int *>(abort) = 1;
+            if (err) atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+    return true;
+}
+
 // ---- TMA ---------------------------------------------------------------------------
 __device__ __forceinline__ void tma_prefetch_map(const CUtensorMap *map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");

@@ -18,7 +18,8 @@ torch = pytest.importorskip("torch")
 import oracle  # noqa: E402
 import paper_2411_09859_gb300 as skew  # noqa: E402
 from paper_2411_09859_gb300 import inputs  # noqa: E402
-from skewcheck import EPS, backward_error, check_structure, tridiag_from_t  # noqa: E402
+from skewcheck import (EPS, backward_error, check_structure, perm_from_piv,  # noqa: E402
+                       tridiag_from_t)
 
 pytestmark = pytest.mark.gpu
 TOL_C = 2000.0
@@ -288,3 +289,52 @@ def test_launch_counter_moves():
     before = skew.kernel_launches()
     gpu_ltlt(inputs.skew_gaussian(100, 1), 16)
     assert skew.kernel_launches() > before
+
+
+def test_order_beyond_one_row_per_panel_thread():
+    """n = 39000: the first panels have more rows than 256 x (multiprocessors), so they
+    run the global-memory panel, the later ones the shared-memory panel.  The oracle
+    would take minutes, so the factors are checked by properties that hold at any
+    order: randomized residuals of P A P^T = L T L^T (O(n^2) per vector), |L| <= 1,
+    L e_0 = e_0, the pivot vector, and log|Pf| against the Pfaffian-only path."""
+    n = 39000
+    props = torch.cuda.get_device_properties(0)
+    if n - 1 <= props.multi_processor_count * 256:
+        pytest.skip("this device's panel keeps one row per thread at n = 39000")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(123)
+    A = torch.tril(torch.randn((n, n), generator=gen, dtype=torch.float64, device="cuda"), -1)
+    A = A - A.t()                                   # skew; element (i, j) is A[i, j]
+    work = skew.fortran_empty(n, n, "cuda")
+    work.copy_(A)
+    L, t, piv, info = skew.ltlt(work, nb=64)
+    torch.cuda.synchronize()
+    del work
+    assert int(info.item()) == 0
+    p = piv.cpu().numpy()
+    assert p[0] == 0 and np.all(p[1:] >= np.arange(1, n))
+    perm = torch.from_numpy(perm_from_piv(p)).cuda()
+    assert float(torch.max(torch.abs(torch.tril(L, -1)))) <= 1.0
+    assert bool(torch.all(L[:, 0] == torch.eye(n, 1, dtype=torch.float64, device="cuda")[:, 0]))
+    normA = float(torch.linalg.norm(A))
+    for _ in range(3):
+        x = torch.randn(n, generator=gen, dtype=torch.float64, device="cuda")
+        xp = torch.zeros_like(x)
+        xp[perm] = x
+        y = (A @ xp)[perm]                          # (P A P^T) x, (P A P^T)[a, b] = A[perm a, perm b]
+        z = L.t() @ x                               # L T L^T x, T[i+1, i] = t[i] = -T[i, i+1]
+        Tz = torch.zeros_like(z)
+        Tz[1:] += t * z[:-1]
+        Tz[:-1] -= t * z[1:]
+        w = L @ Tz
+        rel = float(torch.linalg.norm(y - w)) / (normA * float(torch.linalg.norm(x)))
+        assert rel <= 10 * n * EPS, rel
+    la1, sg1 = skew.pfaffian_from_factors(t, piv, n)
+    del L
+    w2 = skew.fortran_empty(n, n, "cuda")
+    w2.copy_(A)
+    del A
+    la2, sg2, *_ = skew.pfaffian(w2, nb=64)
+    torch.cuda.synchronize()
+    assert int(sg1.item()) == int(sg2.item())
+    assert abs(float(la1.item()) - float(la2.item())) <= 1e-10 * abs(float(la2.item()))
