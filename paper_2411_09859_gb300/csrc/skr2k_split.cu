@@ -191,13 +191,27 @@ __device__ __noinline__ double scaled_to_double_slow(long long v, int e2) {
     return ldexp((double)v, e2);
 }
 
-// v * 2^e2 rounded to nearest (ties to even), built with integer operations
+// v * 2^e2 rounded to nearest (ties to even), two equivalent ways: HW converts v to FP64
+// (one rounding to 53 bits) and scales it exactly through the exponent field; otherwise
+// the same rounding is built with integer operations.  The epilogue uses both, on
+// alternate columns, so that the FP64 pipe (which also does the final add) and the
+// integer pipe share the work.  Results outside the normal range take the out-of-line
+// path.
+template <bool HW>
 __device__ __forceinline__ double scaled_to_double(long long v, int e2) {
+    if (HW) {
+        const long long bits = __double_as_longlong(__ll2double_rn(v));
+        const int be = (int)((bits >> 52) & 0x7ff);
+        if (be == 0) return 0.0;                      // v == 0
+        const int E = be + e2;
+        if (E <= 0 || E >= 2047) return scaled_to_double_slow(v, e2);
+        return __longlong_as_double(bits + ((long long)e2 << 52));
+    }
     if (v == 0) return 0.0;
     const bool neg = v < 0;
     unsigned long long u = neg ? (unsigned long long)(-v) : (unsigned long long)v;
     const int lz = __clzll((long long)u);
-    u <<= lz;                                  // leading one at bit 63
+    u <<= lz;                                         // leading one at bit 63
     int E = 63 - lz + e2 + 1023;
     unsigned long long mant = (u >> 11) & 0x000fffffffffffffull;
     const unsigned long long rem = u & 0x7ffull;
@@ -279,7 +293,8 @@ __device__ __forceinline__ void store_row(double *crow, int64_t ldc, int64_t i, 
         const int Ej = __shfl_sync(0xffffffffu, Ej_lane, k);
         const int64_t j = j0 + k;
         if (!(interior || (i < m && j < m && i > j))) continue;
-        const double upd = scaled_to_double(acc[k], Ei + Ej - 54);
+        const double upd = (k & 1) ? scaled_to_double<true>(acc[k], Ei + Ej - 54)
+                                   : scaled_to_double<false>(acc[k], Ei + Ej - 54);
         if (PLAIN) crow[k * ldc] = cv[k] + upd;
         else crow[k * ldc] = fma(beta, cv[k], alpha * upd);
     }
