@@ -233,13 +233,16 @@ int skew_pfaffian_noalloc(int64_t n, double *A, int64_t lda, double *logabs,
  * the Gauss-transform division, t and the log-Pfaffian stay FP64 in both.
  *   SKEW_PRECISION_FP64       FP64 tensor-core (DMMA) products: rounding as in an FP64
  *                             dot product, entry by entry.
- *   SKEW_PRECISION_SPLIT_BF16 the FP64 operands cut into seven 8-bit digit slices per
- *                             row (relative to the row's largest entry) and multiplied
- *                             on bf16 tensor cores with exact FP32 sums, recombined
- *                             exactly in 64-bit integers (Ozaki-type error-free
- *                             splitting); the update differs from the exact one by
- *                             about 2^-53 K (row max of U)(row max of V).  At most 32
- *                             column pairs per update (panel width nb <= 64).
+ *   SKEW_PRECISION_SPLIT_BF16 the FP64 operands held as 55-bit integers relative to
+ *                             their row's largest entry, cut into seven 8-bit digit
+ *                             slices and multiplied on the fifth-generation tensor
+ *                             cores (tcgen05, bf16 inputs, exact FP32 sums per digit
+ *                             group), recombined exactly in 64-bit integers
+ *                             (Ozaki-type error-free splitting); with k column pairs
+ *                             the update differs from the exact one by at most about
+ *                             (2.02 k + 0.5) 2^-53 (row max of U)(row max of V), plus
+ *                             the rounding of the final FP64 add.  At most 32 column
+ *                             pairs per update (panel width nb <= 64).
  */
 #define SKEW_PRECISION_FP64 0
 #define SKEW_PRECISION_SPLIT_BF16 1
