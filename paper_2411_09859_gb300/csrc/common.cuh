@@ -182,6 +182,22 @@ struct PanelArgs {
 // Picks the shared-memory panel kernel when every panel row gets its own thread on
 // `sms` CTAs and the panel is at most 96 columns wide, else the global-memory one.
 int launch_panel(const PanelArgs &a, int sms, cudaStream_t stream);
+
+// CTAs of a shared-memory panel: one 32-row chunk per CTA up to the SM count, but at
+// most kPanelGridCap unless more are needed for one row per thread.  Fewer CTAs mean
+// fewer participants in each step's grid-wide exchange (and a shorter wait for the
+// slowest) at the price of more rows per CTA for the FP64 gemv; measured at n = 16384,
+// 48 to 96 CTAs were all faster than 152, 64 the fastest.
+constexpr int64_t kPanelGridCap = 64;
+inline int64_t panel_grid(int64_t rows, int sms) {
+    int64_t g = (rows + 31) / 32;
+    const int64_t need = (rows + kPanelThreads - 1) / kPanelThreads;
+    const int64_t cap = need > kPanelGridCap ? need : kPanelGridCap;
+    if (g > cap) g = cap;
+    if (g > sms) g = sms;
+    if (g < 1) g = 1;
+    return g;
+}
 int panel_max_blocks_per_sm(int *out);
 
 // Row exchanges piv[k+1] <-> k+1, k = k0 .. kend-1 in order, on L columns 1 .. k0.

@@ -526,9 +526,7 @@ int launch_panel(const PanelArgs &a, int sms, cudaStream_t stream) {
     const int width = a.kend - a.k0;
     cudaError_t e;
     if (width <= kSmemMaxNb && rows <= (int64_t)sms * kPanelThreads) {
-        int64_t g = (rows + 31) / 32;
-        if (g > sms) g = sms;
-        if (g < 1) g = 1;
+        const int64_t g = panel_grid(rows, sms);
         // (the dynamic shared-memory limit was raised when the device was first used,
         // in panel_max_blocks_per_sm)
         const size_t smem = (size_t)width * kPanelThreads * sizeof(double);

@@ -395,8 +395,7 @@ int launch_twostep_panel(const TwoStepArgs &a, int sms, cudaStream_t stream) {
         }
         attr_set = true;
     }
-    int64_t g = (rows + 31) / 32;
-    if (g > sms) g = sms;
+    int64_t g = panel_grid(rows, sms);
     if (g > kMaxPanelGrid) g = kMaxPanelGrid;
     const int cols = width + (width & 1);
     const size_t smem = (size_t)cols * kPanelThreads * sizeof(double);
