@@ -60,6 +60,26 @@ __device__ __forceinline__ Best warp_best(Best x) {
     return x;
 }
 
+// The same reduction with warp reduce instructions, the result valid in every lane:
+// the largest |v| bits (high word, then low word among the lanes that tie on it), the
+// lowest row among the lanes that tie on both, and the CTA field of that lane.  Fewer
+// dependent steps than the five-level shuffle tree above.
+__device__ __forceinline__ Best warp_best_all(Best x) {
+    const unsigned long long m = x.raw & kAbsMask;
+    const unsigned int hi = (unsigned int)(m >> 32), lo = (unsigned int)m;
+    const unsigned int mh = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned int ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+    const bool top = (hi == mh) && (lo == ml);
+    const unsigned int mi = __reduce_min_sync(0xffffffffu, top ? (unsigned int)x.i : 0xffffffffu);
+    const unsigned int win = __ballot_sync(0xffffffffu, top && (unsigned int)x.i == mi);
+    const int src = __ffs((int)win) - 1;
+    Best r;
+    r.raw = __shfl_sync(0xffffffffu, x.raw, src);
+    r.i = (int)mi;
+    r.c = __shfl_sync(0xffffffffu, x.c, src);
+    return r;
+}
+
 // Reduce one Best per thread; the result is valid in every thread on return.
 __device__ Best block_best(Best x) {
     __shared__ unsigned long long s_raw[kPanelThreads / 32];

@@ -247,6 +247,8 @@ panel_smem_kernel(PanelArgs a) {
     __shared__ double s_t[kSmemMaxNb + 1];   // t[k] of this panel, index k - k0
     __shared__ double s_w[kSmemMaxNb + 1];   // new L row k+1 (old row r), index c - k0 - 1
     __shared__ double s_rp[kSmemMaxNb + 1];  // new L row r (old row k+1)
+    __shared__ unsigned long long s_wraw[kPanelThreads / 32];   // per-warp candidates
+    __shared__ int s_wi[kPanelThreads / 32];
     __shared__ double s_tau, s_vtop;
     __shared__ int s_r, s_win, s_fail;
     __shared__ unsigned int s_base;
@@ -254,7 +256,7 @@ panel_smem_kernel(PanelArgs a) {
     Ctrl *ctrl = a.ctrl;
     const int n = a.n, k0 = a.k0, kend = a.kend;
     const int G = (int)gridDim.x;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double *X = a.X;
     const int64_t ldx = a.ldx, ldl = a.ldl;
     auto Lcol = [&](int q) -> double * { return a.Lp + (int64_t)(q - k0 - 1) * ldl; };
@@ -282,28 +284,41 @@ panel_smem_kernel(PanelArgs a) {
         return (((j >> 5) / G) << 5) + (j & 31);
     };
 
-    // Publish this CTA's step-k candidate (and its L row), the row k+1 of L and
-    // v[k+1] if this CTA owns row k+1, then release the step tag.  Rows are copied
-    // from shared memory by all threads of the CTA.
+    // Publish this CTA's step-k candidate (and its L row), the row k+1 of L if this
+    // CTA owns row k+1, then release the step tag.  One CTA barrier: every warp leaves
+    // its best candidate in shared memory, then warp 0 alone finishes the reduction,
+    // copies the rows from shared memory and releases, while the other warps go on to
+    // wait for the next step's gather.
     auto publish = [&](int k, Best best, bool nonfinite) {
         if (nonfinite) raise_error(ctrl, SKEW_ERR_NONFINITE);
-        best = block_best(best);
+        best = warp_best_all(best);
+        if (lane == 0) {
+            s_wraw[warp] = best.raw;
+            s_wi[warp] = best.i;
+        }
+        __syncthreads();
+        if (warp != 0) return;
+        Best y = no_candidate();
+        if (lane < kPanelThreads / 32) {
+            y.raw = s_wraw[lane];
+            y.i = s_wi[lane];
+        }
+        y = warp_best_all(y);
         ArgmaxPartial *sp = slot(k, blockIdx.x);
         const int nq = k - k0;
-        if (best.i != INT_MAX) {
-            const int ot = owner_tid(best.i);
-            for (int q = tid; q < nq; q += blockDim.x)
-                sp->row[q] = s_L[q * kPanelThreads + ot];
+        if (y.i != INT_MAX) {
+            const int ot = owner_tid(y.i);
+            for (int q = lane; q < nq; q += 32) sp->row[q] = s_L[q * kPanelThreads + ot];
         }
         if (k + 1 < n && owner_cta(k + 1) == (int)blockIdx.x) {
             const int ot = owner_tid(k + 1);
-            for (int q = tid; q < nq; q += blockDim.x)
-                ctrl->rowp[k & 1][q] = s_L[q * kPanelThreads + ot];
+            for (int q = lane; q < nq; q += 32) ctrl->rowp[k & 1][q] = s_L[q * kPanelThreads + ot];
         }
-        __syncthreads();
-        // release: the CTA's writes above (ordered before by the barrier) become
-        // visible to any CTA that sees the tag; candidate and tag in one 128-bit store
-        if (tid == 0) record_release(sp, best.raw, best.i, base + (unsigned int)(k - k0) + 1u);
+        // release: the CTA's writes before the barrier and warp 0's copies (ordered by
+        // __syncwarp) become visible to any CTA that sees the tag; candidate and tag
+        // in one 128-bit store
+        __syncwarp();
+        if (lane == 0) record_release(sp, y.raw, y.i, base + (unsigned int)(k - k0) + 1u);
     };
 
     // ---------------- step k0: v = X[k0+1:, k0]
@@ -324,20 +339,20 @@ panel_smem_kernel(PanelArgs a) {
 
     for (int k = k0; k < kend; ++k) {
         // ---------------- gather the step-k candidates of all CTAs (the barrier).
-        // Lane l of warp 0 watches slots l, l+32, ...: all its tags are polled in one
-        // pass of independent acquire loads, then all values are loaded at once.
-        if (tid < 32) {
+        // Lane l of warp 0 watches slots l, l+32, ...: one 128-bit relaxed load per
+        // slot returns candidate and tag together, all slots of a pass in flight at once.
+        if (warp == 0) {
             constexpr int kPer = kMaxPanelGrid / 32;
             const unsigned int want = base + (unsigned int)(k - k0) + 1u;
             unsigned int pending = 0;
 #pragma unroll
             for (int j = 0; j < kPer; ++j)
-                if (tid + 32 * j < G) pending |= 1u << j;
+                if (lane + 32 * j < G) pending |= 1u << j;
             int fail = 0;
             uint64_t t0 = 0;
             unsigned int polls = 0;
-            // relaxed loads, all in flight at once (acquire loads would serialise);
-            // the fence after the loop turns the observed tags into an acquire
+            // relaxed loads (acquire loads would serialise); the fence after the loop
+            // turns the observed tags into an acquire
             unsigned long long pv[kPer];
             unsigned int pi[kPer];
             while (pending != 0u) {
@@ -346,7 +361,7 @@ panel_smem_kernel(PanelArgs a) {
                     if ((pending >> j) & 1u) {
                         unsigned long long rv;
                         unsigned int ri, rt;
-                        record_poll(slot(k, tid + 32 * j), rv, ri, rt);
+                        record_poll(slot(k, lane + 32 * j), rv, ri, rt);
                         if (rt == want) {
                             pending &= ~(1u << j);
                             pv[j] = rv;
@@ -372,7 +387,7 @@ panel_smem_kernel(PanelArgs a) {
             if (!fail) {
 #pragma unroll
                 for (int j = 0; j < kPer; ++j) {
-                    const int c = tid + 32 * j;
+                    const int c = lane + 32 * j;
                     if (c < G && better(pv[j], (int)pi[j], b.raw, b.i)) {
                         b.raw = pv[j];
                         b.i = (int)pi[j];
@@ -381,8 +396,8 @@ panel_smem_kernel(PanelArgs a) {
                 }
             }
             fail = __any_sync(0xffffffffu, fail);
-            b = warp_best(b);
-            if (tid == 0) {
+            b = warp_best_all(b);
+            if (lane == 0) {
                 s_fail = fail;
                 s_r = (b.i == INT_MAX) ? k + 1 : b.i;    // all NaN: keep the diagonal
                 s_tau = as_double(b.raw);
@@ -415,12 +430,13 @@ panel_smem_kernel(PanelArgs a) {
         }
         __syncthreads();
         const double tau = s_tau, vtop = s_vtop;
+        // s_t[k - k0] is first read at the next step (after more barriers); this
+        // step's h takes tau from the register
         if (tid == 0) s_t[k - k0] = tau;
         if (blockIdx.x == 0 && tid == 0) {
             a.t[k] = tau;
             a.piv[p] = r;
         }
-        __syncthreads();
 
         // exchanged rows of the panel's L columns k0+1..k: new row p = old row r (s_w)
         // in the CTA owning p, new row r = old row p (s_rp) in the CTA owning r
@@ -443,12 +459,13 @@ panel_smem_kernel(PanelArgs a) {
         const bool next = (k + 1 < kend);
         const bool form_x = (!next && a.with_x);
         if (next || form_x) {
+            auto tq = [&](int q) -> double { return q == k ? tau : s_t[q - k0]; };
             for (int q = k0 + 1 + tid; q <= k + 1; q += blockDim.x) {
                 double hq = 0.0;
-                if (q - 1 >= k0 + 1) hq = s_t[q - 1 - k0] * s_w[q - 2 - k0];
+                if (q - 1 >= k0 + 1) hq = tq(q - 1) * s_w[q - 2 - k0];
                 if (q + 1 <= k + 1) {
                     const double lq1 = (q + 1 == k + 1) ? 1.0 : s_w[q - k0];
-                    hq -= s_t[q - k0] * lq1;
+                    hq -= tq(q) * lq1;
                 }
                 s_h[q - k0 - 1] = hq;
             }
@@ -470,7 +487,21 @@ panel_smem_kernel(PanelArgs a) {
                 *lk1 = l;
             }
             if (i > p) {
+                // ---- the gemv of step k+1 first: it needs no global data, so the
+                // loads of x_old and xe are still in flight while it runs
+                double acc0 = 0.0, acc1 = 0.0;
+                if (next || form_x) {
+                    int q = 0;
+#pragma unroll 4
+                    for (; q + 1 <= nq; q += 2) {
+                        acc0 += sL(q) * s_h[q];
+                        acc1 += sL(q + 1) * s_h[q + 1];
+                    }
+                    if (q <= nq) acc0 += sL(q) * s_h[q];
+                }
                 // ---- symmetric exchange of p and r in the strictly lower storage
+                // (the new column p itself is not stored: it only enters v below, and
+                // no later step of the panel reads column p)
                 double xn = x_old;                        // new X[i, p]
                 if (r != p) {
                     if (i < r) {
@@ -482,18 +513,9 @@ panel_smem_kernel(PanelArgs a) {
                         xn = xe;
                         X[(int64_t)r * ldx + i] = x_old;  // X[i, r]
                     }
-                    colp[i] = xn;
                 }
                 // ---- step k+1 for this row (or the updated column kend)
                 if (next || form_x) {
-                    double acc0 = 0.0, acc1 = 0.0;
-                    int q = 0;
-#pragma unroll 4
-                    for (; q + 1 <= nq; q += 2) {
-                        acc0 += sL(q) * s_h[q];
-                        acc1 += sL(q + 1) * s_h[q + 1];
-                    }
-                    if (q <= nq) acc0 += sL(q) * s_h[q];
                     const double vn = xn - (acc0 + acc1);
                     if (!finite_bits((unsigned long long)__double_as_longlong(vn))) nonfinite = true;
                     if (form_x) {
