@@ -183,17 +183,22 @@ struct PanelArgs {
 // `sms` CTAs and the panel is at most 96 columns wide, else the global-memory one.
 int launch_panel(const PanelArgs &a, int sms, cudaStream_t stream);
 
-// CTAs of a shared-memory panel: one 32-row chunk per CTA up to the SM count, but at
-// most kPanelGridCap unless more are needed for one row per thread.  Fewer CTAs mean
-// fewer participants in each step's grid-wide exchange (and a shorter wait for the
-// slowest) at the price of more rows per CTA for the FP64 gemv; measured at n = 16384,
-// 48 to 96 CTAs were all faster than 152, 64 the fastest.
+// CTAs of a shared-memory panel.  Up to 64 x 128 rows, one CTA per 128 rows (four
+// warps of rows: the CTA's FP64 gemv runs on all four schedulers of its SM, as fast as
+// one warp per CTA on one scheduler, with a quarter of the CTAs in each grid-wide
+// exchange); above that, 64 CTAs unless more are needed for one row per thread.  Fewer
+// CTAs mean fewer participants in each step's exchange (and a shorter wait for the
+// slowest) at the price of more rows per CTA for the gemv.  Measured at n = 16384:
+// caps of 48 to 96 CTAs were all faster than 152, 64 the fastest; 128 rather than 32
+// rows per CTA below 8192 rows took the panel from 107.0 to 105.7 ms (n = 4096:
+// 25.0 to 24.2 ms).
 constexpr int64_t kPanelGridCap = 64;
+constexpr int64_t kPanelRowsPerCta = 128;
 inline int64_t panel_grid(int64_t rows, int sms) {
-    int64_t g = (rows + 31) / 32;
+    int64_t g = (rows + kPanelRowsPerCta - 1) / kPanelRowsPerCta;
+    if (g > kPanelGridCap) g = kPanelGridCap;
     const int64_t need = (rows + kPanelThreads - 1) / kPanelThreads;
-    const int64_t cap = need > kPanelGridCap ? need : kPanelGridCap;
-    if (g > cap) g = cap;
+    if (g < need) g = need;
     if (g > sms) g = sms;
     if (g < 1) g = 1;
     return g;

@@ -44,12 +44,14 @@ twostep_panel_kernel(TwoStepArgs A) {
     __shared__ double s_W[kTsMaxNb], s_P1[kTsMaxNb], s_P2[kTsMaxNb];
     __shared__ double s_c1[kTsMaxNb], s_c2[kTsMaxNb + 2];
     __shared__ double s_a, s_vk1, s_vk2, s_xs1, s_xs2;
+    __shared__ unsigned long long s_wraw[kPanelThreads / 32];   // per-warp candidates
+    __shared__ int s_wi[kPanelThreads / 32];
     __shared__ int s_r, s_win, s_fail;
     __shared__ unsigned int s_base;
 
     Ctrl *ctrl = A.ctrl;
     const int n = A.n, k0 = A.k0, kend = A.kend;
-    const int G = (int)gridDim.x, tid = threadIdx.x;
+    const int G = (int)gridDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double *X = A.X;
     const int64_t ldx = A.ldx, ldv = A.ldv;
     auto slot = [&](int j, int cta) -> ArgmaxPartial * {
@@ -76,30 +78,45 @@ twostep_panel_kernel(TwoStepArgs A) {
 
     // Publish pair step j (column k = k0 + 2j): this CTA's best candidate row (> k)
     // with its nc = 2j stored entries, and -- from their owners -- the stored rows and
-    // v of rows k+1 and k+2; then release the step tag.
+    // v of rows k+1 and k+2; then release the step tag.  One CTA barrier: every warp
+    // leaves its best candidate in shared memory (and the owners of rows k+1, k+2
+    // their v), then warp 0 alone finishes the reduction, copies the rows from shared
+    // memory and releases, while the other warps go on to wait for the next gather.
     auto publish = [&](int j, Best best, bool nonfinite, double v) {
         const int k = k0 + 2 * j, nc = 2 * j;
         if (nonfinite) raise_error(ctrl, SKEW_ERR_NONFINITE);
-        best = block_best(best);
+        if (own && i == k + 1) ctrl->vtop[j & 1] = v;
+        if (own && i == k + 2) ctrl->vnext[j & 1] = v;
+        best = warp_best_all(best);
+        if (lane == 0) {
+            s_wraw[warp] = best.raw;
+            s_wi[warp] = best.i;
+        }
+        __syncthreads();
+        if (warp != 0) return;
+        Best y = no_candidate();
+        if (lane < kPanelThreads / 32) {
+            y.raw = s_wraw[lane];
+            y.i = s_wi[lane];
+        }
+        y = warp_best_all(y);
         ArgmaxPartial *sp = slot(j, blockIdx.x);
-        if (best.i != INT_MAX) {
-            const int ot = owner_tid(best.i);
-            for (int c = tid; c < nc; c += blockDim.x) sp->row[c] = s_S[c * kPanelThreads + ot];
+        if (y.i != INT_MAX) {
+            const int ot = owner_tid(y.i);
+            for (int c = lane; c < nc; c += 32) sp->row[c] = s_S[c * kPanelThreads + ot];
         }
         if (k + 1 < n && owner_cta(k + 1) == (int)blockIdx.x) {
             const int ot = owner_tid(k + 1);
-            for (int c = tid; c < nc; c += blockDim.x)
-                ctrl->rowp[j & 1][c] = s_S[c * kPanelThreads + ot];
-            if (tid == ot) ctrl->vtop[j & 1] = v;
+            for (int c = lane; c < nc; c += 32) ctrl->rowp[j & 1][c] = s_S[c * kPanelThreads + ot];
         }
         if (k + 2 < n && owner_cta(k + 2) == (int)blockIdx.x) {
             const int ot = owner_tid(k + 2);
-            for (int c = tid; c < nc; c += blockDim.x)
-                ctrl->rowq[j & 1][c] = s_S[c * kPanelThreads + ot];
-            if (tid == ot) ctrl->vnext[j & 1] = v;
+            for (int c = lane; c < nc; c += 32) ctrl->rowq[j & 1][c] = s_S[c * kPanelThreads + ot];
         }
-        __syncthreads();
-        if (tid == 0) record_release(sp, best.raw, best.i, base + (unsigned int)j + 1u);
+        // release: the CTA's writes before the barrier and warp 0's copies (ordered by
+        // __syncwarp) become visible to any CTA that sees the tag
+        __syncwarp();
+        if (lane == 0) record_release(sp, y.raw, y.i, base + (unsigned int)j + 1u);
     };
 
     // ---------------- pair step 0: v = X[k0+1:, k0]
@@ -173,7 +190,7 @@ twostep_panel_kernel(TwoStepArgs A) {
                 }
             }
             fail = __any_sync(0xffffffffu, fail);
-            b = warp_best(b);
+            b = warp_best_all(b);
             if (tid == 0) {
                 s_fail = fail;
                 s_r = (b.i == INT_MAX) ? k + 1 : b.i;     // all NaN: keep the diagonal
@@ -268,6 +285,27 @@ twostep_panel_kernel(TwoStepArgs A) {
                 v = s_vk1;
             }
             const double l = (a != 0.0) ? v / a : 0.0;
+            // the gemvs over the stored entries first: they need no global data, so the
+            // loads of x_old, xe and x2 are still in flight while they run.  Both in one
+            // loop, four independent accumulators: an FP64 FMA takes a few hundred cycles
+            // on this part, and a warp is often alone on its scheduler here.
+            const bool nxt = next && i >= k + 3;
+            double acc0 = 0.0, acc1 = 0.0, b0 = 0.0, b1 = 0.0;
+            {
+                int c = 0;
+#pragma unroll 4
+                for (; c + 1 < nc; c += 2) {
+                    acc0 = fma(S(c), s_c1[c], acc0);
+                    acc1 = fma(S(c + 1), s_c1[c + 1], acc1);
+                }
+                if (nxt) {
+#pragma unroll 4
+                    for (c = 0; c + 1 < nc; c += 2) {
+                        b0 = fma(S(c), s_c2[c], b0);
+                        b1 = fma(S(c + 1), s_c2[c + 1], b1);
+                    }
+                }
+            }
             double x1 = x_old;                      // X_new[i, k+1]
             if (r != k + 1) {
                 if (i < r) {
@@ -284,26 +322,15 @@ twostep_panel_kernel(TwoStepArgs A) {
                     X[(int64_t)r * ldx + i] = x_old; // X[i, r]
                 }
             }
-            double acc0 = 0.0, acc1 = 0.0;
-            int c = 0;
-#pragma unroll 4
-            for (; c + 1 < nc; c += 2) {
-                acc0 = fma(S(c), s_c1[c], acc0);
-                acc1 = fma(S(c + 1), s_c1[c + 1], acc1);
-            }
             const double y = x1 + (acc0 + acc1);
             S(nc) = l;
             S(nc + 1) = y;
-            if (next && i >= k + 3) {
+            if (nxt) {
                 double x2v = x2;                    // X_new[i, k+2]
                 if (r == k + 2) x2v = x_old;
                 else if (r > k + 2 && i == r) x2v = -s_xs1;
-                double b0 = 0.0, b1 = 0.0;
-#pragma unroll 4
-                for (c = 0; c + 1 < nc + 2; c += 2) {
-                    b0 = fma(S(c), s_c2[c], b0);
-                    b1 = fma(S(c + 1), s_c2[c + 1], b1);
-                }
+                b0 = fma(l, s_c2[nc], b0);          // the pair formed in this step
+                b1 = fma(y, s_c2[nc + 1], b1);
                 const double vn = x2v + (b0 + b1);
                 if (!finite_bits((unsigned long long)__double_as_longlong(vn))) nonfinite = true;
                 v = vn;
