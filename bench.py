@@ -194,14 +194,21 @@ def oracle_sample(A_host: np.ndarray, sample_steps: int) -> dict:
 
 # ----------------------------------------------------------------------------- dist
 # ----------------------------------------------------------------------------- batched
-def run_batched_leg(skew, inputs, torch, dev, steps: int, warmup: int, plain_count: int):
+def run_batched_leg(skew, inputs, torch, dev, steps: int, warmup: int, plain_count: int,
+                    rank: int = 0, world: int = 1):
     """The batched workload: 4096 skew matrices, orders even in [16, 256] (seed 4),
     matrix i from seed 1000+i, all factored in one skew_ltlt_batched launch per step
     (Pfaffian-only: L not stored).  Compared with back-to-back skew_pfaffian calls on
     the same matrices.  Inputs are HBM-resident: a pristine copy is restored before
-    every step outside the timed events."""
-    sizes = inputs.batched_sizes(4096)
-    mats = [inputs.skew_gaussian(int(n), inputs.SEED_BATCH_BASE + i) for i, n in enumerate(sizes)]
+    every step outside the timed events.  With several ranks the 4096 matrices are
+    split into size-balanced shares (one per rank, no exchange on the data path) and
+    the rates are the whole batch over the slowest rank's time."""
+    from paper_2411_09859_gb300 import shard
+    all_sizes = inputs.batched_sizes(4096)
+    total = len(all_sizes)
+    idx = shard.balanced_bins(all_sizes, world)[rank] if world > 1 else np.arange(total)
+    sizes = all_sizes[idx]
+    mats = [inputs.skew_gaussian(int(all_sizes[i]), inputs.SEED_BATCH_BASE + int(i)) for i in idx]
     offs = np.concatenate([[0], np.cumsum(sizes.astype(np.int64) ** 2)])
     flat = np.empty(int(offs[-1]), dtype=np.float64)
     for i, A in enumerate(mats):
@@ -236,7 +243,7 @@ def run_batched_leg(skew, inputs, torch, dev, steps: int, warmup: int, plain_cou
         times.append(ms)
     if int((info != 0).sum().item()) != 0:
         raise RuntimeError("batched factorization reported a nonzero info")
-    ms = statistics.median(times)
+    ms = reduce_max(statistics.median(times), world, dev)
     # the Pfaffian-only form of the same batch: two-step elimination, no T/L output
     as_ = [torch.empty(max(int(n) // 2, 1), dtype=torch.float64, device=dev) for n in sizes]
     pivs2 = [torch.empty(int(n), dtype=torch.int32, device=dev) for n in sizes]
@@ -256,9 +263,10 @@ def run_batched_leg(skew, inputs, torch, dev, steps: int, warmup: int, plain_cou
             times2.append(e0.elapsed_time(e1))
     if int((info2 != 0).sum().item()) != 0:
         raise RuntimeError("two-step batched Pfaffians reported a nonzero info")
-    ms2 = statistics.median(times2)
-    agree = float(torch.max(torch.abs(la2 - la) / torch.clamp(torch.abs(la), min=1.0)).item())
-    signs_equal = bool(torch.equal(sg2, sg))
+    ms2 = reduce_max(statistics.median(times2), world, dev)
+    agree = reduce_max(float(torch.max(torch.abs(la2 - la) / torch.clamp(torch.abs(la), min=1.0)).item()),
+                       world, dev)
+    signs_equal = reduce_max(0.0 if torch.equal(sg2, sg) else 1.0, world, dev) == 0.0
     # the same launch captured once in a CUDA graph (caller-supplied workspace and
     # result buffers), replayed per batch; the inputs are restored outside the graph
     ws = torch.empty(skew.batched_workspace_bytes(len(views), 256), dtype=torch.uint8, device=dev)
@@ -284,8 +292,9 @@ def run_batched_leg(skew, inputs, torch, dev, steps: int, warmup: int, plain_cou
         torch.cuda.synchronize()
         if i >= warmup:
             times3.append(e0.elapsed_time(e1))
-    ms3 = statistics.median(times3)
-    graph_equal = bool(torch.equal(res[0], la2) and torch.equal(res[1], sg2))
+    ms3 = reduce_max(statistics.median(times3), world, dev)
+    graph_equal = reduce_max(0.0 if (torch.equal(res[0], la2) and torch.equal(res[1], sg2)) else 1.0,
+                             world, dev) == 0.0
     del graph
     # back-to-back plain calls on the same matrices (first plain_count of them)
     work.copy_(pristine)
@@ -299,24 +308,27 @@ def run_batched_leg(skew, inputs, torch, dev, steps: int, warmup: int, plain_cou
         skew.pfaffian(views[i], stream=stream, t=ts[i], piv=pivs[i])
     e1.record(stream)
     torch.cuda.synchronize()
-    plain_ms = e0.elapsed_time(e1)
-    plain_rate = m / (plain_ms / 1e3)
-    rate = len(views) / (ms / 1e3)
+    plain_ms = reduce_max(e0.elapsed_time(e1), world, dev)
+    plain_rate = world * m / (plain_ms / 1e3)
+    flops = reduce_sum(flops, world, dev)
+    rate = total / (ms / 1e3)
     return {"metric": "batched Pfaffians/s", "value": rate, "unit": "Pfaffians/s",
             "workload": "4096 skew matrices, n even uniform in [16, 256] (seed 4), "
-                        "matrix i seed 1000+i, FP64, one persistent launch",
+                        "matrix i seed 1000+i, FP64, one persistent launch"
+                        + (f" per rank on {world} size-balanced shares" if world > 1 else ""),
+            "scaling": "strong" if world > 1 else None,
             "ms_per_batch": ms, "tflops": flops / (ms / 1e3) / 1e12,
-            "plain_calls": {"value": plain_rate, "unit": "Pfaffians/s", "matrices": m,
+            "plain_calls": {"value": plain_rate, "unit": "Pfaffians/s", "matrices": m * world,
                             "api": "skew_pfaffian, one call per matrix, back to back"},
             "speedup_vs_plain_calls": rate / plain_rate,
             "accuracy": "same algorithm in FP64; pivots identical to the oracle and "
                         "log|Pf| within 1e-10 relative on the tested sample",
             "pfaffian_only_twostep": {
-                "value": len(views) / (ms2 / 1e3), "unit": "Pfaffians/s", "ms_per_batch": ms2,
+                "value": total / (ms2 / 1e3), "unit": "Pfaffians/s", "ms_per_batch": ms2,
                 "api": "skew_pfaffian_batched (two-step elimination; no T, L output)",
                 "max_rel_logabs_diff_vs_ltlt_batched": agree, "signs_equal": signs_equal,
-                "speedup_vs_plain_calls": (len(views) / (ms2 / 1e3)) / plain_rate,
-                "cuda_graph_replay": {"value": len(views) / (ms3 / 1e3), "unit": "Pfaffians/s",
+                "speedup_vs_plain_calls": (total / (ms2 / 1e3)) / plain_rate,
+                "cuda_graph_replay": {"value": total / (ms3 / 1e3), "unit": "Pfaffians/s",
                                       "ms_per_batch": ms3, "results_equal_direct_call": graph_equal}}}
 
 
@@ -434,7 +446,8 @@ def run_precision_leg(skew, inputs, torch, dev, A_host, nb_fp64, fp64_ms, fp64_t
 
 
 # ----------------------------------------------------------------------------- serving
-def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int):
+def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int,
+                    rank: int = 0, world: int = 1):
     """The serving workload: requests with even orders log-uniform in [32, 4096]
     (seed 6); request i is the leading n_i x n_i block of one seeded 4096 x 4096 skew
     matrix (every principal block of an iid N(0,1) skew matrix is one of order n_i).
@@ -443,10 +456,23 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int):
     submitted at once; and the server fed by Poisson streams at 0.5x, 0.8x and 1.2x the
     serial rate (seeded gaps), reporting p50/p99 latency from submission to completion;
     `poisson` is the 0.8x stream.  Results are consumed in submission order and released
-    at once, so a stream longer than the memory budget holds keeps flowing."""
+    at once, so a stream longer than the memory budget holds keeps flowing.  With several
+    ranks each runs its own server on a size-balanced share of the requests (at their
+    arrival times in the one global stream); rates are all requests over the slowest
+    rank's time and the latency percentiles are taken over the gathered latencies."""
+    from paper_2411_09859_gb300 import shard
     rng = np.random.default_rng(inputs.SEED_SERVING)
     logn = rng.uniform(np.log(32), np.log(4096), size=n_requests)
     sizes = np.clip(2 * np.round(np.exp(logn) / 2), 32, 4096).astype(np.int64)
+    mine = shard.balanced_bins(sizes, world)[rank] if world > 1 else np.arange(n_requests)
+
+    def gather(values):
+        if world <= 1:
+            return list(values)
+        import torch.distributed as dist
+        parts = [None] * world
+        dist.all_gather_object(parts, list(values))
+        return [v for part in parts for v in part]
     master = torch.from_numpy(inputs.skew_gaussian(4096, inputs.SEED_SERVING)).to(dev)
     views = [master[:int(n), :int(n)] for n in sizes]
     flops = float(np.sum(sizes.astype(np.float64) ** 3) / 3.0)
@@ -461,19 +487,19 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int):
             skew.pfaffian(w, stream=stream)
 
     with torch.cuda.stream(stream):
-        serial(range(min(8, n_requests)))
+        serial(mine[:8])
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        serial(range(n_requests))
+        serial(mine)
         e1.record(stream)
     torch.cuda.synchronize()
-    serial_s = e0.elapsed_time(e1) / 1e3
+    serial_s = reduce_max(e0.elapsed_time(e1) / 1e3, world, dev)
     serial_rate = n_requests / serial_s
 
     srv = skew.Server(64 << 30, n_streams=4, small_n_max=512)
-    for tk in [srv.submit(views[i]) for i in range(min(16, n_requests))]:
+    for tk in [srv.submit(views[i]) for i in mine[:16]]:
         srv.wait(tk)
         srv.release(tk)
     def consume(tickets):
@@ -485,11 +511,14 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int):
             srv.release(tk)
         return out
 
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     t0 = time.perf_counter()
-    tickets = [srv.submit(v) for v in views]
+    tickets = [srv.submit(views[i]) for i in mine]
     res = consume(tickets)
-    sat_s = time.perf_counter() - t0
-    sat_lat = np.array([r["latency_s"] for r in res]) * 1e3
+    sat_s = reduce_max(time.perf_counter() - t0, world, dev)
+    sat_lat = np.array(gather(r["latency_s"] for r in res)) * 1e3
     bad = sum(1 for r in res if r["info"] != 0)
 
     def poisson_stream(factor, seed):
@@ -497,25 +526,27 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int):
         serial rate (seeded gaps); a client thread consumes results while the stream is
         still being submitted."""
         lam = factor * serial_rate
-        gaps = np.random.default_rng(seed).exponential(1.0 / lam, size=n_poisson)
+        arrive = np.cumsum(np.random.default_rng(seed).exponential(1.0 / lam, size=n_poisson))
+        todo = [int(i) for i in mine if i < n_poisson]
         pending = queue.Queue()
         out = []
         client = threading.Thread(target=lambda: out.extend(consume(iter(pending.get, None))))
         client.start()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
         t0 = time.perf_counter()
-        next_t = t0
-        for i in range(n_poisson):
-            next_t += gaps[i]
-            delay = next_t - time.perf_counter()
+        for i in todo:
+            delay = t0 + arrive[i] - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
             pending.put(srv.submit(views[i]))
         pending.put(None)
         client.join()
-        seconds = time.perf_counter() - t0
-        if len(out) != n_poisson:
+        seconds = reduce_max(time.perf_counter() - t0, world, dev)
+        if len(out) != len(todo):
             raise RuntimeError("the serving client thread did not consume every result")
-        lat = np.array([r["latency_s"] for r in out]) * 1e3
+        lat = np.array(gather(r["latency_s"] for r in out)) * 1e3
         return out, {"rate_factor": factor, "rate_per_s": lam, "requests": n_poisson,
                      "value": n_poisson / seconds,
                      "p50_ms": float(np.percentile(lat, 50)),
@@ -528,6 +559,7 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int):
         bad += sum(1 for r in out if r["info"] != 0)
         rates.append(summary)
     srv.close()
+    bad = int(reduce_sum(bad, world, dev))
     if bad:
         raise RuntimeError(f"{bad} served requests reported a nonzero info")
     return {"metric": "served Pfaffians/s and latency", "unit": "Pfaffians/s",
@@ -544,7 +576,8 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int):
                            "speedup_vs_serial": serial_s / sat_s},
             "poisson": rates[1],
             "poisson_rates": rates,
-            "server": "budget 64 GB, 4 streams, batched kernel for n <= 512"}
+            "server": "budget 64 GB, 4 streams, batched kernel for n <= 512"
+                      + (f"; one server per rank on {world} size-balanced shares" if world > 1 else "")}
 
 
 def reduce_max(value: float, world: int, device=None) -> float:
@@ -556,6 +589,17 @@ def reduce_max(value: float, world: int, device=None) -> float:
     import torch.distributed as dist
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, world: int, device=None) -> float:
+    """Sum of `value` over the ranks (identity for a single process)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
 
@@ -666,10 +710,18 @@ def run_ours(args):
     from paper_2411_09859_gb300 import inputs
 
     world, rank, local = dist_setup(args)
-    if world > 1:
-        dist.init_process_group("nccl")
+    # one process per GPU; the modulo only matters when fewer GPUs than ranks are
+    # visible (a functional run of the N > 1 code path on one GPU, with the gloo backend
+    # chosen by SKEW_BENCH_DIST_BACKEND)
+    local = local % max(1, torch.cuda.device_count())
     torch.cuda.set_device(local)
-    skew_build.build()
+    if world > 1:
+        dist.init_process_group(os.environ.get("SKEW_BENCH_DIST_BACKEND", "nccl"))
+    # the library is built once per node, before any rank loads it
+    if int(os.environ.get("LOCAL_RANK", "0")) == 0:
+        skew_build.build()
+    if world > 1:
+        dist.barrier()
     dev = torch.device("cuda", local)
 
     n = args.n
@@ -782,12 +834,12 @@ def run_ours(args):
     batched = None
     if not args.skip_batched:
         batched = run_batched_leg(skew, inputs, torch, dev, steps=3, warmup=1,
-                                  plain_count=args.plain_calls)
+                                  plain_count=args.plain_calls, rank=rank, world=world)
 
     serving = None
     if not args.skip_serving:
         serving = run_serving_leg(skew, inputs, torch, dev, args.serve_requests,
-                                  args.serve_poisson)
+                                  args.serve_poisson, rank=rank, world=world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu_baseline:
