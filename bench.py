@@ -609,6 +609,49 @@ def whole_job_rate(units_per_rank: float, seconds_max: float, world: int) -> flo
     return world * units_per_rank / seconds_max
 
 
+def parse_cpulist(text: str) -> set:
+    """CPU numbers of a sysfs cpulist ("0-3,8,10-11")."""
+    cpus = set()
+    for part in text.strip().split(","):
+        if not part:
+            continue
+        lo, _, hi = part.partition("-")
+        cpus.update(range(int(lo), int(hi or lo) + 1))
+    return cpus
+
+
+def gpu_local_cpus(torch, local: int):
+    """The CPUs next to GPU `local` (its PCI device's local_cpulist) that this process
+    may run on, or None when that cannot be read."""
+    try:
+        pr = torch.cuda.get_device_properties(local)
+        bus = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{bus}/local_cpulist") as f:
+            near = parse_cpulist(f.read())
+        mine = os.sched_getaffinity(0) & near
+        return mine or None
+    except (OSError, ValueError, AttributeError):
+        return None
+
+
+def pinned_near_gpu(torch, local: int, make):
+    """Calls make() (which allocates and fills page-locked host buffers) with this
+    process bound to the CPUs next to the GPU, so that the pages are placed in the
+    memory nearest to it (first touch); the previous affinity is restored after.  On
+    a two-socket host, buffers on the far node are copied at a fraction of the link's
+    rate (measured on a GB300 node: 2 x 2 GB per factorization took about 100 ms
+    longer from the far node)."""
+    near = gpu_local_cpus(torch, local)
+    if near is None:
+        return make(), None
+    before = os.sched_getaffinity(0)
+    os.sched_setaffinity(0, near)
+    try:
+        return make(), len(near)
+    finally:
+        os.sched_setaffinity(0, before)
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -800,25 +843,34 @@ def run_ours(args):
     # ---- end to end through the host-buffer C-ABI call (pinned host buffers)
     e2e = None
     if not args.skip_e2e:
-        A_pin = torch.empty((n, n), dtype=torch.float64).pin_memory().t()
-        A_pin.copy_(torch.from_numpy(A_host))
-        L_pin = torch.empty((n, n), dtype=torch.float64).pin_memory().t()
-        t_pin = torch.empty(n - 1, dtype=torch.float64).pin_memory()
-        p_pin = torch.empty(n, dtype=torch.int32).pin_memory()
+        def make_pinned():
+            a = torch.empty((n, n), dtype=torch.float64).pin_memory().t()
+            a.copy_(torch.from_numpy(A_host))
+            lo = torch.empty((n, n), dtype=torch.float64).pin_memory().t()
+            lo.zero_()
+            return (a, lo, torch.zeros(n - 1, dtype=torch.float64).pin_memory(),
+                    torch.zeros(n, dtype=torch.int32).pin_memory())
+        (A_pin, L_pin, t_pin, p_pin), near_cpus = pinned_near_gpu(torch, local, make_pinned)
         A_np, L_np, t_np, p_np = A_pin.numpy(), L_pin.numpy(), t_pin.numpy(), p_pin.numpy()
         skew.ltlt_host(A_np, True, nb, L_out=L_np, t_out=t_np, piv_out=p_np)
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
+        step_ends = []
         for _ in range(K):
             res = skew.ltlt_host(A_np, True, nb, L_out=L_np, t_out=t_np, piv_out=p_np)
+            step_ends.append(time.perf_counter())
             if res[5] != 0:
                 raise RuntimeError(f"host-buffer factorization reported info={res[5]}")
-        el = reduce_max(time.perf_counter() - t0, world, dev)
+        el = reduce_max(step_ends[-1] - t0, world, dev)
+        step_ms = list(np.diff([t0] + step_ends) * 1e3)
         e2e = {"value": whole_job_rate(K * factorization_flops(n), el, world) / 1e12, "unit": UNIT,
                "h2d_bytes_per_step": n * n * 8,
                "d2h_bytes_per_step": n * n * 8 + (n - 1) * 8 + n * 4 + 8 + 4 + 4,
-               "ms_per_step": el / K * 1e3,
+               "ms_per_step": el / K * 1e3, "step_ms_rank0": [float(x) for x in step_ms],
+               "host_buffers": ("page-locked, allocated while bound to the "
+                                f"{near_cpus} CPUs next to the GPU" if near_cpus else
+                                "page-locked (GPU-local CPUs unknown: not bound)"),
                "api": "skew_ltlt_host (page-locked host A in, L, t, piv, log|Pf|, sign out)"}
 
     precision = None
