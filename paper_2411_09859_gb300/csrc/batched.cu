@@ -419,6 +419,7 @@ __device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_
                 int bi = 0;
                 while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
                 const int bj = tile - bi * (bi + 1) / 2;
+                const bool diag = bi == bj;   // a tile on the diagonal: 10 of its 16 sub-tiles
                 double acc[4][4][2];
 #pragma unroll
                 for (int mi = 0; mi < 4; ++mi)
@@ -449,7 +450,8 @@ __device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_
                     for (int mi = 0; mi < 4; ++mi)
 #pragma unroll
                         for (int ni = 0; ni < 4; ++ni)
-                            dmma884(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
+                            if (!diag || mi >= ni)   // above the diagonal: nothing stored
+                                dmma884(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
                 }
 #pragma unroll
                 for (int mi = 0; mi < 4; ++mi) {
@@ -655,6 +657,7 @@ __device__ void pfaff_one_twostep(const skew_problem &P, double *logabs, int32_t
                 int bi = 0;
                 while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
                 const int bj = tile - bi * (bi + 1) / 2;
+                const bool diag = bi == bj;   // a tile on the diagonal: 10 of its 16 sub-tiles
                 double acc[4][4][2];
 #pragma unroll
                 for (int mi = 0; mi < 4; ++mi)
@@ -687,7 +690,8 @@ __device__ void pfaff_one_twostep(const skew_problem &P, double *logabs, int32_t
                     for (int mi = 0; mi < 4; ++mi)
 #pragma unroll
                         for (int ni = 0; ni < 4; ++ni)
-                            dmma884(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
+                            if (!diag || mi >= ni)   // above the diagonal: nothing stored
+                                dmma884(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
                 }
 #pragma unroll
                 for (int mi = 0; mi < 4; ++mi) {
