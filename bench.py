@@ -451,11 +451,14 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int,
     """The serving workload: requests with even orders log-uniform in [32, 4096]
     (seed 6); request i is the leading n_i x n_i block of one seeded 4096 x 4096 skew
     matrix (every principal block of an iid N(0,1) skew matrix is one of order n_i).
-    Compared: serial back-to-back skew_pfaffian calls; the continuous-batching server
-    (64 GB budget, 4 streams, batched kernel up to n = 512) with all requests
-    submitted at once; and the server fed by Poisson streams at 0.5x, 0.8x and 1.2x the
-    serial rate (seeded gaps), reporting p50/p99 latency from submission to completion;
-    `poisson` is the 0.8x stream.  Results are consumed in submission order and released
+    The requests ask for the Pfaffian only (SKEW_SERVE_PFAFFIAN: the two-step
+    elimination).  Compared: serial back-to-back skew_pfaffian_twostep calls (the same
+    algorithm, so the same accuracy); the continuous-batching server (64 GB budget, 4
+    streams, batched kernel up to n = 512) with all requests submitted at once; and the
+    server fed by Poisson streams at 0.5x, 0.8x and 1.2x the serial rate (seeded gaps),
+    reporting p50/p99 latency from submission to completion; `poisson` is the 0.8x
+    stream.  `factors_kept` repeats the serial and saturation runs with requests that
+    keep their LTL^T factors (SKEW_SERVE_FACTORS; serial skew_pfaffian calls).  Results are consumed in submission order and released
     at once, so a stream longer than the memory budget holds keeps flowing.  With several
     ranks each runs its own server on a size-balanced share of the requests (at their
     arrival times in the one global stream); rates are all requests over the slowest
@@ -479,29 +482,37 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int,
     stream = torch.cuda.Stream(device=dev)
     work = skew.fortran_empty(4096, 4096, dev)
 
-    def serial(idx):
+    def serial(idx, pf_only):
         for i in idx:
             n = int(sizes[i])
             w = work[:n, :n]
             w.copy_(views[i])
-            skew.pfaffian(w, stream=stream)
+            if pf_only:
+                skew.pfaffian_twostep(w, stream=stream)
+            else:
+                skew.pfaffian(w, stream=stream)
 
-    with torch.cuda.stream(stream):
-        serial(mine[:8])
+    def time_serial(pf_only):
+        with torch.cuda.stream(stream):
+            serial(mine[:8], pf_only)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            serial(mine, pf_only)
+            e1.record(stream)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        serial(mine)
-        e1.record(stream)
-    torch.cuda.synchronize()
-    serial_s = reduce_max(e0.elapsed_time(e1) / 1e3, world, dev)
+        return reduce_max(e0.elapsed_time(e1) / 1e3, world, dev)
+
+    serial_s = time_serial(True)
     serial_rate = n_requests / serial_s
+    serial_f_s = time_serial(False)
 
     srv = skew.Server(64 << 30, n_streams=4, small_n_max=512)
-    for tk in [srv.submit(views[i]) for i in mine[:16]]:
-        srv.wait(tk)
-        srv.release(tk)
+    for pf in (True, False):
+        for tk in [srv.submit(views[i], pfaffian_only=pf) for i in mine[:16]]:
+            srv.wait(tk)
+            srv.release(tk)
     def consume(tickets):
         # results are read in submission order and released at once, as a client
         # would: the factors of a long stream do not all fit the budget together
@@ -511,15 +522,20 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int,
             srv.release(tk)
         return out
 
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    t0 = time.perf_counter()
-    tickets = [srv.submit(views[i]) for i in mine]
-    res = consume(tickets)
-    sat_s = reduce_max(time.perf_counter() - t0, world, dev)
-    sat_lat = np.array(gather(r["latency_s"] for r in res)) * 1e3
-    bad = sum(1 for r in res if r["info"] != 0)
+    def saturation(pf_only):
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        t0 = time.perf_counter()
+        tickets = [srv.submit(views[i], pfaffian_only=pf_only) for i in mine]
+        res = consume(tickets)
+        sec = reduce_max(time.perf_counter() - t0, world, dev)
+        lat = np.array(gather(r["latency_s"] for r in res)) * 1e3
+        return sec, lat, sum(1 for r in res if r["info"] != 0)
+
+    sat_s, sat_lat, bad = saturation(True)
+    sat_f_s, sat_f_lat, bad_f = saturation(False)
+    bad += bad_f
 
     def poisson_stream(factor, seed):
         """Requests 0 .. n_poisson-1 arriving as a Poisson stream at `factor` x the
@@ -540,7 +556,7 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int,
             delay = t0 + arrive[i] - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            pending.put(srv.submit(views[i]))
+            pending.put(srv.submit(views[i], pfaffian_only=True))
         pending.put(None)
         client.join()
         seconds = reduce_max(time.perf_counter() - t0, world, dev)
@@ -567,8 +583,10 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int,
                          "leading blocks of one seeded 4096^2 iid N(0,1) skew matrix"
                          + ("" if n_requests >= 20000 else "; the 20000-request stream is "
                             "shortened to keep the run short")),
+            "requests": "Pfaffian only (SKEW_SERVE_PFAFFIAN, two-step elimination)",
             "serial_plain_calls": {"value": serial_rate, "seconds": serial_s,
-                                   "tflops": flops / serial_s / 1e12},
+                                   "tflops": flops / serial_s / 1e12,
+                                   "api": "skew_pfaffian_twostep, one call per request, back to back"},
             "saturation": {"value": n_requests / sat_s, "seconds": sat_s,
                            "tflops": flops / sat_s / 1e12,
                            "p50_ms": float(np.percentile(sat_lat, 50)),
@@ -576,6 +594,14 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int,
                            "speedup_vs_serial": serial_s / sat_s},
             "poisson": rates[1],
             "poisson_rates": rates,
+            "factors_kept": {
+                "requests": "SKEW_SERVE_FACTORS (pivoted LTL^T, t and piv kept)",
+                "serial_plain_calls": {"value": n_requests / serial_f_s, "seconds": serial_f_s,
+                                       "api": "skew_pfaffian, one call per request, back to back"},
+                "saturation": {"value": n_requests / sat_f_s, "seconds": sat_f_s,
+                               "p50_ms": float(np.percentile(sat_f_lat, 50)),
+                               "p99_ms": float(np.percentile(sat_f_lat, 99)),
+                               "speedup_vs_serial": serial_f_s / sat_f_s}},
             "server": "budget 64 GB, 4 streams, batched kernel for n <= 512"
                       + (f"; one server per rank on {world} size-balanced shares" if world > 1 else "")}
 

@@ -378,9 +378,9 @@ int skew_ltlt_batched(int count, const skew_problem *problems, double *logabs,
 /*
  * skew_pfaffian_batched -- the Pfaffians of `count` independent skew matrices by the
  * two-step elimination of skew_pfaffian_twostep, each matrix factored in place by one
- * CTA of a persistent kernel (largest orders first): panels of 16 columns (8 pairs)
- * formed left-looking in shared memory, one skew rank-2k update per panel on FP64
- * tensor cores.  Arguments as for skew_ltlt_batched, with these differences: max_n
+ * CTA of a persistent kernel (largest orders first): panels (8, 16 or 32 columns, per
+ * order bucket from the table of skew_set_batched_nb_table) formed left-looking in
+ * shared memory, one skew rank-2k update per panel on FP64 tensor cores.  Arguments as for skew_ltlt_batched, with these differences: max_n
  * <= 512; problem j's `t` (n/2 doubles, required for n >= 2) receives the pivot-block
  * entries a_i and its `piv` (n int32) the even-step exchanges; its `L` is not used;
  * info[j] = 1 + the first even k with a_(k/2) = 0 (Pf = 0), -100 for a non-finite
@@ -398,11 +398,12 @@ int skew_pfaffian_batched(int count, const skew_problem *problems, double *logab
  * returns at once with a ticket.  A worker thread of the server admits queued
  * requests in arrival order as soon as their device memory (a copy of the matrix, t,
  * piv, and L if asked for) fits in the budget; it launches admitted work on the first
- * free stream -- all admitted requests of order <= small_n_max together in one
- * skew_ltlt_batched launch, larger ones one at a time through skew_ltlt /
- * skew_pfaffian -- so that requests arriving while others are on the GPU are batched
- * and run beside them on other streams.  Results (log|Pf|, sign, info, and the
- * factors t, piv, L in device memory) stay resident until skew_server_release.
+ * free stream -- all admitted small requests of one kind together in one batched
+ * launch, larger ones one at a time (the kinds and the calls they use are listed at
+ * SKEW_SERVE_FACTORS below) -- so that requests arriving while others are on the GPU
+ * are batched and run beside them on other streams.  Results (log|Pf|, sign, info,
+ * and the factors t, piv, L in device memory when the request keeps them) stay
+ * resident until skew_server_release.
  * The matrix a request points to must be fully written when it is submitted (its
  * producing work complete), and is read before the request completes: keep it
  * unchanged until skew_server_poll reports it done.  A request whose buffers exceed
@@ -417,10 +418,24 @@ typedef struct skew_server skew_server;
 int skew_server_create(size_t device_budget_bytes, int n_streams, int small_n_max,
                        skew_server **out);
 
+/* What a request asks for (argument 5 of skew_server_submit):
+ *   SKEW_SERVE_FACTORS    log|Pf|, sign, and the factors t, piv kept on the device
+ *                         (the pivoted LTL^T: skew_ltlt_batched, skew_pfaffian)
+ *   SKEW_SERVE_FACTORS_L  the same with L kept too (skew_ltlt_batched, skew_ltlt)
+ *   SKEW_SERVE_PFAFFIAN   log|Pf| and sign only, by the two-step elimination
+ *                         (skew_pfaffian_batched for orders up to min(small_n_max, 512),
+ *                         else skew_pfaffian_twostep, or skew_pfaffian above its order
+ *                         limit); no factors are kept: skew_server_wait returns NULL t
+ *                         and piv, skew_server_copy_factors returns -3.
+ * Requests of different kinds are never batched together. */
+#define SKEW_SERVE_FACTORS 0
+#define SKEW_SERVE_FACTORS_L 1
+#define SKEW_SERVE_PFAFFIAN 2
+
 /*   1 server, 2 n, 3 A (device, lda x n, strictly lower triangle read, not modified),
- *   4 lda, 5 want_L (nonzero: keep L), 6 ticket (out) */
+ *   4 lda, 5 mode (SKEW_SERVE_*; -5 for another value), 6 ticket (out) */
 int skew_server_submit(skew_server *server, int64_t n, const double *A, int64_t lda,
-                       int want_L, uint64_t *ticket);
+                       int mode, uint64_t *ticket);
 
 /* done = 1 once the request has completed (or failed), else 0.  -2: unknown ticket. */
 int skew_server_poll(skew_server *server, uint64_t ticket, int *done);
@@ -441,8 +456,9 @@ int skew_server_wait(skew_server *server, uint64_t ticket, double timeout_s, dou
 int skew_server_release(skew_server *server, uint64_t ticket);
 
 /* Copy a completed request's factors to host buffers (any of them NULL to skip):
- * t_host (n-1 values), piv_host (n), L_host (ldl x n; the request must have kept L).
- * Synchronous.  SKEW_ERR_BUSY if the request has not completed. */
+ * t_host (n-1 values), piv_host (n), L_host (ldl x n; the request must have kept L,
+ * else -5).  Synchronous.  SKEW_ERR_BUSY if the request has not completed; -3 for a
+ * SKEW_SERVE_PFAFFIAN request (it keeps no factors). */
 int skew_server_copy_factors(skew_server *server, uint64_t ticket, double *t_host,
                              int32_t *piv_host, double *L_host, int64_t ldl);
 

@@ -448,6 +448,9 @@ def pfaffian_batched(As, stream=None, max_n: int | None = None, table=None, outs
     return logabs, sign, info, as_, pivs
 
 
+SERVE_FACTORS, SERVE_FACTORS_L, SERVE_PFAFFIAN = 0, 1, 2   # SKEW_SERVE_*
+
+
 class Server:
     """Continuous-batching server (skew_server_*).  Requests are column-major float64
     CUDA tensors; keep each one unchanged until its result has been waited for."""
@@ -458,12 +461,17 @@ class Server:
                                                               small_n_max, ctypes.byref(self._h)))
         self._keep = {}
 
-    def submit(self, A, want_L: bool = False) -> int:
+    def submit(self, A, want_L: bool = False, pfaffian_only: bool = False) -> int:
+        """Queue A; want_L keeps L with the factors, pfaffian_only asks for log|Pf|
+        and sign alone (two-step elimination, no factors kept)."""
+        if want_L and pfaffian_only:
+            raise ValueError("a Pfaffian-only request keeps no L")
         n = A.shape[0]
         lda = _colmajor("A", A, n)
         tk = ctypes.c_uint64()
+        mode = SERVE_PFAFFIAN if pfaffian_only else (SERVE_FACTORS_L if want_L else SERVE_FACTORS)
         _check("skew_server_submit", lib().skew_server_submit(
-            self._h, n, _ptr(A) if n > 0 else None, lda, 1 if want_L else 0, ctypes.byref(tk)))
+            self._h, n, _ptr(A) if n > 0 else None, lda, mode, ctypes.byref(tk)))
         self._keep[tk.value] = A
         return tk.value
 

@@ -4,10 +4,12 @@
 //   - admits queued requests in arrival order while their device memory fits in the
 //     budget (the matrix copy, t, piv, optionally L): admission happens as soon as
 //     memory frees up, also while other work is running;
-//   - launches admitted work on the first free stream: all admitted small requests
-//     (n <= small_n_max) together in one skew_ltlt_batched launch, or one large
-//     request as a skew_ltlt / skew_pfaffian call -- so work submitted while other
-//     work is on the GPU is batched and overlaps it on other streams;
+//   - launches admitted work on the first free stream: all admitted small requests of
+//     one kind together in one batched launch (skew_ltlt_batched for requests that keep
+//     their factors, skew_pfaffian_batched for Pfaffian-only ones), or one large
+//     request as a skew_ltlt / skew_pfaffian / skew_pfaffian_twostep call -- so work
+//     submitted while other work is on the GPU is batched and overlaps it on other
+//     streams;
 //   - detects completions through events and wakes waiters.
 // Factors stay resident in device memory until skew_server_release.
 #include <chrono>
@@ -36,7 +38,7 @@ enum class ReqState { Queued, Admitted, Running, Done, Failed };
 struct Request {
     uint64_t ticket = 0;
     int64_t n = 0;
-    bool want_L = false;
+    int mode = SKEW_SERVE_FACTORS;  // SKEW_SERVE_*
     const double *src = nullptr;   // caller's matrix (read before completion)
     int64_t src_ld = 0;
     double *A = nullptr, *L = nullptr, *t = nullptr;
@@ -83,6 +85,13 @@ struct skew_server {
 
 namespace {
 
+// Largest order a request of this kind may have to join a batched launch (the
+// Pfaffian-only batched kernel takes orders up to 512).
+int64_t batch_limit(const skew_server *s, const Request &r) {
+    const int64_t lim = s->small_n_max;
+    return (r.mode == SKEW_SERVE_PFAFFIAN && lim > 512) ? 512 : lim;
+}
+
 size_t request_bytes(int64_t n, bool want_L) {
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t nn = (size_t)(n > 0 ? n : 1);
@@ -124,7 +133,7 @@ int materialise(Request &r, cudaStream_t st) {
     r.d_sign = static_cast<int32_t *>(p);
     SKEW_TRY_STATUS(alloc(sizeof(int32_t)));
     r.d_info = static_cast<int32_t *>(p);
-    if (r.want_L) {
+    if (r.mode == SKEW_SERVE_FACTORS_L) {
         SKEW_TRY_STATUS(alloc(nn * nn * sizeof(double)));
         r.L = static_cast<double *>(p);
     }
@@ -159,13 +168,15 @@ bool launch_next(skew_server *s, int lane_index) {
     Request &first = s->reqs[s->admitted.front()];
     ln.tickets.clear();
     int status = SKEW_OK;
-    if (first.n <= s->small_n_max) {
-        // every admitted small request goes into one batched launch
+    const bool pf_only = first.mode == SKEW_SERVE_PFAFFIAN;
+    if (first.n <= batch_limit(s, first)) {
+        // every admitted small request of the first one's kind goes into one batched
+        // launch
         std::deque<uint64_t> rest;
         int max_n = 0;
         for (uint64_t tk : s->admitted) {
             Request &r = s->reqs[tk];
-            if (r.n <= s->small_n_max) {
+            if (r.n <= batch_limit(s, r) && (r.mode == SKEW_SERVE_PFAFFIAN) == pf_only) {
                 ln.tickets.push_back(tk);
                 if (r.n > max_n) max_n = (int)r.n;
             } else {
@@ -213,7 +224,11 @@ bool launch_next(skew_server *s, int lane_index) {
             if (status == SKEW_OK) status = skew::pool_alloc((void **)&sg, count * sizeof(int32_t), ln.stream);
             if (status == SKEW_OK) status = skew::pool_alloc((void **)&inf, count * sizeof(int32_t), ln.stream);
             if (status == SKEW_OK)
-                status = skew_ltlt_batched(count, ln.d_table, la, sg, inf, max_n, nullptr, 0, ln.stream);
+                status = pf_only
+                             ? skew_pfaffian_batched(count, ln.d_table, la, sg, inf, max_n, nullptr, 0,
+                                                     ln.stream)
+                             : skew_ltlt_batched(count, ln.d_table, la, sg, inf, max_n, nullptr, 0,
+                                                 ln.stream);
             for (int i = 0; i < count && status == SKEW_OK; ++i) {
                 Request &r = s->reqs[ln.tickets[i]];
                 e = cudaMemcpyAsync(&r.host->logabs, la + i, sizeof(double), cudaMemcpyDeviceToHost, ln.stream);
@@ -235,10 +250,19 @@ bool launch_next(skew_server *s, int lane_index) {
         status = materialise(r, ln.stream);
         const int64_t ld = r.n > 1 ? r.n : 1;
         if (status == SKEW_OK) {
-            if (r.want_L) {
+            if (r.mode == SKEW_SERVE_FACTORS_L) {
                 status = skew_ltlt(r.n, r.A, ld, r.L, ld, r.t, r.piv, r.d_info, 0, nullptr, 0, ln.stream);
                 if (status == SKEW_OK)
                     status = skew_pfaffian_from_factors(r.n, r.t, r.piv, r.d_logabs, r.d_sign, ln.stream);
+            } else if (r.mode == SKEW_SERVE_PFAFFIAN) {
+                // the two-step elimination; an order too large for its panel (-1) takes
+                // the factorization's Pfaffian instead
+                status = skew_pfaffian_twostep(r.n, r.A, ld, r.d_logabs, r.d_sign, r.t, r.piv,
+                                               r.d_info, 0, SKEW_PRECISION_FP64, nullptr, 0,
+                                               ln.stream);
+                if (status == -1)
+                    status = skew_pfaffian(r.n, r.A, ld, r.d_logabs, r.d_sign, r.t, r.piv, r.d_info,
+                                           0, nullptr, 0, ln.stream);
             } else {
                 status = skew_pfaffian(r.n, r.A, ld, r.d_logabs, r.d_sign, r.t, r.piv, r.d_info, 0,
                                        nullptr, 0, ln.stream);
@@ -365,20 +389,22 @@ int skew_server_create(size_t device_budget_bytes, int n_streams, int small_n_ma
     return SKEW_OK;
 }
 
-int skew_server_submit(skew_server *s, int64_t n, const double *A, int64_t lda, int want_L,
+int skew_server_submit(skew_server *s, int64_t n, const double *A, int64_t lda, int mode,
                        uint64_t *ticket) {
     if (s == nullptr) return -1;
     if (n < 0 || n > kMaxOrder) return -2;
     if (A == nullptr && n > 0) return -3;
     if (lda < (n > 1 ? n : 1)) return -4;
+    if (mode != SKEW_SERVE_FACTORS && mode != SKEW_SERVE_FACTORS_L && mode != SKEW_SERVE_PFAFFIAN)
+        return -5;
     if (ticket == nullptr) return -6;
-    const size_t bytes = request_bytes(n, want_L != 0);
+    const size_t bytes = request_bytes(n, mode == SKEW_SERVE_FACTORS_L);
     std::lock_guard<std::mutex> lock(s->mu);
     if (bytes > s->budget) return SKEW_ERR_NOMEM;
     Request r;
     r.ticket = s->next_ticket++;
     r.n = n;
-    r.want_L = want_L != 0;
+    r.mode = mode;
     r.src = A;
     r.src_ld = lda;
     r.bytes = bytes;
@@ -424,8 +450,9 @@ int skew_server_wait(skew_server *s, uint64_t ticket, double timeout_s, double *
     if (logabs) *logabs = r.host->logabs;
     if (sign) *sign = r.host->sign;
     if (info) *info = r.host->info;
-    if (t) *t = r.t;
-    if (piv) *piv = r.piv;
+    const bool factors = r.mode != SKEW_SERVE_PFAFFIAN;   // Pfaffian-only: none kept
+    if (t) *t = factors ? r.t : nullptr;
+    if (piv) *piv = factors ? r.piv : nullptr;
     if (L) *L = r.L;
     if (latency_s) *latency_s = std::chrono::duration<double>(r.t_done - r.t_submit).count();
     return SKEW_OK;
@@ -466,6 +493,7 @@ int skew_server_copy_factors(skew_server *s, uint64_t ticket, double *t_host, in
         if (it == s->reqs.end()) return -2;
         Request &r = it->second;
         if (r.state != ReqState::Done) return r.state == ReqState::Failed ? r.status : SKEW_ERR_BUSY;
+        if (r.mode == SKEW_SERVE_PFAFFIAN) return -3;   // no factors kept
         if (L_host != nullptr && (r.L == nullptr || ldl < (r.n > 1 ? r.n : 1))) return -5;
         t = r.t;
         piv = r.piv;

@@ -73,6 +73,43 @@ def test_alone_equals_in_the_mix_and_oracle():
     srv.close()
 
 
+def test_pfaffian_only_requests_alone_in_the_mix_and_oracle():
+    """SKEW_SERVE_PFAFFIAN: small orders go to the batched two-step kernel, larger ones
+    to the two-step call; interleaved with factor requests of the same matrices, each
+    result equals the request run alone, agrees with the oracle's two-step elimination
+    and with the factor request's Pfaffian, and keeps no factors."""
+    sizes = [32, 100, 256, 300, 512, 600, 1000, 2, 1, 0, 48, 777]
+    mats = [inputs.skew_gaussian(n, 7100 + n) for n in sizes]
+    devs = [dev(A) for A in mats]
+    torch.cuda.synchronize()
+    srv = skew.Server(8 << 30, n_streams=4, small_n_max=512)
+    pairs = [(srv.submit(d, pfaffian_only=True), srv.submit(d)) for d in devs]
+    for A, d, (tp, tf) in zip(mats, devs, pairs):
+        n = A.shape[0]
+        rp, rf = srv.wait(tp, 120.0), srv.wait(tf, 120.0)
+        assert rp["t_ptr"] is None and rp["piv_ptr"] is None and rp["L_ptr"] is None
+        with pytest.raises(skew.SkewError):
+            srv.factors(tp, n)
+        la0, sg0, _, _, info0 = oracle.pfaffian_twostep(A)
+        assert rp["sign"] == sg0 == rf["sign"]
+        if sg0 != 0:
+            assert close(rp["logabs"], la0) and close(rp["logabs"], rf["logabs"])
+        if n % 2 == 0:
+            assert rp["info"] == info0
+        alone = skew.Server(8 << 30, n_streams=1, small_n_max=512)
+        ta = alone.submit(d, pfaffian_only=True)
+        ra = alone.wait(ta, 60.0)
+        assert ra["sign"] == rp["sign"] and ra["logabs"] == rp["logabs"]
+        alone.release(ta)
+        alone.close()
+        srv.release(tp)
+        srv.release(tf)
+    with pytest.raises(ValueError):
+        srv.submit(devs[0], want_L=True, pfaffian_only=True)
+    assert srv.stats() == {"used_bytes": 0, "queued": 0, "in_flight": 0}
+    srv.close()
+
+
 def test_admission_follows_budget():
     n = 400
     A = dev(inputs.skew_gaussian(n, 11))
