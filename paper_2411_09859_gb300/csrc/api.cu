@@ -14,6 +14,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace skew {
@@ -67,12 +69,20 @@ cudaEvent_t take_event() {
 }
 
 // Brackets one launch with events on `st` while profiling is enabled.
+// Each stage of a call is an NVTX range named for its kind (a host-side range around
+// the launch: it marks when the work was enqueued, which is what a profiler needs to
+// select the stage's kernels, e.g. ncu --nvtx --nvtx-include "skr2k/").  With no tool
+// attached an NVTX call returns at once.  With profiling on, the stage is also
+// bracketed by two CUDA events on its stream.
+const char *const kProfNames[] = {"prologue", "panel", "pivot_rows", "skr2k", "finish", "batched"};
+
 struct ProfScope {
     bool on;
     ProfRec r;
     cudaStream_t st;
     ProfScope(int kind, cudaStream_t stream, double flops, double bytes)
         : on(g_prof_on.load()), st(stream) {
+        nvtxRangePushA(kProfNames[kind]);
         if (!on) return;
         r.kind = kind;
         r.flops = flops;
@@ -85,6 +95,7 @@ struct ProfScope {
         }
     }
     ~ProfScope() {
+        nvtxRangePop();
         if (!on) return;
         if (cudaEventRecord(r.b, st) != cudaSuccess) {
             cudaGetLastError();

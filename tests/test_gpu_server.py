@@ -162,3 +162,31 @@ def test_destroy_with_pending_requests():
     for _ in range(20):
         srv.submit(A)
     srv.close()                              # finishes admitted work, drops the rest
+
+
+def test_cancel_and_malformed_requests():
+    import ctypes
+    lib = skew.lib()
+    n = 300
+    A = dev(inputs.skew_gaussian(n, 13))
+    per = 8 * n * n + 8 * n + 4 * n + 4096
+    srv = skew.Server(int(1.5 * per), n_streams=1, small_n_max=512)
+    tk = ctypes.c_uint64()
+    ptr = ctypes.c_void_p(A.data_ptr())
+    assert lib.skew_server_submit(srv._h, -1, ptr, n, 0, ctypes.byref(tk)) == -2   # order
+    assert lib.skew_server_submit(srv._h, n, None, n, 0, ctypes.byref(tk)) == -3   # no matrix
+    assert lib.skew_server_submit(srv._h, n, ptr, n - 1, 0, ctypes.byref(tk)) == -4  # lda
+    assert lib.skew_server_submit(srv._h, n, ptr, n, 7, ctypes.byref(tk)) == -5    # kind
+    assert lib.skew_server_release(srv._h, 10 ** 9) == -2                         # unknown
+    # a request that cannot be admitted yet is cancelled before it runs
+    t1 = srv.submit(A)
+    srv.wait(t1, 60.0)                       # done, still holding its memory
+    t2 = srv.submit(A)
+    assert srv.stats()["queued"] == 1
+    srv.release(t2)                          # cancel: dropped from the queue
+    assert srv.stats()["queued"] == 0
+    with pytest.raises(skew.SkewError):
+        srv.wait(t2, 0.1)                    # the ticket is gone
+    srv.release(t1)
+    assert srv.stats() == {"used_bytes": 0, "queued": 0, "in_flight": 0}
+    srv.close()
