@@ -15,16 +15,20 @@
 // L columns, then sets t[k] = v[k+1] and L[k+2:, k+1] = v[k+2:] / t[k].
 // Columns of L left of the panel are exchanged later (pivot_rows).
 //
-// GPU organisation: one CTA per SM (cooperative launch).  Row i is owned by thread
-// i mod (#threads) for the whole panel, so everything a step does to row i -- its
-// exchange, its scaled L entry, and the next step's v_i -- is done by one thread
-// without synchronisation.  What crosses rows is published before the one grid
-// barrier of each step: every CTA writes its best candidate (|v|, index) together
-// with that row's L values in the panel columns, and the owner of row k+1 writes
-// v[k+1] and its L row.  After the barrier every CTA knows the pivot r, t[k], the
-// new row k+1 of L (old row r) and so the next h, and goes straight on.  The
-// published data are double-buffered by step parity: a CTA can be at most one step
-// ahead of another.  Data written inside this launch are read with ld.global.cg.
+// GPU organisation: one cooperative launch per panel (its CTAs wait on each other at
+// every step).  Every row of the unfactored block has one owner thread for the whole
+// panel, so everything a step does to row i -- its exchange, its scaled L entry, and
+// the next step's v_i -- is done by one thread without synchronisation.  What crosses
+// rows is published at each step: every CTA writes its best candidate (|v|, index)
+// together with that row's L values in the panel columns, and the owner of row k+1
+// writes v[k+1] and its L row.  Once every CTA has published, each knows the pivot r,
+// t[k], the new row k+1 of L (old row r) and so the next h, and goes straight on.
+// The published data are double-buffered by step parity: a CTA can be at most one
+// step ahead of another.  Data written inside this launch are read with ld.global.cg.
+// Two variants: the shared-memory panel (the panel's L rows in shared memory, one
+// thread per row, the grid sized by panel_grid) for panels of at most 96 columns whose
+// rows fit one per thread, and the global-memory panel (L in global memory, rows
+// strided over all threads, a grid barrier per step) for the rest.
 #include <cfloat>
 #include <climits>
 
@@ -231,8 +235,8 @@ panel_global_kernel(PanelArgs a) {
 // There is no separate grid barrier: each CTA publishes its step-k partial with a
 // release store of a step tag, and every CTA's warp 0 acquires all G tags -- the
 // gather of the argmax candidates is the barrier.  Rows are dealt to CTAs in chunks
-// of 32 (one warp) round-robin, so the rows of a step are spread over all SMs and
-// each warp's accesses to a column are coalesced.
+// of 32 (one warp) round-robin, so the rows of a step are spread over all the panel's
+// CTAs and each warp's accesses to a column are coalesced.
 // ------------------------------------------------------------------------------------
 constexpr int kSmemMaxNb = 96;
 
