@@ -240,10 +240,6 @@ panel_global_kernel(PanelArgs a) {
 // ------------------------------------------------------------------------------------
 constexpr int kSmemMaxNb = 96;
 
-__device__ __forceinline__ void st_release_u32_gpu(unsigned int *p, unsigned int v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 __global__ void __launch_bounds__(kPanelThreads)
 panel_smem_kernel(PanelArgs a) {
     extern __shared__ double s_L[];          // [q][threadIdx.x], q < kend - k0
@@ -540,7 +536,7 @@ panel_smem_kernel(PanelArgs a) {
         }
     }
     // tags of this launch were base+1 .. base+(kend-k0); the next launch starts above
-    if (blockIdx.x == 0 && tid == 0) st_release_u32_gpu(&ctrl->bar_gen, base + (unsigned int)(kend - k0) + 1u);
+    if (blockIdx.x == 0 && tid == 0) st_release_u32(&ctrl->bar_gen, base + (unsigned int)(kend - k0) + 1u);
 }
 
 }  // namespace

@@ -34,10 +34,6 @@ namespace {
 
 constexpr int kTsMaxNb = 96;     // panel width (columns), 48 pairs: 192 KB of rows
 
-__device__ __forceinline__ void st_release_gpu(unsigned int *p, unsigned int v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 __global__ void __launch_bounds__(kPanelThreads)
 twostep_panel_kernel(TwoStepArgs A) {
     extern __shared__ double s_S[];                 // [c][tid]: c = 2q: l_q, 2q+1: y_q
@@ -349,7 +345,7 @@ twostep_panel_kernel(TwoStepArgs A) {
         for (int c = 0; c < 2 * npairs; ++c) A.V[i + (int64_t)c * ldv] = S(c);
     // tags of this launch were base+1 .. base+npairs; the next launch starts above
     if (blockIdx.x == 0 && tid == 0)
-        st_release_gpu(&ctrl->bar_gen, base + (unsigned int)npairs + 1u);
+        st_release_u32(&ctrl->bar_gen, base + (unsigned int)npairs + 1u);
 }
 
 // log|Pf| = sum_j log|a_j|, sign = det(P) prod_j sign(-a_j): one CTA, each thread a
