@@ -177,16 +177,17 @@ struct PanelArgs {
 // `sms` CTAs and the panel is at most 96 columns wide, else the global-memory one.
 int launch_panel(const PanelArgs &a, int sms, cudaStream_t stream);
 
-// CTAs of a shared-memory panel.  Up to 64 x 128 rows, one CTA per 128 rows (four
-// warps of rows: the CTA's FP64 gemv runs on all four schedulers of its SM, as fast as
-// one warp per CTA on one scheduler, with a quarter of the CTAs in each grid-wide
-// exchange); above that, 64 CTAs unless more are needed for one row per thread.  Fewer
-// CTAs mean fewer participants in each step's exchange (and a shorter wait for the
-// slowest) at the price of more rows per CTA for the gemv.  Measured at n = 16384:
-// caps of 48 to 96 CTAs were all faster than 152, 64 the fastest; 128 rather than 32
-// rows per CTA below 8192 rows took the panel from 107.0 to 105.7 ms (n = 4096:
-// 25.0 to 24.2 ms).
-constexpr int64_t kPanelGridCap = 64;
+// CTAs of a shared-memory panel.  One CTA per 128 rows (four warps of rows: the CTA's
+// FP64 gemv runs on all four schedulers of its SM, as fast as one warp per CTA on one
+// scheduler, with a quarter of the CTAs in each grid-wide exchange), at most 96 CTAs
+// unless more are needed for one row per thread.  Fewer CTAs mean fewer participants
+// in each step's exchange (and a shorter wait for the slowest) at the price of more
+// rows per CTA for the gemv.  Measured at n = 16384 (panel ms, FP64 update): 96 / 128
+// / 160 / 256 rows per CTA with caps of 48 / 64 / 96 CTAs gave 110.8 / 107.5 / 107.0,
+// 110.5 / 107.5 / 106.4, 111.1 / 108.1 / 106.7, 119.2 / 119.2 / 119.5 (n = 4096:
+// 24.4 - 24.7 ms for 96 to 160 rows, 28.3 for 256); one CTA per 32 rows and at most
+// 152 had given 117.2 ms.
+constexpr int64_t kPanelGridCap = 96;
 constexpr int64_t kPanelRowsPerCta = 128;
 inline int64_t panel_grid(int64_t rows, int sms) {
     int64_t g = (rows + kPanelRowsPerCta - 1) / kPanelRowsPerCta;
