@@ -80,6 +80,25 @@ def workload_config(n: int, nb: int, seed: int) -> dict:
             "parallelism": "independent replicas (one matrix per GPU)"}
 
 
+def table_nb(n: int) -> int:
+    """The panel width the library picks for order n (nb = 0): from the saved tuned
+    table when there is one, else its built-in rule (16 up to 256, 32 up to 2048, 64).
+    Read from the file here so that the reference arm, which runs no GPU code, reports
+    the same configuration as the GPU arm."""
+    path = os.path.join(ROOT, "paper_2411_09859_gb300", "nb_table.json")
+    try:
+        with open(path) as f:
+            table = json.load(f).get("table", [])
+    except (OSError, ValueError):
+        table = []
+    for hi, nb in table:
+        if n <= hi:
+            return int(nb)
+    if table:
+        return int(table[-1][1])
+    return 16 if n <= 256 else (32 if n <= 2048 else 64)
+
+
 # ----------------------------------------------------------------------------- peaks
 def fp64_peak():
     """FP64 tensor peak per the measured bf16 figure x the nominal FP64:bf16 ratio."""
@@ -707,7 +726,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_full * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": workload_config(n, args.nb, seed),
+            "config": workload_config(n, args.nb if args.nb > 0 else table_nb(n), seed),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"],
                              "kind": "oracle", "sample": last["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
