@@ -42,6 +42,23 @@ __device__ __forceinline__ Cand warp_cand(Cand x) {
     return x;
 }
 
+// The same reduction with warp reduce instructions, the result valid in every lane:
+// the largest |v| bits (high word, then low word among the lanes that tie on it), then
+// the lowest row among the lanes that tie on both.
+__device__ __forceinline__ Cand warp_cand_all(Cand x) {
+    const unsigned long long m = x.raw & kAbs;
+    const unsigned int hi = (unsigned int)(m >> 32), lo = (unsigned int)m;
+    const unsigned int mh = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned int ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+    const bool top = (hi == mh) && (lo == ml);
+    const unsigned int mi = __reduce_min_sync(0xffffffffu, top ? (unsigned int)x.i : 0xffffffffu);
+    const unsigned int win = __ballot_sync(0xffffffffu, top && (unsigned int)x.i == mi);
+    Cand r;
+    r.raw = __shfl_sync(0xffffffffu, x.raw, __ffs((int)win) - 1);
+    r.i = (int)mi;
+    return r;
+}
+
 struct BatchShared {
     unsigned long long w_raw[kBatchThreads / 32];
     int w_i[kBatchThreads / 32];
@@ -251,28 +268,24 @@ struct BlkShared {
     int bad;
 };
 
+// argmax over the candidates of all threads (and the OR of their non-finite flags),
+// valid in every thread on return.  One CTA barrier: each warp leaves its best in
+// shared memory, then every warp reduces those itself.  The per-warp slots are next
+// written by the following call, which comes after at least one more CTA barrier.
 __device__ Cand blk_cand(Cand x, bool bad, BlkShared &sh, bool &any_bad) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    x = warp_cand(x);
+    x = warp_cand_all(x);
     const int wb = __any_sync(0xffffffffu, bad);
     if (lane == 0) { sh.w_raw[w] = x.raw; sh.w_i[w] = x.i; sh.w_bad[w] = wb; }
     __syncthreads();
-    if (w == 0) {
-        Cand y;
-        y.raw = 0ull;
-        y.i = INT_MAX;
-        int b = 0;
-        if (lane < kBlkThreads / 32) { y.raw = sh.w_raw[lane]; y.i = sh.w_i[lane]; b = sh.w_bad[lane]; }
-        y = warp_cand(y);
-        b = __any_sync(0xffffffffu, b);
-        if (lane == 0) { sh.best_raw = y.raw; sh.best_i = y.i; sh.bad = b; }
-    }
-    __syncthreads();
-    Cand r;
-    r.raw = sh.best_raw;
-    r.i = sh.best_i;
-    any_bad = sh.bad != 0;
-    return r;
+    Cand y;
+    y.raw = 0ull;
+    y.i = INT_MAX;
+    int b = 0;
+    if (lane < kBlkThreads / 32) { y.raw = sh.w_raw[lane]; y.i = sh.w_i[lane]; b = sh.w_bad[lane]; }
+    y = warp_cand_all(y);
+    any_bad = __any_sync(0xffffffffu, b) != 0;
+    return y;
 }
 
 // smem: Lp[NB][nmax] (panel L columns), Ws[NB/2+1][nmax] (odd W columns),
@@ -339,6 +352,9 @@ __device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_
             const Cand best = blk_cand(c, bad, sh, any_bad);
             nonfinite |= any_bad;
             const int r = (best.i == INT_MAX) ? p : best.i;
+            // the exchange and the new L column in one phase: the column takes its
+            // values from v before the exchange (row r gets old row p's v)
+            const double tau = sv[r], vp = sv[p];
             if (r != p) {
                 double *colp = X + (int64_t)p * ldx;
                 for (int i = p + 1 + tid; i < n; i += nthr) {
@@ -361,22 +377,17 @@ __device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_
                     Lp[q * nmax + p] = Lp[q * nmax + r];
                     Lp[q * nmax + r] = tmp;
                 }
-                if (tid == 0) {
-                    const double tmp = sv[p];
-                    sv[p] = sv[r];
-                    sv[r] = tmp;
-                }
             }
-            __syncthreads();
-            const double tau = sv[p];
             if (tid == 0) {
                 sh.t[nq] = tau;
                 t[k] = tau;
                 piv[p] = r;
             }
             double *lnew = Lp + (size_t)nq * nmax;             // panel column k+1
-            for (int i = p + tid; i < n; i += nthr)
-                lnew[i] = (i == p) ? 1.0 : ((tau != 0.0) ? sv[i] / tau : 0.0);
+            for (int i = p + tid; i < n; i += nthr) {
+                const double val = (i == r) ? vp : sv[i];
+                lnew[i] = (i == p) ? 1.0 : ((tau != 0.0) ? val / tau : 0.0);
+            }
             __syncthreads();
         }
         const int s = kend;
@@ -595,9 +606,22 @@ __device__ void pfaff_one_twostep(const skew_problem &P, double *logabs, int32_t
             const Cand best = blk_cand(cd, bad, sh, any_bad);
             nonfinite |= any_bad;
             const int r = (best.i == INT_MAX) ? p : best.i;
+            // the exchange and the coefficients of the new row p in one phase: each
+            // thread handling a panel vector c swaps its rows p and r and writes the
+            // coefficient that vector's old row r gives (h[2q] = y_q[p], h[2q+1] =
+            // -l_q[p] of the new row p); v is taken before the exchange below
+            const double a = sv[r], vp = sv[p];
+            for (int c = tid; c < nc; c += nthr) {
+                const double vr = Vp[(size_t)c * nmax + r];
+                if (r != p) {
+                    Vp[(size_t)c * nmax + r] = Vp[(size_t)c * nmax + p];
+                    Vp[(size_t)c * nmax + p] = vr;
+                }
+                if (c & 1) sh.t[c - 1] = vr;
+                else sh.t[c + 1] = -vr;
+            }
             if (r != p) {
-                // exchange of indices p and r in X[p:, p:] (lower storage), in the panel's
-                // vectors and in v
+                // exchange of indices p and r in X[p:, p:] (lower storage)
                 double *colp = X + (int64_t)p * ldx;
                 for (int i = p + 1 + tid; i < n; i += nthr) {
                     if (i < r) {
@@ -614,32 +638,19 @@ __device__ void pfaff_one_twostep(const skew_problem &P, double *logabs, int32_t
                         colr[i] = tmp;
                     }
                 }
-                for (int c = tid; c < nc; c += nthr) {
-                    const double tmp = Vp[(size_t)c * nmax + p];
-                    Vp[(size_t)c * nmax + p] = Vp[(size_t)c * nmax + r];
-                    Vp[(size_t)c * nmax + r] = tmp;
-                }
-                if (tid == 0) {
-                    const double tmp = sv[p];
-                    sv[p] = sv[r];
-                    sv[r] = tmp;
-                }
             }
-            __syncthreads();
-            const double a = sv[p];
             if (tid == 0) {
                 aout[k / 2] = a;
                 piv[p] = r;
             }
-            // y = X[:, k+1] + sum_c Vp[c][i] h[c] with h from the new row k+1;  l = v / a
-            for (int c = tid; c < nc; c += nthr)
-                sh.t[c] = (c & 1) ? -Vp[(size_t)(c - 1) * nmax + p] : Vp[(size_t)(c + 1) * nmax + p];
             __syncthreads();
+            // y = X[:, k+1] + sum_c Vp[c][i] h[c] with h from the new row k+1;  l = v / a
             const double *colp = X + (int64_t)p * ldx;
             for (int i = p + 1 + tid; i < n; i += nthr) {
                 double y = colp[i];
                 for (int c = 0; c < nc; ++c) y += Vp[(size_t)c * nmax + i] * sh.t[c];
-                Vp[(size_t)nc * nmax + i] = (a != 0.0) ? sv[i] / a : 0.0;
+                const double val = (i == r) ? vp : sv[i];
+                Vp[(size_t)nc * nmax + i] = (a != 0.0) ? val / a : 0.0;
                 Vp[(size_t)(nc + 1) * nmax + i] = y;
             }
             __syncthreads();
