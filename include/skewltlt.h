@@ -78,8 +78,11 @@ int skew_trim_memory(void);
 
 /*
  * Per-kernel timing.  While enabled, every kernel launch made by skew_ltlt,
- * skew_pfaffian, skew_rank2k and skew_tridiag_rankk is bracketed by two CUDA events
- * recorded on the launch's stream, tagged with the launch's algorithmic work.
+ * skew_pfaffian, skew_pfaffian_twostep, the batched calls, skew_rank2k and
+ * skew_tridiag_rankk is bracketed by two CUDA events recorded on the launch's stream,
+ * tagged with the launch's algorithmic work.  (Whether enabled or not, each such
+ * launch is also enclosed in an NVTX range named for its kind -- "prologue",
+ * "panel", "pivot_rows", "skr2k", "finish", "batched" -- for profilers.)
  * skew_profile_read waits for the recorded events, adds up the elapsed times per
  * kernel kind, and clears the record.  Kinds: 0 prologue, 1 panel, 2 pivot_rows,
  * 3 skr2k (the skew rank-2k update), 4 finish, 5 batched (the whole batched call).
