@@ -11,7 +11,18 @@ HBM before the timed region: one fresh copy per step (2.1 GB each, larger than t
 
 Under torchrun (N > 1) every rank factors its own copy of the matrix (independent
 replicas, no collective on the data path); the barrier and the max over ranks of
-the timed region give the whole-job throughput.
+the timed region give the whole-job throughput.  The batched and serving legs split
+their matrices / requests into size-balanced shares instead (one per rank), and
+report all units over the slowest rank's time.
+
+The same line carries the other forms: `e2e` (the host-buffer call, copies
+included), `precision` (split-precision update; QDQ^T accuracy at n = 2048 against
+the oracle and at n = 16384 against the closed form), `pfaffian_only` (the two-step
+elimination), `batched` (4096 matrices of order 16..256 in one launch, LTL^T and
+Pfaffian-only, with a CUDA graph replay), `serving` (Pfaffian-only requests of order
+32..4096 against serial calls, saturation and Poisson streams; the factor-keeping
+mode alongside) and `cpu_baseline` (the oracle on a bounded sample, all host cores).
+`--skip-<leg>` drops a leg; `--impl reference` times the oracle alone.
 """
 from __future__ import annotations
 
