@@ -410,7 +410,11 @@ int skew_pfaffian_batched(int count, const skew_problem *problems, double *logab
  * The matrix a request points to must be fully written when it is submitted (its
  * producing work complete), and is read before the request completes: keep it
  * unchanged until skew_server_poll reports it done.  A request whose buffers exceed
- * the whole budget is refused with SKEW_ERR_NOMEM.  All calls are thread-safe.
+ * the whole budget is refused with SKEW_ERR_NOMEM.  Admitted requests keep their
+ * buffers until skew_server_release, so a client that submits more than the budget
+ * holds must release results as it reads them: requests queued behind a full budget
+ * are admitted only as memory is released (skew_server_wait on one of them times out
+ * otherwise).  All calls are thread-safe.
  */
 typedef struct skew_server skew_server;
 
