@@ -46,6 +46,26 @@ def test_binding_declares_every_symbol():
     assert set(_native.SIGNATURES) == set(declared_functions())
 
 
+def declared_arity():
+    """Number of parameters of each prototype in include/*.h (comments removed)."""
+    arity = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"\b(skew_\w+)\s*\(([^;{]*?)\)\s*;", text):
+            args = m.group(2).strip()
+            arity[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return arity
+
+
+def test_binding_argument_counts_match_the_header():
+    from paper_2411_09859_gb300 import _native
+    arity = declared_arity()
+    assert set(arity) == set(_native.SIGNATURES)
+    wrong = {name: (len(_native.SIGNATURES[name][0]), n) for name, n in arity.items()
+             if len(_native.SIGNATURES[name][0]) != n}
+    assert not wrong, wrong
+
+
 def test_host_only_queries(lib):
     assert lib.skew_version() >= 100
     assert lib.skew_default_nb(16384) in (16, 32, 64, 128)
