@@ -241,6 +241,64 @@ def ltlt_blocked(A: np.ndarray, nb: int, fused_w: bool = False):
     return L, t, piv
 
 
+def ltlt_blocked_delayed(A: np.ndarray, nb: int):
+    """The fused right-looking ordering of Invariant 2a (Section 4.2 "Fused
+    right-looking algorithms"): the last Gauss transform of a panel is not applied at
+    the end of that panel but fused with the next one.  Its coupling t[k0] between L
+    columns k0 and k0+1 (k0 = the panel's first column) is then part of the next
+    panel: the left-looking column uses L[:, k0 .. k] with its real entries (column k0
+    is no longer the unit vector e_f, so the panel also exchanges its rows), and the
+    trailing update after the panel is X[s:, s:] -= A' T' A'^T with A' = L[s:, k0 .. s]
+    (one column more) and T' the tridiagonal block of t[k0 .. s-1].  No updated column
+    x and no separate skew rank-2 pass are needed.  The factorization reached is the
+    same as Variant 1's (same pivots, factors up to rounding)."""
+    n = A.shape[0]
+    X = full_skew_from_lower(np.asarray(A, dtype=np.float64))
+    L = np.eye(n)
+    t = np.zeros(max(n - 1, 0))
+    piv = np.arange(n)
+
+    def h_vector(k, k0):
+        # h_q for q = k0 .. k (L[k, k] = 1): the coupling t[q-1] enters only for
+        # q - 1 >= k0, i.e. the couplings t[k0] .. t[k-1] not yet applied to X
+        h = np.zeros(k - k0 + 1)
+        for q in range(k0, k + 1):
+            val = 0.0
+            if q - 1 >= k0:
+                val += t[q - 1] * L[k, q - 1]
+            if q + 1 <= k:
+                val -= t[q] * L[k, q + 1]
+            h[q - k0] = val
+        return h
+
+    k0 = 0
+    while k0 < n - 1:
+        kend = min(k0 + nb, n - 1)
+        for k in range(k0, kend):
+            h = h_vector(k, k0)
+            v = X[k + 1:, k] - L[k + 1:, k0:k + 1] @ h
+            r = k + 1 + int(np.argmax(np.abs(v)))
+            piv[k + 1] = r
+            if r != k + 1:
+                v[[0, r - k - 1]] = v[[r - k - 1, 0]]
+                X[[k + 1, r], :] = X[[r, k + 1], :]
+                X[:, [k + 1, r]] = X[:, [r, k + 1]]
+                L[[k + 1, r], k0:k + 1] = L[[r, k + 1], k0:k + 1]
+            t[k] = v[0]
+            L[k + 2:, k + 1] = v[1:] / t[k] if t[k] != 0.0 else 0.0
+        for k in range(k0, kend):                         # pivot_rows: columns < k0
+            r = piv[k + 1]
+            if r != k + 1:
+                L[[k + 1, r], 1:k0] = L[[r, k + 1], 1:k0]
+        s = kend
+        if s < n - 1:
+            Ap = L[s:, k0:s + 1]
+            Tp = tridiag_from_t(t[k0:s], Ap.shape[1])
+            X[s:, s:] -= Ap @ Tp @ Ap.T
+        k0 = kend
+    return L, t, piv
+
+
 def twostep_blocked(A, nb):
     """Blocked left-looking restatement of the two-step (Pfaffian-only) elimination,
     in the order the GPU path takes it.  Returns ``(a, piv)``.

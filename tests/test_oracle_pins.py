@@ -12,7 +12,7 @@ import pytest
 
 from paper_2411_09859_gb300 import inputs
 from skewcheck import (backward_error, check_structure, full_skew_from_lower,
-                       ltlt_blocked, perm_from_piv, pf4_closed_form,
+                       ltlt_blocked, ltlt_blocked_delayed, perm_from_piv, pf4_closed_form,
                        pfaffian_by_definition, pfaffian_by_matchings,
                        pfaffian_from_t_piv, tridiag_from_t)
 
@@ -168,6 +168,21 @@ def test_blocked_equals_unblocked(orc, n, nb):
         assert np.array_equal(p0, p1)
         assert np.max(np.abs(L0 - L1)) <= 1e-12
         assert np.max(np.abs(t0 - t1)) <= 1e-12 * max(1.0, np.max(np.abs(t0)))
+
+
+@pytest.mark.parametrize("n,nb", [(50, 1), (50, 4), (61, 8), (64, 32), (7, 3),
+                                  (33, 2), (40, 5), (100, 16), (130, 64)])
+def test_delayed_transform_ordering_reaches_the_same_factorization(orc, n, nb):
+    """The fused ordering of Invariant 2a (the last Gauss transform of each panel
+    applied with the next panel, Section 4.2) reaches the oracle's factorization:
+    identical pivots, factors equal up to rounding.  The GPU path keeps Variant 1 and
+    fuses that last transform into the same trailing-update launch instead."""
+    A = inputs.skew_gaussian(n, 900 + n + nb)
+    L0, t0, p0, _ = orc.ltlt(A)
+    L1, t1, p1 = ltlt_blocked_delayed(A, nb)
+    assert np.array_equal(p0, p1)
+    assert np.max(np.abs(L0 - L1)) <= 1e-12
+    assert np.max(np.abs(t0 - t1)) <= 1e-12 * max(1.0, np.max(np.abs(t0)))
 
 
 def test_w_identity_and_tridiag_rankk(orc):
