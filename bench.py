@@ -21,8 +21,10 @@ the oracle and at n = 16384 against the closed form), `pfaffian_only` (the two-s
 elimination), `batched` (4096 matrices of order 16..256 in one launch, LTL^T and
 Pfaffian-only, with a CUDA graph replay), `serving` (Pfaffian-only requests of order
 32..4096 against serial calls, saturation and Poisson streams; the factor-keeping
-mode alongside) and `cpu_baseline` (the oracle on a bounded sample, all host cores).
-`--skip-<leg>` drops a leg; `--impl reference` times the oracle alone.
+mode alongside), `cpu_baseline` (the oracle on the whole factorization, all host
+cores, timed once) and `oracle_parity` (the timed GPU factors against the oracle's).
+`--skip-<leg>` drops a leg; `--impl reference` times the oracle alone: the whole
+factorization in W + K consecutive pieces of equal update work, K of them timed.
 """
 from __future__ import annotations
 
@@ -60,8 +62,6 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--nb", type=int, default=0)
-    ap.add_argument("--cpu-sample-steps", type=int, default=384,
-                    help="elimination steps of the oracle timed per CPU sample")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
@@ -195,37 +195,63 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle
-def oracle_sample(A_host: np.ndarray, sample_steps: int) -> dict:
-    """Time the CPU oracle (as it stands) on the first `sample_steps` elimination
-    steps of this factorization and extrapolate to the whole one by the share of
-    its rank-2 update work (entries updated per step: (n-k-2)(n-k-3)/2)."""
+def update_work(n: int) -> np.ndarray:
+    """Entries the rank-2 update of elimination step k touches, (n-k-2)(n-k-3)/2, for
+    k = 0 .. n-2: the unit by which a piece of the oracle's factorization is credited
+    with its share of the n^3/3 flops of the whole one."""
+    k = np.arange(n - 1, dtype=np.float64)
+    return np.maximum(n - k - 2, 0) * np.maximum(n - k - 3, 0) / 2.0
+
+
+def oracle_full(A_host: np.ndarray) -> dict:
+    """The CPU oracle (as it stands, all host cores) on the whole factorization of
+    A_host, timed once from its set-up to its last elimination step.  Returns the
+    baseline figures and the oracle's factors (for the parity check of the GPU run on
+    the same matrix)."""
     import oracle
     n = A_host.shape[0]
-    X = np.array(A_host, order="F", copy=True)
     t0 = time.perf_counter()
-    oracle.ltlt(X, nsteps=0, overwrite=True)
-    t_init = time.perf_counter() - t0
-    X = np.array(A_host, order="F", copy=True)
-    t0 = time.perf_counter()
-    oracle.ltlt(X, nsteps=sample_steps, overwrite=True)
-    t_s = time.perf_counter() - t0
-    k = np.arange(n - 1, dtype=np.float64)
-    work = (n - k - 2) * (n - k - 3) / 2.0
-    frac = float(np.sum(work[:sample_steps]) / np.sum(work))
-    t_full = t_init + max(t_s - t_init, 0.0) / frac
-    return {"value": factorization_flops(n) / t_full / 1e12, "unit": UNIT,
+    st = oracle.ltlt_begin(A_host)
+    oracle.ltlt_continue(st, n - 1)
+    sec = time.perf_counter() - t0
+    return {"value": factorization_flops(n) / sec / 1e12, "unit": UNIT,
             "cores": oracle.threads(), "kind": "oracle",
-            "sample": (f"first {sample_steps} of {n - 1} elimination steps of the n={n} "
-                       f"factorization ({100 * frac:.1f}% of its update work, "
-                       f"{t_s:.1f} s) plus its O(n^2) set-up ({t_init:.1f} s), "
-                       f"extrapolated to the whole factorization: {t_full:.1f} s"),
-            "seconds_full_estimate": t_full}
+            "sample": (f"full: the whole n={n} factorization (set-up and all {n - 1} "
+                       f"elimination steps), timed once: {sec:.1f} s"),
+            "seconds": sec, "L": st["L"], "t": st["t"], "piv": st["piv"],
+            "info": st["info"]}
+
+
+def oracle_parity(orc: dict, L_dev, t: np.ndarray, piv: np.ndarray, n: int) -> dict:
+    """The GPU factors of the timed matrix against the oracle's: pivots, t and L
+    element by element, and log|Pf| and sign read off each side's own factors."""
+    import oracle
+    eps = 2.0 ** -52
+    tol = 2000.0 * n * eps
+    dL = 0.0
+    for j in range(0, n, 1024):
+        blk = L_dev[:, j:j + 1024].cpu().numpy()
+        dL = max(dL, float(np.max(np.abs(blk - orc["L"][:, j:j + 1024]))))
+    t0, p0 = orc["t"], orc["piv"]
+    dt = float(np.max(np.abs(t - t0))) / max(1.0, float(np.max(np.abs(t0))))
+    la0, sg0 = oracle.pfaffian_from_factors(n, t0, p0)
+    la1, sg1 = oracle.pfaffian_from_factors(n, t, piv)
+    return {"pivots_identical": bool(np.array_equal(piv, p0)),
+            "first_pivot_difference": (None if np.array_equal(piv, p0)
+                                       else int(np.argmax(piv != p0))),
+            "max_abs_dL": dL, "max_abs_dt_over_max_t": dt, "tol_L_t": tol,
+            "log_abs_pf_oracle": la0, "log_abs_pf_gpu": la1,
+            "rel_dlog_abs_pf": abs(la1 - la0) / max(1.0, abs(la0)),
+            "signs_equal": sg0 == sg1,
+            "within_bars": bool(np.array_equal(piv, p0) and dL <= tol and dt <= tol
+                                and sg0 == sg1
+                                and abs(la1 - la0) <= 1e-10 * max(1.0, abs(la0)))}
 
 
 # ----------------------------------------------------------------------------- dist
 # ----------------------------------------------------------------------------- batched
 def run_batched_leg(skew, inputs, torch, dev, steps: int, warmup: int, plain_count: int,
-                    rank: int = 0, world: int = 1):
+                    rank: int = 0, world: int = 1, cpu_baseline: bool = True):
     """The batched workload: 4096 skew matrices, orders even in [16, 256] (seed 4),
     matrix i from seed 1000+i, all factored in one skew_ltlt_batched launch per step
     (Pfaffian-only: L not stored).  Compared with back-to-back skew_pfaffian calls on
@@ -342,6 +368,32 @@ def run_batched_leg(skew, inputs, torch, dev, steps: int, warmup: int, plain_cou
     plain_rate = world * m / (plain_ms / 1e3)
     flops = reduce_sum(flops, world, dev)
     rate = total / (ms / 1e3)
+    # CPU baseline: the oracle on the whole batch, one matrix per host thread, largest
+    # first; its log|Pf| and signs are also the reference for every GPU result
+    cpu = None
+    oracle_check = None
+    if world == 1 and cpu_baseline:
+        import oracle
+        order = np.argsort(-sizes, kind="stable")
+        la_o, sg_o, inf_o, _, _, sec = oracle.ltlt_many([mats[i] for i in order])
+        la_c = np.empty(len(sizes))
+        sg_c = np.empty(len(sizes), dtype=np.int64)
+        la_c[order] = la_o
+        sg_c[order] = sg_o
+        la_g = la.cpu().numpy()
+        sg_g = sg.cpu().numpy()
+        la_t = la2.cpu().numpy()
+        cpu = {"value": total / sec, "unit": "Pfaffians/s", "cores": oracle.threads(),
+               "kind": "oracle",
+               "sample": (f"full: all {total} matrices, one matrix per host thread, "
+                          f"largest first, {sec:.2f} s")}
+        oracle_check = {
+            "matrices": int(total),
+            "signs_equal": bool(np.array_equal(sg_g, sg_c)),
+            "max_rel_dlog_abs_pf": float(np.max(np.abs(la_g - la_c) / np.maximum(1.0, np.abs(la_c)))),
+            "twostep_signs_equal": bool(np.array_equal(sg2.cpu().numpy(), sg_c)),
+            "twostep_max_rel_dlog_abs_pf": float(np.max(np.abs(la_t - la_c) / np.maximum(1.0, np.abs(la_c)))),
+            "oracle_info_nonzero": int(np.count_nonzero(inf_o))}
     return {"metric": "batched Pfaffians/s", "value": rate, "unit": "Pfaffians/s",
             "workload": "4096 skew matrices, n even uniform in [16, 256] (seed 4), "
                         "matrix i seed 1000+i, FP64, one persistent launch"
@@ -351,8 +403,10 @@ def run_batched_leg(skew, inputs, torch, dev, steps: int, warmup: int, plain_cou
             "plain_calls": {"value": plain_rate, "unit": "Pfaffians/s", "matrices": m * world,
                             "api": "skew_pfaffian, one call per matrix, back to back"},
             "speedup_vs_plain_calls": rate / plain_rate,
-            "accuracy": "same algorithm in FP64; pivots identical to the oracle and "
-                        "log|Pf| within 1e-10 relative on the tested sample",
+            "cpu_baseline": cpu,
+            "oracle_check": oracle_check,
+            "accuracy": "same algorithm in FP64; every log|Pf| and sign against the "
+                        "oracle in oracle_check",
             "pfaffian_only_twostep": {
                 "value": total / (ms2 / 1e3), "unit": "Pfaffians/s", "ms_per_batch": ms2,
                 "api": "skew_pfaffian_batched (two-step elimination; no T, L output)",
@@ -716,32 +770,57 @@ def dist_setup(args):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle (this paper has no code to install; the oracle
+    is its algorithm A1 written out) on the same n = 16384 matrix.  The whole
+    factorization is run once, in W + K consecutive pieces of equal rank-2 update work;
+    the first W pieces are the warm-up and each of the K timed steps is one piece,
+    credited with its share of the n^3/3 flops.  Every timed piece is measured, none is
+    extrapolated."""
     world, rank, local = dist_setup(args)
     if rank != 0:
         return 0
+    import oracle
     from paper_2411_09859_gb300 import inputs
     n = args.n
     seed = inputs.SEED_SCALE.get(n, 3)
     A_host = inputs.skew_gaussian(n, seed)
-    sample = max(1, min(args.cpu_sample_steps, n - 1))
-    est = []
-    last = None
-    for i in range(args.warmup + args.steps):
-        r = oracle_sample(A_host, sample)
+    pieces = args.warmup + args.steps
+    work = update_work(n)
+    cum = np.concatenate([[0.0], np.cumsum(work)])
+    bounds = [0] + [int(np.searchsorted(cum, cum[-1] * (i + 1) / pieces)) for i in range(pieces)]
+    bounds[-1] = n - 1
+    t0 = time.perf_counter()
+    st = oracle.ltlt_begin(A_host)
+    t_setup = time.perf_counter() - t0
+    times, credit = [], []
+    for i in range(pieces):
+        t0 = time.perf_counter()
+        oracle.ltlt_continue(st, bounds[i + 1])
+        dt = time.perf_counter() - t0
         if i >= args.warmup:
-            est.append(r["seconds_full_estimate"])
-            last = r
-    t_full = statistics.mean(est)
-    value = factorization_flops(n) / t_full / 1e12
+            times.append(dt)
+            credit.append(float(cum[bounds[i + 1]] - cum[bounds[i]]) / cum[-1])
+    sec = sum(times)
+    value = factorization_flops(n) * sum(credit) / sec / 1e12
+    sample = (f"the whole n={n} factorization in {pieces} consecutive pieces of equal "
+              f"rank-2 update work (set-up {t_setup:.1f} s, then the {args.warmup} warm-up "
+              f"pieces, elimination steps 0..{bounds[args.warmup] - 1}); timed: the "
+              f"{args.steps} pieces of steps {bounds[args.warmup]}..{n - 2}, "
+              f"{100 * sum(credit):.1f}% of the update work in {sec:.1f} s, credited with "
+              "that share of n^3/3")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_full * 1e3,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": workload_config(n, args.nb if args.nb > 0 else table_nb(n), seed),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"],
-                             "kind": "oracle", "sample": last["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+                    "d2h_bytes_per_step": 0},
+            "timed_pieces": [{"steps": [bounds[args.warmup + i], bounds[args.warmup + i + 1] - 1],
+                              "seconds": times[i], "share_of_work": credit[i]}
+                             for i in range(args.steps)]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -882,6 +961,7 @@ def run_ours(args):
         raise RuntimeError(f"timed factorization reported info={int(info.item())}")
     del copies
     torch.cuda.empty_cache()
+    t_host, piv_host = t.cpu().numpy(), piv.cpu().numpy()
 
     value = whole_job_rate(K * factorization_flops(n), ms / 1e3, world) / 1e12
     peak, peak_note = fp64_peak()
@@ -913,17 +993,32 @@ def run_ours(args):
             dist.barrier()
         t0 = time.perf_counter()
         step_ends = []
+        phases = []
         for _ in range(K):
             res = skew.ltlt_host(A_np, True, nb, L_out=L_np, t_out=t_np, piv_out=p_np)
             step_ends.append(time.perf_counter())
+            phases.append(skew.ltlt_host_timing())
             if res[5] != 0:
                 raise RuntimeError(f"host-buffer factorization reported info={res[5]}")
         el = reduce_max(step_ends[-1] - t0, world, dev)
         step_ms = list(np.diff([t0] + step_ends) * 1e3)
+        ph = np.array([p for p in phases if p is not None]).reshape(-1, 3)
+        med = np.median(ph, axis=0) if len(ph) else [None] * 3
+        h2d_b, d2h_b = n * n * 8, n * n * 8 + (n - 1) * 8 + n * 4 + 8 + 4 + 4
         e2e = {"value": whole_job_rate(K * factorization_flops(n), el, world) / 1e12, "unit": UNIT,
                "h2d_bytes_per_step": n * n * 8,
                "d2h_bytes_per_step": n * n * 8 + (n - 1) * 8 + n * 4 + 8 + 4 + 4,
                "ms_per_step": el / K * 1e3, "step_ms_rank0": [float(x) for x in step_ms],
+               "phases_ms_median_rank0": {
+                   "h2d_ms": float(med[0]) if len(ph) else None,
+                   "device_ms": float(med[1]) if len(ph) else None,
+                   "d2h_ms": float(med[2]) if len(ph) else None,
+                   "host_side_ms": (float(np.median(step_ms) - np.sum(med)) if len(ph) else None),
+                   "h2d_gbs": float(h2d_b / (med[0] / 1e3) / 1e9) if len(ph) else None,
+                   "d2h_gbs": float(d2h_b / (med[2] / 1e3) / 1e9) if len(ph) else None,
+                   "what": ("CUDA events on the call's stream around the copy of A, the "
+                            "factorization and the copies back; host_side_ms = median step "
+                            "wall time minus their sum")},
                "host_buffers": ("page-locked, allocated while bound to the "
                                 f"{near_cpus} CPUs next to the GPU" if near_cpus else
                                 "page-locked (GPU-local CPUs unknown: not bound)"),
@@ -932,7 +1027,7 @@ def run_ours(args):
     precision = None
     if not args.skip_precision:
         precision = run_precision_leg(skew, inputs, torch, dev, A_host, nb, ms / K,
-                                      t.cpu().numpy(), piv.cpu().numpy(), steps=2, warmup=1,
+                                      t_host, piv_host, steps=2, warmup=1,
                                       n_qdq=args.qdq_n, n_full=args.qdq_full_n)
 
     twostep = None
@@ -942,7 +1037,8 @@ def run_ours(args):
     batched = None
     if not args.skip_batched:
         batched = run_batched_leg(skew, inputs, torch, dev, steps=3, warmup=1,
-                                  plain_count=args.plain_calls, rank=rank, world=world)
+                                  plain_count=args.plain_calls, rank=rank, world=world,
+                                  cpu_baseline=not args.skip_cpu_baseline)
 
     serving = None
     if not args.skip_serving:
@@ -950,9 +1046,14 @@ def run_ours(args):
                                   args.serve_poisson, rank=rank, world=world)
 
     cpu = None
+    parity = None
     if rank == 0 and world == 1 and not args.skip_cpu_baseline:
-        r = oracle_sample(A_host, max(1, min(args.cpu_sample_steps, n - 1)))
+        r = oracle_full(A_host)
         cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        parity = oracle_parity(r, L, t_host, piv_host, n)
+        parity["what"] = ("the timed GPU factorization (last timed step) against the "
+                          "oracle's on the same matrix")
+        del r
 
     if rank == 0:
         line = {
@@ -975,6 +1076,7 @@ def run_ours(args):
             "batched": batched,
             "serving": serving,
             "cpu_baseline": cpu,
+            "oracle_parity": parity,
             "gpu_launches": launches,
             "clocks": clocks,
         }

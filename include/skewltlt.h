@@ -479,8 +479,10 @@ int skew_server_destroy(skew_server *server);
  * skew_ltlt_host -- convenience form of skew_ltlt + skew_pfaffian_from_factors on
  * HOST buffers, for callers without device memory of their own.  Copies A to the
  * device, factors it on the current device, copies the results back and returns
- * when they are in host memory (synchronous).  Device buffers are allocated and
- * freed by the call.  A is not modified.
+ * when they are in host memory (synchronous).  A is not modified.  The library keeps,
+ * per device, one stream and the device buffers of the largest order seen so far
+ * (an n x n matrix for A, another for L when L_host is given, and O(n) more) between
+ * calls; skew_trim_memory releases them.  Calls on one device are serialised.
  *   1  n
  *   2  A_host    lda x n host input (strictly lower triangle read)
  *   3  lda
@@ -498,6 +500,16 @@ int skew_server_destroy(skew_server *server);
 int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
                    int64_t ldl, double *t_host, int32_t *piv_host, double *logabs,
                    int32_t *sign, int32_t *info, int nb);
+
+/*
+ * skew_ltlt_host_timing -- where the time of the last completed skew_ltlt_host call
+ * on the current device went, from CUDA events on its stream: the host-to-device copy
+ * of A (h2d_ms), the factorization and read-off (device_ms), and the copies of the
+ * results back to host memory (d2h_ms).  Any pointer may be NULL.  Returns SKEW_OK,
+ * or -1 when no call has completed on this device since its buffers were created.
+ * No counterpart in the paper: an instrument of the host-buffer call.
+ */
+int skew_ltlt_host_timing(float *h2d_ms, float *device_ms, float *d2h_ms);
 
 #ifdef __cplusplus
 }

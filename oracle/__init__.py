@@ -71,6 +71,12 @@ class OracleLib:
         lib.oracle_skew_tridiag_rankk.restype = None
         lib.oracle_pfaffian_twostep.argtypes = [i64, p, i64, p, p, p, p]
         lib.oracle_pfaffian_twostep.restype = ctypes.c_int
+        lib.oracle_ltlt_setup.argtypes = [i64, p, i64, p, i64, p, p]
+        lib.oracle_ltlt_setup.restype = ctypes.c_int
+        lib.oracle_ltlt_range.argtypes = [i64, p, i64, p, i64, p, p, i64, i64]
+        lib.oracle_ltlt_range.restype = ctypes.c_int
+        lib.oracle_ltlt_many.argtypes = [i64, p, p, p, p, p, p, p, p]
+        lib.oracle_ltlt_many.restype = None
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = ctypes.c_int
         self.lib = lib
@@ -110,6 +116,64 @@ class OracleLib:
             return (np.zeros((0, 0), order="F"), np.zeros(0), np.zeros(0, np.int32),
                     int(info))
         return L, t[: n - 1], piv, int(info)
+
+    def ltlt_begin(self, A: np.ndarray):
+        """Set up the factorization of ``A`` for :meth:`ltlt_continue` (the state of
+        ``oracle_ltlt_setup``).  Returns a dict holding the workspace X, L, t, piv,
+        the order, the next step and info."""
+        n = int(A.shape[0])
+        if A.shape != (n, n) or n < 2:
+            raise ValueError("A must be square of order >= 2")
+        st = {"n": n, "X": _fortran_copy(A),
+              "L": np.zeros((n, n), dtype=np.float64, order="F"),
+              "t": np.zeros(n - 1, dtype=np.float64),
+              "piv": np.zeros(n, dtype=np.int32), "k": 0, "info": 0}
+        info = self.lib.oracle_ltlt_setup(n, _ptr(st["X"]), n, _ptr(st["L"]), n,
+                                          _ptr(st["t"]), _ptr(st["piv"]))
+        if info != 0:
+            raise ValueError(f"oracle_ltlt_setup failed with {info}")
+        return st
+
+    def ltlt_continue(self, st: dict, kend: int) -> int:
+        """Elimination steps st["k"] .. kend-1 of the factorization begun by
+        :meth:`ltlt_begin` (``oracle_ltlt_range``); the results after the last step
+        (n-1) are those of :meth:`ltlt`.  Returns the next step."""
+        n = st["n"]
+        kend = min(int(kend), n - 1)
+        info = self.lib.oracle_ltlt_range(n, _ptr(st["X"]), n, _ptr(st["L"]), n,
+                                          _ptr(st["t"]), _ptr(st["piv"]), st["k"], kend)
+        if info and not st["info"]:
+            st["info"] = int(info)
+        st["k"] = max(st["k"], kend)
+        return st["k"]
+
+    def ltlt_many(self, As):
+        """Whole factorizations and Pfaffians of the matrices ``As`` (a list), one
+        matrix per host thread (``oracle_ltlt_many``).  The inputs are copied first;
+        returns ``(logabs, sign, info, ts, pivs, seconds)`` with ``seconds`` the wall
+        time of the C call alone."""
+        import time
+        count = len(As)
+        ns = np.array([A.shape[0] for A in As], dtype=np.int64)
+        Xs = [_fortran_copy(A) if A.shape[0] > 0 else np.zeros((1, 1), order="F") for A in As]
+        Ls = [np.zeros((max(n, 1), max(n, 1)), dtype=np.float64, order="F") for n in ns]
+        ts = [np.zeros(max(n - 1, 1), dtype=np.float64) for n in ns]
+        pivs = [np.zeros(max(n, 1), dtype=np.int32) for n in ns]
+
+        def table(arrs):
+            return (ctypes.c_void_p * max(count, 1))(*[a.ctypes.data for a in arrs])
+
+        tX, tL, tt, tp = table(Xs), table(Ls), table(ts), table(pivs)
+        info = np.zeros(max(count, 1), dtype=np.int32)
+        logabs = np.zeros(max(count, 1), dtype=np.float64)
+        sign = np.zeros(max(count, 1), dtype=np.int32)
+        t0 = time.perf_counter()
+        self.lib.oracle_ltlt_many(count, _ptr(ns), tX, tL, tt, tp, _ptr(info),
+                                  _ptr(logabs), _ptr(sign))
+        seconds = time.perf_counter() - t0
+        return (logabs[:count], sign[:count], info[:count],
+                [t[: max(int(n) - 1, 0)] for t, n in zip(ts, ns)],
+                [p[: int(n)] for p, n in zip(pivs, ns)], seconds)
 
     def pfaffian_from_factors(self, n: int, t: np.ndarray, piv: np.ndarray):
         """``(log|Pf|, sign)`` read off T and P (sign in {-1, 0, 1})."""
@@ -190,6 +254,18 @@ def ltlt(A, nsteps=None, overwrite=False):
 
 def pfaffian_from_factors(n, t, piv):
     return default().pfaffian_from_factors(n, t, piv)
+
+
+def ltlt_begin(A):
+    return default().ltlt_begin(A)
+
+
+def ltlt_continue(st, kend):
+    return default().ltlt_continue(st, kend)
+
+
+def ltlt_many(As):
+    return default().ltlt_many(As)
 
 
 def pfaffian(A):

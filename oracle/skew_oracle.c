@@ -31,6 +31,9 @@
 #include <math.h>
 #include <stddef.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define X_(i, j) X[(size_t)(i) + (size_t)(j) * (size_t)ldx]
 #define L_(i, j) L[(size_t)(i) + (size_t)(j) * (size_t)ldl]
@@ -57,9 +60,19 @@
  * (the factorization is still complete and valid), ORACLE_ERR_NONFINITE (nothing
  * written) if the strictly lower triangle holds a NaN or infinity, and -1 for a bad
  * argument.
+ *
+ * It is oracle_ltlt_setup followed by oracle_ltlt_range over steps 0 .. nsteps-1.
  */
-int oracle_ltlt_steps(int64_t n, double *X, int64_t ldx, double *L, int64_t ldl,
-                      double *t, int32_t *piv, int64_t nsteps)
+int oracle_ltlt_range(int64_t n, double *X, int64_t ldx, double *L, int64_t ldl,
+                      double *t, int32_t *piv, int64_t kbegin, int64_t kend);
+
+/*
+ * oracle_ltlt_setup: the checks and the initial state of oracle_ltlt_steps (same
+ * arguments and error returns): L := I, piv := identity, t := 0.  Returns 0 when the
+ * elimination steps may start.
+ */
+int oracle_ltlt_setup(int64_t n, double *X, int64_t ldx, double *L, int64_t ldl,
+                      double *t, int32_t *piv)
 {
     if (n < 0) return -1;
     if (n == 0) return 0;
@@ -75,12 +88,32 @@ int oracle_ltlt_steps(int64_t n, double *X, int64_t ldx, double *L, int64_t ldl,
             L_(i, j) = (i == j) ? 1.0 : 0.0;
     for (int64_t i = 0; i < n; ++i) piv[i] = (int32_t)i;
     for (int64_t k = 0; k + 1 < n; ++k) t[k] = 0.0;
+    return 0;
+}
 
+int oracle_ltlt_steps(int64_t n, double *X, int64_t ldx, double *L, int64_t ldl,
+                      double *t, int32_t *piv, int64_t nsteps)
+{
+    const int st = oracle_ltlt_setup(n, X, ldx, L, ldl, t, piv);
+    if (st != 0 || n == 0) return st;
+    return oracle_ltlt_range(n, X, ldx, L, ldl, t, piv, 0, nsteps);
+}
+
+/*
+ * oracle_ltlt_range: elimination steps k = kbegin .. min(kend, n-1) - 1 of
+ * oracle_ltlt_steps, on the state that oracle_ltlt_setup and the steps before kbegin
+ * left in X, L, t and piv (so that a long factorization can be run, and timed, in
+ * consecutive pieces with results identical to one call).  Returns 0, or 1 + the
+ * first k of this range with t[k] == 0.
+ */
+int oracle_ltlt_range(int64_t n, double *X, int64_t ldx, double *L, int64_t ldl,
+                      double *t, int32_t *piv, int64_t kbegin, int64_t kend)
+{
     int info = 0;
     int64_t last = n - 1;                 /* steps k = 0 .. n-2 */
-    if (nsteps < last) last = nsteps;
+    if (kend < last) last = kend;
 
-    for (int64_t k = 0; k < last; ++k) {
+    for (int64_t k = kbegin; k < last; ++k) {
         /* ---- pivot: r = (k+1) + iamax(X[k+1:, k])  (Definition of iamax) ---- */
         int64_t r = k + 1;
         double best = fabs(X_(k + 1, k));
@@ -306,9 +339,6 @@ int oracle_pfaffian_twostep(int64_t n, double *X, int64_t ldx, double *a, int32_
     return info;
 }
 
-#ifdef _OPENMP
-#include <omp.h>
-#endif
 /* Number of host threads the rank-2 update of oracle_ltlt_steps may use. */
 int oracle_threads(void)
 {
@@ -316,5 +346,37 @@ int oracle_threads(void)
     return omp_get_max_threads();
 #else
     return 1;
+#endif
+}
+
+/*
+ * oracle_ltlt_many: oracle_ltlt_steps (whole factorizations) and oracle_pfaffian on
+ * `count` independent matrices, one matrix per host thread (OpenMP, dynamic schedule
+ * in the order given; the update loop inside each factorization runs on its own
+ * thread).  Matrix b has order n[b], leading dimensions max(n[b], 1), and its own X,
+ * L, t and piv arrays as for oracle_ltlt_steps; info[b], logabs[b] and sign[b] are
+ * its results.  This is the CPU baseline of a batch of small factorizations.
+ */
+void oracle_ltlt_many(int64_t count, const int64_t *n, double *const *X,
+                      double *const *L, double *const *t, int32_t *const *piv,
+                      int *info, double *logabs, int *sign)
+{
+#ifdef _OPENMP
+    const int levels = omp_get_max_active_levels();
+    omp_set_max_active_levels(1);
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t b = 0; b < count; ++b) {
+        const int64_t nn = n[b], ld = nn > 0 ? nn : 1;
+        info[b] = oracle_ltlt_steps(nn, X[b], ld, L[b], ld, t[b], piv[b], nn);
+        if (info[b] >= 0)
+            oracle_pfaffian(nn, t[b], piv[b], &logabs[b], &sign[b]);
+        else {
+            logabs[b] = NAN;
+            sign[b] = 0;
+        }
+    }
+#ifdef _OPENMP
+    omp_set_max_active_levels(levels);
 #endif
 }

@@ -48,6 +48,7 @@ SIGNATURES = {
     "skew_rank2k": ([_i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _vp], _i32),
     "skew_tridiag_rankk": ([_i64, _i64, _dbl, _vp, _i64, _vp, _dbl, _vp, _i64, _vp], _i32),
     "skew_ltlt_host": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32], _i32),
+    "skew_ltlt_host_timing": ([_vp, _vp, _vp], _i32),
     "skew_batched_workspace_bytes": ([_i32, _i32], _sz),
     "skew_ltlt_ex": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i32, _i32, _vp, _sz, _vp], _i32),
     "skew_pfaffian_ex": ([_i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _vp, _sz, _vp], _i32),
@@ -360,6 +361,17 @@ def ltlt_host(A: np.ndarray, want_L: bool = True, nb: int = 0, L_out=None, t_out
                               ctypes.byref(logabs), ctypes.byref(sign), ctypes.byref(info), nb)
     _check("skew_ltlt_host", st)
     return L, t[: max(n - 1, 0)], piv[:n], logabs.value, sign.value, info.value
+
+
+def ltlt_host_timing():
+    """(h2d_ms, device_ms, d2h_ms) of the last completed :func:`ltlt_host` call on the
+    current device, or None if there is none."""
+    v = [ctypes.c_float(0.0) for _ in range(3)]
+    st = lib().skew_ltlt_host_timing(*[ctypes.byref(x) for x in v])
+    if st == -1:
+        return None
+    _check("skew_ltlt_host_timing", st)
+    return tuple(float(x.value) for x in v)
 
 
 BATCH_MAX_N = 8192

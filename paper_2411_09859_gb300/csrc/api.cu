@@ -507,6 +507,44 @@ BatchedNb batched_nb_table() {
 
 using namespace skew;
 
+namespace {
+// Context of the host-buffer call, one per device, created on first use and kept
+// until skew_trim_memory: the stream, the phase events, and the device buffers (grown
+// when a larger order arrives).  Calls on one device are serialised by its mutex.
+struct HostCall {
+    std::mutex mu;
+    bool ready = false;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev[4] = {};
+    void *buf = nullptr;          // dA | dL | dt | dpiv | dlog | dsign | dinfo
+    size_t buf_bytes = 0;
+    float ms[3] = {0.f, 0.f, 0.f};
+    bool have_ms = false;
+};
+HostCall g_host[kMaxDevices];
+
+int host_ready(HostCall &h) {
+    if (h.ready) return SKEW_OK;
+    SKEW_TRY(cudaStreamCreateWithFlags(&h.st, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : h.ev) SKEW_TRY(cudaEventCreate(&e));
+    h.ready = true;
+    return SKEW_OK;
+}
+
+int host_release_buffers(HostCall &h) {
+    if (h.buf == nullptr) return SKEW_OK;
+    cudaError_t e = cudaFreeAsync(h.buf, h.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h.st);
+    h.buf = nullptr;
+    h.buf_bytes = 0;
+    if (e != cudaSuccess) {
+        set_last_error(e);
+        return SKEW_ERR_CUDA;
+    }
+    return SKEW_OK;
+}
+}  // namespace
+
 extern "C" {
 
 int skew_version(void) { return 100; }   // 0.1.0
@@ -670,6 +708,10 @@ int skew_selftest_mbarrier_wait(double timeout_s, int32_t *status) {
 int skew_trim_memory(void) {
     int dev;
     SKEW_TRY(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < kMaxDevices) {
+        std::lock_guard<std::mutex> lock(g_host[dev].mu);
+        SKEW_TRY_STATUS(host_release_buffers(g_host[dev]));
+    }
     cudaMemPool_t pool;
     SKEW_TRY_STATUS(device_pool(dev, &pool));
     SKEW_TRY(cudaMemPoolTrimTo(pool, 0));
@@ -1010,26 +1052,46 @@ int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
     if (nb < 0 || nb > kMaxNb) return -11;
     DeviceInfo di;
     SKEW_TRY_STATUS(current_device_info(&di));
-    cudaStream_t st;
-    SKEW_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    int dev;
+    SKEW_TRY(cudaGetDevice(&dev));
+    HostCall &h = g_host[dev];
+    std::lock_guard<std::mutex> lock(h.mu);
+    SKEW_TRY_STATUS(host_ready(h));
+    cudaStream_t st = h.st;
     const size_t nn = (size_t)(n > 0 ? n : 1);
-    double *dA = nullptr, *dL = nullptr, *dt = nullptr, *dlog = nullptr;
-    int32_t *dpiv = nullptr, *dsign = nullptr, *dinfo = nullptr;
+    const size_t mat = align256(nn * nn * sizeof(double));
+    const size_t vec = align256(nn * sizeof(double));
+    const size_t need = mat + (L_host ? mat : 0) + 2 * vec + 3 * 256;
+    if (need > h.buf_bytes) {
+        SKEW_TRY_STATUS(host_release_buffers(h));
+        SKEW_TRY_STATUS(pool_alloc(&h.buf, need, st));
+        h.buf_bytes = need;
+    }
+    char *b = static_cast<char *>(h.buf);
+    double *dA = reinterpret_cast<double *>(b);
+    b += mat;
+    double *dL = nullptr;
+    if (L_host) {
+        dL = reinterpret_cast<double *>(b);
+        b += mat;
+    }
+    double *dt = reinterpret_cast<double *>(b);
+    b += vec;
+    int32_t *dpiv = reinterpret_cast<int32_t *>(b);
+    b += vec;
+    double *dlog = reinterpret_cast<double *>(b);
+    int32_t *dsign = reinterpret_cast<int32_t *>(b + 256);
+    int32_t *dinfo = reinterpret_cast<int32_t *>(b + 512);
     int status = SKEW_OK;
     double h_log = 0.0;
     int32_t h_sign = 0, h_info = 0;
+    h.have_ms = false;
     do {
-        if ((status = pool_alloc((void **)&dA, nn * nn * sizeof(double), st))) break;
-        if (L_host && (status = pool_alloc((void **)&dL, nn * nn * sizeof(double), st))) break;
-        if ((status = pool_alloc((void **)&dt, nn * sizeof(double), st))) break;
-        if ((status = pool_alloc((void **)&dpiv, nn * sizeof(int32_t), st))) break;
-        if ((status = pool_alloc((void **)&dlog, sizeof(double), st))) break;
-        if ((status = pool_alloc((void **)&dsign, sizeof(int32_t), st))) break;
-        if ((status = pool_alloc((void **)&dinfo, sizeof(int32_t), st))) break;
-        cudaError_t e = cudaSuccess;
-        if (n > 0)
+        cudaError_t e = cudaEventRecord(h.ev[0], st);
+        if (e == cudaSuccess && n > 0)
             e = cudaMemcpy2DAsync(dA, n * sizeof(double), A_host, lda * sizeof(double),
                                   n * sizeof(double), n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaEventRecord(h.ev[1], st);
         if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
         if (L_host) {
             status = skew_ltlt(n, dA, ld_min, dL, ld_min, dt, dpiv, dinfo, nb, nullptr, 0, st);
@@ -1038,7 +1100,8 @@ int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
             status = skew_pfaffian(n, dA, ld_min, dlog, dsign, dt, dpiv, dinfo, nb, nullptr, 0, st);
         }
         if (status != SKEW_OK) break;
-        if (L_host && n > 0)
+        e = cudaEventRecord(h.ev[2], st);
+        if (e == cudaSuccess && L_host && n > 0)
             e = cudaMemcpy2DAsync(L_host, ldl * sizeof(double), dL, n * sizeof(double),
                                   n * sizeof(double), n, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && t_host && n > 1)
@@ -1051,18 +1114,20 @@ int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
             e = cudaMemcpyAsync(&h_sign, dsign, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(&h_info, dinfo, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaEventRecord(h.ev[3], st);
         if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
     } while (0);
-    void *bufs[] = {dA, dL, dt, dlog, dpiv, dsign, dinfo};
-    for (void *b : bufs)
-        if (b) cudaFreeAsync(b, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess && status == SKEW_OK) {
         set_last_error(e);
         status = SKEW_ERR_CUDA;
     }
-    cudaStreamDestroy(st);
     if (status == SKEW_OK) {
+        bool ok = true;
+        for (int i = 0; i < 3 && ok; ++i)
+            ok = cudaEventElapsedTime(&h.ms[i], h.ev[i], h.ev[i + 1]) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+        h.have_ms = ok;
         if (n == 0) {   // empty factorization: Pf = 1
             h_info = 0;
         }
@@ -1071,6 +1136,19 @@ int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
         if (info) *info = h_info;
     }
     return status;
+}
+
+int skew_ltlt_host_timing(float *h2d_ms, float *device_ms, float *d2h_ms) {
+    int dev;
+    SKEW_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return SKEW_ERR_NODEVICE;
+    HostCall &h = g_host[dev];
+    std::lock_guard<std::mutex> lock(h.mu);
+    if (!h.have_ms) return -1;             // no completed call on this device
+    if (h2d_ms) *h2d_ms = h.ms[0];
+    if (device_ms) *device_ms = h.ms[1];
+    if (d2h_ms) *d2h_ms = h.ms[2];
+    return SKEW_OK;
 }
 
 }  // extern "C"

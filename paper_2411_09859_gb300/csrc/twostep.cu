@@ -406,9 +406,11 @@ int launch_twostep_panel(const TwoStepArgs &a, int sms, cudaStream_t stream) {
     const int64_t rows = (int64_t)a.n - a.k0 - 1;
     const int width = a.kend - a.k0;
     if (rows < 1 || width > kTsMaxNb || rows > (int64_t)sms * kPanelThreads) return SKEW_ERR_CUDA;
-    static bool attr_set = false;            // per process: the attribute is per function
+    // The attribute belongs to the current device's copy of the function: set it on
+    // every launch (as the other panel launches do), which is cheap and keeps no
+    // process-wide state shared between devices or threads.
     const size_t smem_max = (size_t)kTsMaxNb * kPanelThreads * sizeof(double);
-    if (!attr_set) {
+    {
         cudaError_t e = cudaFuncSetAttribute((const void *)twostep_panel_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem_max);
@@ -416,7 +418,6 @@ int launch_twostep_panel(const TwoStepArgs &a, int sms, cudaStream_t stream) {
             set_last_error(e);
             return SKEW_ERR_CUDA;
         }
-        attr_set = true;
     }
     int64_t g = panel_grid(rows, sms);
     if (g > kMaxPanelGrid) g = kMaxPanelGrid;

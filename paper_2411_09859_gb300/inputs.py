@@ -87,16 +87,19 @@ def qdq_skew(n: int, seed: int, smax: float = 1e6):
     return np.asfortranarray((M - M.T) / 2.0), s
 
 
-def qdq_skew_device(n: int, seed: int, smax: float = 1e6, device="cuda"):
+def qdq_skew_device(n: int, seed: int, smax: float = 1e6, device="cuda",
+                    special: bool = True):
     """A = Q D Q^T generated on the device, for orders whose host generation would take
     minutes (n = 16384).  G: n x n standard normal from a torch generator seeded with
     `seed` (not the numpy stream of `qdq_skew`); Q: the Householder QR of G with the
-    sign(diag R) correction (Haar); D = block_diag_skew(log_spaced_s(n, smax)).
-    A = U V^T - V U^T with U = Q[:, 0::2] * s and V = Q[:, 1::2] (= Q D Q^T, exactly
-    skew).  det(Q) = (-1)^(number of nonzero reflectors) * prod sign(R_ii).
+    sign(diag R) correction (Haar in O(n)); with `special` (the default) column 0 of Q
+    is negated when det(Q) = -1, so that Q is Haar in SO(n).  det(Q) before that is
+    (-1)^(number of nonzero reflectors) * prod sign(R_ii).
+    D = block_diag_skew(log_spaced_s(n, smax)); A = U V^T - V U^T with
+    U = Q[:, 0::2] * s and V = Q[:, 1::2] (= Q D Q^T, exactly skew).
 
-    Returns (A, s, detQ): A a column-major float64 CUDA tensor, s (numpy), detQ in
-    {-1, +1}; Pf(A) = detQ * prod(s)."""
+    Returns (A, s, detQ): A a column-major float64 CUDA tensor, s (numpy), detQ the
+    determinant of the Q used (+1 with `special`); Pf(A) = detQ * prod(s)."""
     import torch
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed))
@@ -110,6 +113,9 @@ def qdq_skew_device(n: int, seed: int, smax: float = 1e6, device="cuda"):
     nneg = int((dR < 0).sum().item())
     nref = int((tau != 0).sum().item())
     detQ = -1 if (nneg + nref) % 2 else 1
+    if special and detQ < 0:
+        Q[:, 0] = -Q[:, 0]
+        detQ = 1
     del H, tau
     s = log_spaced_s(n, smax)
     st = torch.from_numpy(s).to(device)

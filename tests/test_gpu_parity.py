@@ -198,6 +198,24 @@ def test_host_entry_point_matches_device_path():
     assert_pf_close(la2, sg2, la0, sg0)
 
 
+def test_host_entry_point_keeps_buffers_and_reports_phases():
+    """Repeated host calls of one order reuse the library's buffers (no change in free
+    device memory after the first) and report their three phases."""
+    A = inputs.skew_gaussian(1000, 8)
+    r0 = skew.ltlt_host(A, want_L=True, nb=32)
+    ph = skew.ltlt_host_timing()
+    assert ph is not None and all(x > 0 for x in ph)
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        r1 = skew.ltlt_host(A, want_L=True, nb=32)
+        assert np.array_equal(r1[0], r0[0]) and np.array_equal(r1[2], r0[2])
+    assert torch.cuda.mem_get_info()[0] == free0
+    small = skew.ltlt_host(inputs.skew_gaussian(40, 9), want_L=True, nb=8)
+    assert small[5] == 0
+    assert torch.cuda.mem_get_info()[0] == free0        # a smaller order fits the same buffers
+    skew.trim_memory()
+
+
 def test_input_sizes_rejected():
     with pytest.raises(skew.SkewError):
         skew.ltlt(to_dev(inputs.skew_gaussian(8, 0)), nb=300)

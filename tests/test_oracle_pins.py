@@ -294,12 +294,47 @@ def test_generator_is_skew_and_seeded():
 
 def test_device_qdq_generator_closed_form_on_cpu(orc):
     """The device QDQ^T generator (used at n = 16384), run on the CPU: exactly skew,
-    Pf = det(Q) prod s with det(Q) read off the Householder reflectors."""
+    Pf = det(Q) prod s with det(Q) read off the Householder reflectors; with Q forced
+    into SO(n) (the default) the sign is +1 for every seed, including the seeds whose
+    QR factor had det(Q) = -1."""
     torch = pytest.importorskip("torch")
-    for n, seed in ((12, 3), (40, 5), (64, 9)):
-        A, s, detQ = inputs.qdq_skew_device(n, seed, smax=1e3, device="cpu")
+    raw_dets = []
+    for n, seed in ((12, 3), (40, 5), (64, 9), (12, 1), (12, 2), (12, 4), (12, 6)):
+        A, s, detQ = inputs.qdq_skew_device(n, seed, smax=1e3, device="cpu", special=False)
         A = A.numpy()
         assert np.array_equal(A, -A.T)
         la, sg = orc.pfaffian(np.asfortranarray(A))
         assert sg == detQ
         assert math.isclose(la, float(np.sum(np.log(s))), rel_tol=1e-10)
+        raw_dets.append(detQ)
+        A, s, detQ = inputs.qdq_skew_device(n, seed, smax=1e3, device="cpu")
+        la, sg = orc.pfaffian(np.asfortranarray(A.numpy()))
+        assert detQ == 1 and sg == 1
+        assert math.isclose(la, float(np.sum(np.log(s))), rel_tol=1e-10)
+    assert -1 in raw_dets and 1 in raw_dets
+
+def test_oracle_in_pieces_and_batched_equal_single_calls(orc):
+    """The oracle run in consecutive pieces of elimination steps (how the CPU baseline
+    times a long factorization) and the one-matrix-per-thread batch driver give
+    results bitwise equal to one whole call per matrix."""
+    A = inputs.skew_gaussian(300, 5)
+    L, t, piv, info = orc.ltlt(A)
+    st = orc.ltlt_begin(A)
+    for kend in (7, 50, 51, 200, 400):
+        orc.ltlt_continue(st, kend)
+    assert np.array_equal(st["L"], L) and np.array_equal(st["t"], t)
+    assert np.array_equal(st["piv"], piv) and st["info"] == info
+    D = inputs.block_diag_skew([2.0, 3.0, 5.0])              # zero pivots at odd steps
+    st = orc.ltlt_begin(D)
+    orc.ltlt_continue(st, 2)
+    orc.ltlt_continue(st, 5)
+    assert st["info"] == orc.ltlt(D)[3] == 2
+    As = [inputs.skew_gaussian(n, 10 + n) for n in (0, 1, 2, 5, 16, 40, 33, 64)] + [D]
+    la, sg, inf, ts, pivs, _ = orc.ltlt_many(As)
+    for A, l1, s1, i1, t1, p1 in zip(As, la, sg, inf, ts, pivs):
+        n = A.shape[0]
+        L0, t0, p0, i0 = orc.ltlt(A)
+        l0, s0 = orc.pfaffian_from_factors(n, t0, p0)
+        assert i1 == i0 and s1 == s0
+        assert np.array_equal(t1, t0) and np.array_equal(p1, p0)
+        assert l1 == l0 or (math.isinf(l1) and math.isinf(l0))
