@@ -72,8 +72,14 @@ def parse_args():
     ap.add_argument("--skip-twostep", action="store_true",
                     help="skip the Pfaffian-only (two-step and one-step) leg")
     ap.add_argument("--qdq-n", type=int, default=2048)
-    ap.add_argument("--serve-requests", type=int, default=1000)
-    ap.add_argument("--serve-poisson", type=int, default=500)
+    ap.add_argument("--serve-requests", type=int, default=20000,
+                    help="requests of the serving stream (all of them at saturation)")
+    ap.add_argument("--serve-poisson", type=int, default=2000,
+                    help="first requests of the stream replayed as each Poisson stream")
+    ap.add_argument("--serve-serial", type=int, default=2000,
+                    help="first requests of the stream timed as serial calls")
+    ap.add_argument("--serve-factors", type=int, default=1000,
+                    help="first requests of the stream run with their factors kept")
     ap.add_argument("--plain-calls", type=int, default=1024,
                     help="matrices of the batched workload timed as back-to-back plain calls")
     return ap.parse_args()
@@ -192,6 +198,34 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- kernels
+SIDE_STREAM_KERNELS = ("pivot_rows",)
+
+
+def kernel_table(prof: dict, steps: int, total_ms: float) -> dict:
+    """Per-kernel time from the library's event pairs (recorded on each launch's own
+    stream).  Kernels on the critical stream get ms per step and their share of the
+    step.  A side-stream kernel (pivot_rows) runs beside the trailing update: its event
+    span includes the time it waits for multiprocessors the update holds, so it is
+    reported as a span only, with no share (its device time per launch is in the ncu
+    launch list)."""
+    out = {}
+    for k, v in prof.items():
+        if not v["launches"]:
+            continue
+        row = {"launches_per_step": v["launches"] / steps}
+        if k in SIDE_STREAM_KERNELS:
+            row.update({"ms_per_step": None, "event_span_ms_per_step": v["ms"] / steps,
+                        "share": None,
+                        "note": "side stream, overlaps the trailing update; span, not "
+                                "device time"})
+        else:
+            row.update({"ms_per_step": v["ms"] / steps,
+                        "share": v["ms"] / total_ms if total_ms > 0 else None})
+        out[k] = row
+    return out
 
 
 # ----------------------------------------------------------------------------- oracle
@@ -454,8 +488,7 @@ def run_precision_leg(skew, inputs, torch, dev, A_host, nb_fp64, fp64_ms, fp64_t
     prof = skew.profile_read()
     skew.profile_enable(False)
     ms = statistics.median(times)
-    kernels = {k: {"ms_per_step": v["ms"] / steps, "share": v["ms"] / steps / ms}
-               for k, v in prof.items() if v["launches"]}
+    kernels = kernel_table(prof, steps, ms * steps)
     sk = prof["skr2k"]
     split_tflops = (sk["flops"] / (sk["ms"] / 1e3) / 1e12) if sk["ms"] > 0 else None
     t_s, piv_s = t.cpu().numpy(), piv.cpu().numpy()
@@ -530,28 +563,57 @@ def run_precision_leg(skew, inputs, torch, dev, A_host, nb_fp64, fp64_ms, fp64_t
 
 
 # ----------------------------------------------------------------------------- serving
+def latency_summary(res) -> dict:
+    """p50/p99 of the latency and of its three parts (waiting for the memory budget,
+    for a stream, then running), and the mean parts of the requests at or above the
+    p99 latency, in milliseconds."""
+    lat = np.array([r["latency_s"] for r in res]) * 1e3
+    out = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+    if res and all("queued_s" in r for r in res):
+        parts = {k: np.array([r[k] for r in res]) * 1e3
+                 for k in ("queued_s", "waiting_s", "running_s")}
+        tail = lat >= np.percentile(lat, 99)
+        out["breakdown"] = {
+            k.replace("_s", ""): {"p50_ms": float(np.percentile(v, 50)),
+                                  "p99_ms": float(np.percentile(v, 99)),
+                                  "mean_ms_of_p99_requests": float(np.mean(v[tail]))}
+            for k, v in parts.items()}
+        out["breakdown"]["what"] = ("queued: submission to admission (memory budget); "
+                                    "waiting: admission to launch (free stream or batch); "
+                                    "running: launch to observed completion")
+    return out
+
+
 def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int,
-                    rank: int = 0, world: int = 1):
-    """The serving workload: requests with even orders log-uniform in [32, 4096]
-    (seed 6); request i is the leading n_i x n_i block of one seeded 4096 x 4096 skew
-    matrix (every principal block of an iid N(0,1) skew matrix is one of order n_i).
-    The requests ask for the Pfaffian only (SKEW_SERVE_PFAFFIAN: the two-step
-    elimination).  Compared: serial back-to-back skew_pfaffian_twostep calls (the same
-    algorithm, so the same accuracy); the continuous-batching server (64 GB budget, 4
-    streams, batched kernel up to n = 512) with all requests submitted at once; and the
-    server fed by Poisson streams at 0.5x, 0.8x and 1.2x the serial rate (seeded gaps),
-    reporting p50/p99 latency from submission to completion; `poisson` is the 0.8x
-    stream.  `factors_kept` repeats the serial and saturation runs with requests that
-    keep their LTL^T factors (SKEW_SERVE_FACTORS; serial skew_pfaffian calls).  Results are consumed in submission order and released
-    at once, so a stream longer than the memory budget holds keeps flowing.  With several
-    ranks each runs its own server on a size-balanced share of the requests (at their
-    arrival times in the one global stream); rates are all requests over the slowest
-    rank's time and the latency percentiles are taken over the gathered latencies."""
+                    n_serial: int, n_factors: int, rank: int = 0, world: int = 1):
+    """The serving workload: a stream of n_requests requests with even orders
+    log-uniform in [32, 4096] (seed 6); request i is the leading n_i x n_i block of one
+    seeded 4096 x 4096 skew matrix (every principal block of an iid N(0,1) skew matrix
+    is one of order n_i).  The requests ask for the Pfaffian only (SKEW_SERVE_PFAFFIAN:
+    the two-step elimination).  Measured:
+      - saturation: the continuous-batching server (64 GB budget, 4 streams, batched
+        kernel up to n = 512) with the whole stream submitted at once;
+      - serial: back-to-back skew_pfaffian_twostep calls (the same algorithm, so the
+        same accuracy) on the first n_serial requests, as a rate;
+      - Poisson streams of the first n_poisson requests at 0.5x, 0.8x and 1.2x that
+        serial rate (seeded gaps), p50/p99 latency from submission to completion and
+        where it went (budget, stream, running); `poisson` is the 0.8x stream;
+      - factors_kept: serial and saturation runs on the first n_factors requests with
+        requests that keep their LTL^T factors (SKEW_SERVE_FACTORS; serial skew_pfaffian
+        calls).
+    Results are consumed in submission order and released at once, so a stream longer
+    than the memory budget holds keeps flowing.  With several ranks each runs its own
+    server on a size-balanced share of the requests (at their arrival times in the one
+    global stream); rates are all requests over the slowest rank's time and the latency
+    percentiles are taken over the gathered latencies."""
     from paper_2411_09859_gb300 import shard
     rng = np.random.default_rng(inputs.SEED_SERVING)
     logn = rng.uniform(np.log(32), np.log(4096), size=n_requests)
     sizes = np.clip(2 * np.round(np.exp(logn) / 2), 32, 4096).astype(np.int64)
     mine = shard.balanced_bins(sizes, world)[rank] if world > 1 else np.arange(n_requests)
+    n_serial = min(n_serial, n_requests)
+    n_poisson = min(n_poisson, n_requests)
+    n_factors = min(n_factors, n_requests)
 
     def gather(values):
         if world <= 1:
@@ -562,7 +624,7 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int,
         return [v for part in parts for v in part]
     master = torch.from_numpy(inputs.skew_gaussian(4096, inputs.SEED_SERVING)).to(dev)
     views = [master[:int(n), :int(n)] for n in sizes]
-    flops = float(np.sum(sizes.astype(np.float64) ** 3) / 3.0)
+    flops_of = lambda count: float(np.sum(sizes[:count].astype(np.float64) ** 3) / 3.0)
     stream = torch.cuda.Stream(device=dev)
     work = skew.fortran_empty(4096, 4096, dev)
 
@@ -576,27 +638,29 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int,
             else:
                 skew.pfaffian(w, stream=stream)
 
-    def time_serial(pf_only):
+    def time_serial(count, pf_only):
+        idx = [int(i) for i in mine if i < count]
         with torch.cuda.stream(stream):
-            serial(mine[:8], pf_only)
+            serial(idx[:8], pf_only)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            serial(mine, pf_only)
+            serial(idx, pf_only)
             e1.record(stream)
         torch.cuda.synchronize()
         return reduce_max(e0.elapsed_time(e1) / 1e3, world, dev)
 
-    serial_s = time_serial(True)
-    serial_rate = n_requests / serial_s
-    serial_f_s = time_serial(False)
+    serial_s = time_serial(n_serial, True)
+    serial_rate = n_serial / serial_s
+    serial_f_s = time_serial(n_factors, False)
 
     srv = skew.Server(64 << 30, n_streams=4, small_n_max=512)
     for pf in (True, False):
         for tk in [srv.submit(views[i], pfaffian_only=pf) for i in mine[:16]]:
             srv.wait(tk)
             srv.release(tk)
+
     def consume(tickets):
         # results are read in submission order and released at once, as a client
         # would: the factors of a long stream do not all fit the budget together
@@ -606,19 +670,18 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int,
             srv.release(tk)
         return out
 
-    def saturation(pf_only):
+    def saturation(count, pf_only):
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
         t0 = time.perf_counter()
-        tickets = [srv.submit(views[i], pfaffian_only=pf_only) for i in mine]
+        tickets = [srv.submit(views[i], pfaffian_only=pf_only) for i in mine if i < count]
         res = consume(tickets)
         sec = reduce_max(time.perf_counter() - t0, world, dev)
-        lat = np.array(gather(r["latency_s"] for r in res)) * 1e3
-        return sec, lat, sum(1 for r in res if r["info"] != 0)
+        return sec, gather(res), sum(1 for r in res if r["info"] != 0)
 
-    sat_s, sat_lat, bad = saturation(True)
-    sat_f_s, sat_f_lat, bad_f = saturation(False)
+    sat_s, sat_res, bad = saturation(n_requests, True)
+    sat_f_s, sat_f_res, bad_f = saturation(n_factors, False)
     bad += bad_f
 
     def poisson_stream(factor, seed):
@@ -646,11 +709,10 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int,
         seconds = reduce_max(time.perf_counter() - t0, world, dev)
         if len(out) != len(todo):
             raise RuntimeError("the serving client thread did not consume every result")
-        lat = np.array(gather(r["latency_s"] for r in out)) * 1e3
-        return out, {"rate_factor": factor, "rate_per_s": lam, "requests": n_poisson,
-                     "value": n_poisson / seconds,
-                     "p50_ms": float(np.percentile(lat, 50)),
-                     "p99_ms": float(np.percentile(lat, 99))}
+        summary = {"rate_factor": factor, "rate_per_s": lam, "requests": n_poisson,
+                   "value": n_poisson / seconds}
+        summary.update(latency_summary(gather(out)))
+        return out, summary
 
     rates = []
     # gap seeds: 0.8x (the headline stream) seed 7, 0.5x seed 8, 1.2x seed 9
@@ -662,30 +724,34 @@ def run_serving_leg(skew, inputs, torch, dev, n_requests: int, n_poisson: int,
     bad = int(reduce_sum(bad, world, dev))
     if bad:
         raise RuntimeError(f"{bad} served requests reported a nonzero info")
+    sat = {"value": n_requests / sat_s, "requests": n_requests, "seconds": sat_s,
+           "tflops": flops_of(n_requests) / sat_s / 1e12,
+           "speedup_vs_serial": serial_rate and (n_requests / sat_s) / serial_rate}
+    sat.update(latency_summary(sat_res))
+    sat_f = {"value": n_factors / sat_f_s, "requests": n_factors, "seconds": sat_f_s,
+             "speedup_vs_serial": (n_factors / sat_f_s) / (n_factors / serial_f_s)}
+    sat_f.update(latency_summary(sat_f_res))
     return {"metric": "served Pfaffians/s and latency", "unit": "Pfaffians/s",
+            "value": n_requests / sat_s,
             "workload": (f"{n_requests} requests, even n log-uniform in [32, 4096] (seed 6), "
-                         "leading blocks of one seeded 4096^2 iid N(0,1) skew matrix"
-                         + ("" if n_requests >= 20000 else "; the 20000-request stream is "
-                            "shortened to keep the run short")),
+                         "leading blocks of one seeded 4096^2 iid N(0,1) skew matrix; "
+                         f"saturation on all {n_requests}; serial rate on the first "
+                         f"{n_serial}; Poisson streams on the first {n_poisson}; factor-"
+                         f"keeping runs on the first {n_factors}"),
             "requests": "Pfaffian only (SKEW_SERVE_PFAFFIAN, two-step elimination)",
-            "serial_plain_calls": {"value": serial_rate, "seconds": serial_s,
-                                   "tflops": flops / serial_s / 1e12,
+            "serial_plain_calls": {"value": serial_rate, "requests": n_serial,
+                                   "seconds": serial_s,
+                                   "tflops": flops_of(n_serial) / serial_s / 1e12,
                                    "api": "skew_pfaffian_twostep, one call per request, back to back"},
-            "saturation": {"value": n_requests / sat_s, "seconds": sat_s,
-                           "tflops": flops / sat_s / 1e12,
-                           "p50_ms": float(np.percentile(sat_lat, 50)),
-                           "p99_ms": float(np.percentile(sat_lat, 99)),
-                           "speedup_vs_serial": serial_s / sat_s},
+            "saturation": sat,
             "poisson": rates[1],
             "poisson_rates": rates,
             "factors_kept": {
                 "requests": "SKEW_SERVE_FACTORS (pivoted LTL^T, t and piv kept)",
-                "serial_plain_calls": {"value": n_requests / serial_f_s, "seconds": serial_f_s,
+                "serial_plain_calls": {"value": n_factors / serial_f_s, "requests": n_factors,
+                                       "seconds": serial_f_s,
                                        "api": "skew_pfaffian, one call per request, back to back"},
-                "saturation": {"value": n_requests / sat_f_s, "seconds": sat_f_s,
-                               "p50_ms": float(np.percentile(sat_f_lat, 50)),
-                               "p99_ms": float(np.percentile(sat_f_lat, 99)),
-                               "speedup_vs_serial": serial_f_s / sat_f_s}},
+                "saturation": sat_f},
             "server": "budget 64 GB, 4 streams, batched kernel for n <= 512"
                       + (f"; one server per rank on {world} size-balanced shares" if world > 1 else "")}
 
@@ -969,12 +1035,11 @@ def run_ours(args):
     achieved = sk["flops"] / (sk["ms"] / 1e3) / 1e12 if sk["ms"] > 0 else None
     ratio = recorded_traffic()
     traffic = (ratio * sk["bytes"] / sk["launches"]) if (ratio and sk["launches"]) else None
-    kernels = {k: {"ms_per_step": v["ms"] / K, "launches_per_step": v["launches"] / K,
-                   "share": v["ms"] / ms if ms > 0 else None}
-               for k, v in prof.items()}
+    kernels = kernel_table(prof, K, ms)
     panel = prof["panel"]
     kernels["panel"]["achieved_gbs"] = (panel["bytes"] / (panel["ms"] / 1e3) / 1e9
                                         if panel["ms"] > 0 else None)
+    kernels["panel"]["us_per_column_step"] = panel["ms"] / K * 1e3 / max(n - 1, 1)
 
     # ---- end to end through the host-buffer C-ABI call (pinned host buffers)
     e2e = None
@@ -1043,7 +1108,8 @@ def run_ours(args):
     serving = None
     if not args.skip_serving:
         serving = run_serving_leg(skew, inputs, torch, dev, args.serve_requests,
-                                  args.serve_poisson, rank=rank, world=world)
+                                  args.serve_poisson, args.serve_serial, args.serve_factors,
+                                  rank=rank, world=world)
 
     cpu = None
     parity = None
@@ -1060,7 +1126,9 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(n, nb, seed),
+            "config": dict(workload_config(n, nb, seed),
+                           **({"serving_workload": serving["workload"]} if serving else {}),
+                           **({"batched_workload": batched["workload"]} if batched else {})),
             "pct_of_fp64_peak": 100.0 * (value / world) / peak,
             "roofline": {"kernel": "skr2k (fused skew rank-2k trailing update, DMMA)",
                          "bound": "tensor", "achieved": achieved, "peak": peak,

@@ -141,6 +141,17 @@ int skew_set_nb_table(int count, const int64_t *n_upper, const int32_t *nb);
 int skew_set_batched_nb_table(int count, const int32_t *n_upper, const int32_t *nb);
 int skew_get_batched_nb(int n);
 
+/* The same table with the trailing update's warp tile per bucket as well: a matrix of
+ * order n <= n_upper[i] also takes warp_tile[i] (16 or 32; NULL: 32 for every bucket),
+ * the side of the square tile of the lower triangle that one warp of the CTA updates
+ * with 8 x 8 FP64 DMMA sub-tiles (16 wastes less on the ragged edge of small orders,
+ * 32 reuses each staged operand over more sub-tiles).  No counterpart in the paper.
+ * Returns 0, or -1 / -2 / -3 / -4 for a bad count / n_upper / nb / warp_tile;
+ * skew_get_batched_warp_tile(n) reports the tile an order takes. */
+int skew_set_batched_tiles(int count, const int32_t *n_upper, const int32_t *nb,
+                           const int32_t *warp_tile);
+int skew_get_batched_warp_tile(int n);
+
 /*
  * Device workspace, in bytes, that skew_ltlt / skew_pfaffian need for order n and
  * panel width nb (0 = default).  `with_L` = 0 gives the figure for skew_pfaffian,
@@ -244,8 +255,14 @@ int skew_pfaffian_noalloc(int64_t n, double *A, int64_t lda, double *logabs,
  *                             (Ozaki-type error-free splitting); with k column pairs
  *                             the update differs from the exact one by at most about
  *                             (2.02 k + 0.5) 2^-53 (row max of U)(row max of V), plus
- *                             the rounding of the final FP64 add.  At most 32 column
- *                             pairs per update (panel width nb <= 64).
+ *                             the rounding of the final FP64 add.  In the
+ *                             factorization's trailing updates each pair (a_p, w_p)
+ *                             is first balanced to (2^e a_p, 2^-e w_p) with
+ *                             2^(2e) about the size of the T entries in w_p (its
+ *                             term a_p w_p^T - w_p a_p^T is unchanged, exactly), so
+ *                             that large T entries do not raise the row maxima.
+ *                             At most 32 column pairs per update (panel width
+ *                             nb <= 64).
  */
 #define SKEW_PRECISION_FP64 0
 #define SKEW_PRECISION_SPLIT_BF16 1
@@ -468,6 +485,17 @@ int skew_server_release(skew_server *server, uint64_t ticket);
  * SKEW_SERVE_PFAFFIAN request (it keeps no factors). */
 int skew_server_copy_factors(skew_server *server, uint64_t ticket, double *t_host,
                              int32_t *piv_host, double *L_host, int64_t ldl);
+
+/* Where the latency of a finished request (not yet released) went, in seconds:
+ * queued_s from submission to admission (waiting for the memory budget), waiting_s from
+ * admission to the launch of its work (waiting for a free stream, or for the batch it
+ * joined), running_s from that launch to the worker's observing its completion (device
+ * time of its launch, which it may share with a batch, plus the worker's polling).
+ * Their sum is the latency skew_server_wait reports.  Any pointer may be NULL.  Returns
+ * 0, -1 / -2 for a bad server / ticket, SKEW_ERR_BUSY while the request has not
+ * finished (or failed before its launch).  No counterpart in the paper. */
+int skew_server_timing(skew_server *server, uint64_t ticket, double *queued_s,
+                       double *waiting_s, double *running_s);
 
 /* Budget bytes in use, requests waiting for admission, requests admitted or running. */
 int skew_server_stats(skew_server *server, size_t *used_bytes, int *queued, int *in_flight);

@@ -40,6 +40,8 @@ SIGNATURES = {
     "skew_set_nb_table": ([_i32, _vp, _vp], _i32),
     "skew_set_batched_nb_table": ([_i32, _vp, _vp], _i32),
     "skew_get_batched_nb": ([_i32], _i32),
+    "skew_set_batched_tiles": ([_i32, _vp, _vp, _vp], _i32),
+    "skew_get_batched_warp_tile": ([_i32], _i32),
     "skew_workspace_bytes": ([_i64, _i32, _i32], _sz),
     "skew_ltlt": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
     "skew_pfaffian": ([_i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
@@ -64,6 +66,7 @@ SIGNATURES = {
     "skew_server_wait": ([_vp, ctypes.c_uint64, _dbl, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
     "skew_server_release": ([_vp, ctypes.c_uint64], _i32),
     "skew_server_stats": ([_vp, _vp, _vp, _vp], _i32),
+    "skew_server_timing": ([_vp, ctypes.c_uint64, _vp, _vp, _vp], _i32),
     "skew_server_copy_factors": ([_vp, ctypes.c_uint64, _vp, _vp, _vp, _i64], _i32),
     "skew_server_destroy": ([_vp], _i32),
 }
@@ -118,9 +121,11 @@ def _install_saved_nb_table(L):
     nbs = (ctypes.c_int32 * max(len(table), 1))(*[int(b) for _, b in table])
     L.skew_set_nb_table(len(table), ctypes.cast(nu, ctypes.c_void_p), ctypes.cast(nbs, ctypes.c_void_p))
     bt = saved.get("batched_table", [])
-    bu = (ctypes.c_int32 * max(len(bt), 1))(*[int(a) for a, _ in bt])
-    bn = (ctypes.c_int32 * max(len(bt), 1))(*[int(b) for _, b in bt])
-    L.skew_set_batched_nb_table(len(bt), ctypes.cast(bu, ctypes.c_void_p), ctypes.cast(bn, ctypes.c_void_p))
+    bu = (ctypes.c_int32 * max(len(bt), 1))(*[int(e[0]) for e in bt])
+    bn = (ctypes.c_int32 * max(len(bt), 1))(*[int(e[1]) for e in bt])
+    bw = (ctypes.c_int32 * max(len(bt), 1))(*[int(e[2]) if len(e) > 2 else 32 for e in bt])
+    L.skew_set_batched_tiles(len(bt), ctypes.cast(bu, ctypes.c_void_p), ctypes.cast(bn, ctypes.c_void_p),
+                             ctypes.cast(bw, ctypes.c_void_p))
 
 
 def _check(fn: str, status: int):
@@ -189,18 +194,25 @@ def default_nb(n: int) -> int:
 
 
 def set_batched_nb_table(table):
-    """Install ``[(n_upper, nb), ...]`` (nb in 8, 16, 32) as the batched kernels' panel
-    width per order bucket; an empty list restores 16."""
+    """Install ``[(n_upper, nb), ...]`` or ``[(n_upper, nb, warp_tile), ...]`` (nb in 8,
+    16, 32; warp_tile in 16, 32, default 32) as the batched kernels' panel width and
+    update warp tile per order bucket; an empty list restores width 16, tile 32."""
     count = len(table)
-    nu = (ctypes.c_int32 * max(count, 1))(*[int(a) for a, _ in table])
-    nbs = (ctypes.c_int32 * max(count, 1))(*[int(b) for _, b in table])
-    _check("skew_set_batched_nb_table",
-           lib().skew_set_batched_nb_table(count, ctypes.cast(nu, ctypes.c_void_p),
-                                           ctypes.cast(nbs, ctypes.c_void_p)))
+    nu = (ctypes.c_int32 * max(count, 1))(*[int(e[0]) for e in table])
+    nbs = (ctypes.c_int32 * max(count, 1))(*[int(e[1]) for e in table])
+    wts = (ctypes.c_int32 * max(count, 1))(*[int(e[2]) if len(e) > 2 else 32 for e in table])
+    _check("skew_set_batched_tiles",
+           lib().skew_set_batched_tiles(count, ctypes.cast(nu, ctypes.c_void_p),
+                                        ctypes.cast(nbs, ctypes.c_void_p),
+                                        ctypes.cast(wts, ctypes.c_void_p)))
 
 
 def batched_nb(n: int) -> int:
     return int(lib().skew_get_batched_nb(n))
+
+
+def batched_warp_tile(n: int) -> int:
+    return int(lib().skew_get_batched_warp_tile(n))
 
 
 def set_nb_table(table):
@@ -500,8 +512,13 @@ class Server:
                                     ctypes.byref(sg), ctypes.byref(inf), ctypes.byref(tp),
                                     ctypes.byref(pp), ctypes.byref(lp), ctypes.byref(lat))
         _check("skew_server_wait", st)
-        return {"logabs": la.value, "sign": sg.value, "info": inf.value, "t_ptr": tp.value,
-                "piv_ptr": pp.value, "L_ptr": lp.value, "latency_s": lat.value}
+        out = {"logabs": la.value, "sign": sg.value, "info": inf.value, "t_ptr": tp.value,
+               "piv_ptr": pp.value, "L_ptr": lp.value, "latency_s": lat.value}
+        q, w, r = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        if lib().skew_server_timing(self._h, ticket, ctypes.byref(q), ctypes.byref(w),
+                                    ctypes.byref(r)) == 0:
+            out.update(queued_s=q.value, waiting_s=w.value, running_s=r.value)
+        return out
 
     def factors(self, ticket: int, n: int, want_L: bool = False):
         """Host copies (t, piv, L or None) of a completed request's factors."""

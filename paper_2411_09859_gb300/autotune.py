@@ -5,7 +5,12 @@ order bucket (skew_set_batched_nb_table), timed on batches of that bucket.  The 
 (``nb_table.json``) and installed again by the package at import.
 
     python -m paper_2411_09859_gb300.autotune [--sizes 512,2048,4096,8192,16384]
-                                              [--candidates 32,48,64,96] [--reps 2]
+                                              [--candidates 32,48,64,96,128] [--reps 2]
+
+Panel widths above 96 use the global-memory panel (the shared-memory one holds at most
+96 columns per row); the candidates include 128 so that the table records what that
+costs.  The batched kernels are tuned over two parameters per order bucket: the panel
+width (8, 16, 32) and the trailing update's warp tile (16 or 32).
 
 The inputs are the synthetic iid N(0,1) skew matrices of ``inputs.skew_gaussian``.
 """
@@ -61,7 +66,7 @@ def table_from_ms(ms: dict):
     return [(int(n), pick(d)) for n, d in sorted(ms.items(), key=lambda e: int(e[0]))]
 
 
-def tune(sizes=(512, 2048, 4096, 8192, 16384), candidates=(32, 48, 64, 96), reps: int = 2):
+def tune(sizes=(512, 2048, 4096, 8192, 16384), candidates=(32, 48, 64, 96, 128), reps: int = 2):
     """Returns ``{"table": [(n_upper, nb), ...], "ms": {n: {nb: ms}}}``."""
     sizes = sorted(int(s) for s in sizes)
     ms = {n: {nb: measure(n, nb, reps) for nb in candidates if nb < n} for n in sizes}
@@ -71,6 +76,7 @@ def tune(sizes=(512, 2048, 4096, 8192, 16384), candidates=(32, 48, 64, 96), reps
 
 BUCKETS = (64, 128, 256, 512)      # order buckets of the batched kernels
 BATCHED_NB = (8, 16, 32)
+BATCHED_WT = (16, 32)
 
 
 def _batch(sizes, seed_base: int):
@@ -125,12 +131,14 @@ def measure_batched_mix(sizes, table_nb, reps: int = 2, batch=None) -> float:
     return total
 
 
-def tune_batched(sizes=None, buckets=BUCKETS, candidates=BATCHED_NB, reps: int = 2):
-    """The batched kernels' width per order bucket, chosen on a workload mix (default:
-    the batched workload, 4096 orders even in [16, 256]): every combination of widths
-    over the buckets the mix populates is timed (both batched kernels, summed) and the
-    fastest kept; a bucket the mix does not reach takes the fastest width on a batch of
-    its own orders."""
+def tune_batched(sizes=None, buckets=BUCKETS, candidates=BATCHED_NB, tiles=BATCHED_WT,
+                 reps: int = 2):
+    """The batched kernels' panel width and update warp tile per order bucket, chosen on
+    a workload mix (default: the batched workload, 4096 orders even in [16, 256]).
+    First every combination of widths over the buckets the mix populates is timed with
+    warp tile 32 (both batched kernels, summed); then, with those widths, every
+    combination of warp tiles.  A bucket the mix does not reach takes the fastest
+    (width, tile) on a batch of its own orders."""
     import itertools
 
     from . import inputs
@@ -142,21 +150,31 @@ def tune_batched(sizes=None, buckets=BUCKETS, candidates=BATCHED_NB, reps: int =
     used = [hi for lo, hi in zip(lows, buckets) if any(lo <= n <= hi for n in sizes)]
     mix_ms = {}
     for combo in itertools.product(candidates, repeat=len(used)):
-        tab = [(hi, nb) for hi, nb in zip(used, combo)]
+        tab = [(hi, nb, 32) for hi, nb in zip(used, combo)]
         mix_ms[combo] = measure_batched_mix(sizes, tab, reps, batch)
-    best = dict(zip(used, min(mix_ms, key=mix_ms.get)))
+    best_nb = dict(zip(used, min(mix_ms, key=mix_ms.get)))
+    wt_ms = {}
+    for combo in itertools.product(tiles, repeat=len(used)):
+        tab = [(hi, best_nb[hi], wt) for hi, wt in zip(used, combo)]
+        wt_ms[combo] = measure_batched_mix(sizes, tab, reps, batch)
+    best_wt = dict(zip(used, min(wt_ms, key=wt_ms.get)))
     del batch
     extra = {}
     for lo, hi in zip(lows, buckets):
-        if hi in best:
+        if hi in best_nb:
             continue
         own = [lo + 2 * ((hi - lo) // 4)] * 256
-        extra[hi] = {nb: measure_batched_mix(own, [(hi, nb)], reps) for nb in candidates}
-        best[hi] = pick(extra[hi])
-    return {"batched_table": [(hi, best[hi]) for hi in buckets],
+        extra[hi] = {(nb, wt): measure_batched_mix(own, [(hi, nb, wt)], reps)
+                     for nb in candidates for wt in tiles}
+        fastest = min(extra[hi].values())
+        nb, wt = min(k for k, v in extra[hi].items() if v <= fastest * (1.0 + TIE))
+        best_nb[hi], best_wt[hi] = nb, wt
+    return {"batched_table": [(hi, best_nb[hi], best_wt[hi]) for hi in buckets],
             "batched_mix_ms": {",".join(map(str, k)): v for k, v in mix_ms.items()},
+            "batched_mix_warp_tile_ms": {",".join(map(str, k)): v for k, v in wt_ms.items()},
             "batched_mix_buckets": used,
-            "batched_own_ms": {str(h): {str(b): v for b, v in d.items()} for h, d in extra.items()}}
+            "batched_own_ms": {str(h): {f"{a},{b}": v for (a, b), v in d.items()}
+                               for h, d in extra.items()}}
 
 
 def save(result, path: str = TABLE_PATH):
@@ -182,7 +200,7 @@ def load(path: str = TABLE_PATH) -> bool:
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--sizes", default="512,2048,4096,8192,16384")
-    ap.add_argument("--candidates", default="32,48,64,96")
+    ap.add_argument("--candidates", default="32,48,64,96,128")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--no-save", action="store_true")
     ap.add_argument("--batched-only", action="store_true",

@@ -496,7 +496,7 @@ int factor_twostep(int64_t n, double *A, int64_t lda, double *a, int32_t *piv, i
 namespace skew {
 namespace {
 std::mutex g_bnb_mutex;
-BatchedNb g_bnb = {0, {0}, {0}};
+BatchedNb g_bnb = {0, {0}, {0}, {0}};
 }  // namespace
 
 BatchedNb batched_nb_table() {
@@ -575,24 +575,36 @@ int skew_set_nb_table(int count, const int64_t *n_upper, const int32_t *nb) {
     return SKEW_OK;
 }
 
-int skew_set_batched_nb_table(int count, const int32_t *n_upper, const int32_t *nb) {
+int skew_set_batched_tiles(int count, const int32_t *n_upper, const int32_t *nb,
+                           const int32_t *warp_tile) {
     if (count < 0 || count > 8) return -1;
     if (count > 0 && n_upper == nullptr) return -2;
     if (count > 0 && nb == nullptr) return -3;
-    BatchedNb t = {count, {0}, {0}};
+    BatchedNb t = {count, {0}, {0}, {0}};
     for (int i = 0; i < count; ++i) {
         if (nb[i] != 8 && nb[i] != 16 && nb[i] != 32) return -3;
         if (n_upper[i] < 1 || (i > 0 && n_upper[i] <= n_upper[i - 1])) return -2;
+        const int wt = warp_tile ? warp_tile[i] : 32;
+        if (wt != 16 && wt != 32) return -4;
         t.n_upper[i] = n_upper[i];
         t.nb[i] = nb[i];
+        t.wt[i] = wt;
     }
     std::lock_guard<std::mutex> lock(g_bnb_mutex);
     g_bnb = t;
     return SKEW_OK;
 }
 
+int skew_set_batched_nb_table(int count, const int32_t *n_upper, const int32_t *nb) {
+    return skew_set_batched_tiles(count, n_upper, nb, nullptr);
+}
+
 int skew_get_batched_nb(int n) {
     return batched_nb_for(batched_nb_table(), n);
+}
+
+int skew_get_batched_warp_tile(int n) {
+    return batched_wt_for(batched_nb_table(), n);
 }
 
 int skew_default_nb(int64_t n) {

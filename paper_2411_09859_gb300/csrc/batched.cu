@@ -290,7 +290,7 @@ __device__ Cand blk_cand(Cand x, bool bad, BlkShared &sh, bool &any_bad) {
 
 // smem: Lp[NB][nmax] (panel L columns), Ws[NB/2+1][nmax] (odd W columns),
 // sv[nmax] (v of the current step)
-template <int NB>
+template <int NB, int WT>
 __device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_t *sign,
                                    int32_t *info, double *smem, int nmax, BlkShared &sh,
                                    BatchShared &fin) {
@@ -422,7 +422,7 @@ __device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_
             const int m = n - s - 1;
             const int K = 2 * npairs;                  // U = [a | -w], V = [w | a]
             const int K4 = (K + 3) / 4 * 4;
-            const int nt = (m + 31) / 32;
+            const int nt = (m + WT - 1) / WT;
             const int ntiles = nt * (nt + 1) / 2;
             const int g = lane >> 2, tg = lane & 3;
             auto acol = [&](int pp) { return (2 * pp + 1 < b) ? 2 * pp + 1 : b - 1; };
@@ -430,18 +430,19 @@ __device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_
                 int bi = 0;
                 while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
                 const int bj = tile - bi * (bi + 1) / 2;
-                const bool diag = bi == bj;   // a tile on the diagonal: 10 of its 16 sub-tiles
-                double acc[4][4][2];
+                const bool diag = bi == bj;   // a diagonal tile: its sub-tiles on or below the diagonal
+                constexpr int FR = WT / 8;    // 8 x 8 DMMA sub-tiles per warp-tile side
+                double acc[FR][FR][2];
 #pragma unroll
-                for (int mi = 0; mi < 4; ++mi)
+                for (int mi = 0; mi < FR; ++mi)
 #pragma unroll
-                    for (int ni = 0; ni < 4; ++ni) acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
+                    for (int ni = 0; ni < FR; ++ni) acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
                 for (int kb = 0; kb < K4; kb += 4) {
                     const int kc = kb + tg;
-                    double af[4], bf[4];
+                    double af[FR], bf[FR];
 #pragma unroll
-                    for (int mi = 0; mi < 4; ++mi) {
-                        const int li = bi * 32 + mi * 8 + g;          // local row in C
+                    for (int mi = 0; mi < FR; ++mi) {
+                        const int li = bi * WT + mi * 8 + g;          // local row in C
                         const int i = s + 1 + li;
                         double u = 0.0;
                         if (li < m && kc < K)
@@ -449,8 +450,8 @@ __device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_
                         af[mi] = u;
                     }
 #pragma unroll
-                    for (int ni = 0; ni < 4; ++ni) {
-                        const int lj = bj * 32 + ni * 8 + g;
+                    for (int ni = 0; ni < FR; ++ni) {
+                        const int lj = bj * WT + ni * 8 + g;
                         const int j = s + 1 + lj;
                         double v = 0.0;
                         if (lj < m && kc < K)
@@ -458,20 +459,20 @@ __device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_
                         bf[ni] = v;
                     }
 #pragma unroll
-                    for (int mi = 0; mi < 4; ++mi)
+                    for (int mi = 0; mi < FR; ++mi)
 #pragma unroll
-                        for (int ni = 0; ni < 4; ++ni)
+                        for (int ni = 0; ni < FR; ++ni)
                             if (!diag || mi >= ni)   // above the diagonal: nothing stored
                                 dmma884(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
                 }
 #pragma unroll
-                for (int mi = 0; mi < 4; ++mi) {
-                    const int li = bi * 32 + mi * 8 + g;
+                for (int mi = 0; mi < FR; ++mi) {
+                    const int li = bi * WT + mi * 8 + g;
 #pragma unroll
-                    for (int ni = 0; ni < 4; ++ni)
+                    for (int ni = 0; ni < FR; ++ni)
 #pragma unroll
                         for (int cc = 0; cc < 2; ++cc) {
-                            const int lj = bj * 32 + ni * 8 + 2 * tg + cc;
+                            const int lj = bj * WT + ni * 8 + 2 * tg + cc;
                             if (li < m && lj < m && li > lj) {
                                 double *dst = X + (int64_t)(s + 1 + lj) * ldx + (s + 1 + li);
                                 *dst = *dst + acc[mi][ni][cc];
@@ -562,7 +563,7 @@ __device__ void factor_one_blocked(const skew_problem &P, double *logabs, int32_
 // entries a_j, P.piv the even-step exchanges (identity elsewhere); P.L is not used.
 // smem: Vp[NB][nmax] (c = 2q: l_q, 2q+1: y_q), sv[nmax].
 // ------------------------------------------------------------------------------------
-template <int NB>
+template <int NB, int WT>
 __device__ void pfaff_one_twostep(const skew_problem &P, double *logabs, int32_t *sign,
                                   int32_t *info, double *smem, int nmax, BlkShared &sh,
                                   BatchShared &fin) {
@@ -661,25 +662,26 @@ __device__ void pfaff_one_twostep(const skew_problem &P, double *logabs, int32_t
             // C = X[k1:, k1:] += sum_q (l_q y_q^T - y_q l_q^T): U = [l | -y], V = [y | l]
             const int K = 2 * np;
             const int K4 = (K + 3) / 4 * 4;
-            const int nt = (m + 31) / 32;
+            const int nt = (m + WT - 1) / WT;
             const int ntiles = nt * (nt + 1) / 2;
             const int g = lane >> 2, tg = lane & 3;
             for (int tile = warp; tile < ntiles; tile += nwarps) {
                 int bi = 0;
                 while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
                 const int bj = tile - bi * (bi + 1) / 2;
-                const bool diag = bi == bj;   // a tile on the diagonal: 10 of its 16 sub-tiles
-                double acc[4][4][2];
+                const bool diag = bi == bj;   // a diagonal tile: its sub-tiles on or below the diagonal
+                constexpr int FR = WT / 8;    // 8 x 8 DMMA sub-tiles per warp-tile side
+                double acc[FR][FR][2];
 #pragma unroll
-                for (int mi = 0; mi < 4; ++mi)
+                for (int mi = 0; mi < FR; ++mi)
 #pragma unroll
-                    for (int ni = 0; ni < 4; ++ni) acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
+                    for (int ni = 0; ni < FR; ++ni) acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
                 for (int kb = 0; kb < K4; kb += 4) {
                     const int kc = kb + tg;
-                    double af[4], bf[4];
+                    double af[FR], bf[FR];
 #pragma unroll
-                    for (int mi = 0; mi < 4; ++mi) {
-                        const int li = bi * 32 + mi * 8 + g;
+                    for (int mi = 0; mi < FR; ++mi) {
+                        const int li = bi * WT + mi * 8 + g;
                         const int i = k1 + li;
                         double u = 0.0;
                         if (li < m && kc < K)
@@ -688,8 +690,8 @@ __device__ void pfaff_one_twostep(const skew_problem &P, double *logabs, int32_t
                         af[mi] = u;
                     }
 #pragma unroll
-                    for (int ni = 0; ni < 4; ++ni) {
-                        const int lj = bj * 32 + ni * 8 + g;
+                    for (int ni = 0; ni < FR; ++ni) {
+                        const int lj = bj * WT + ni * 8 + g;
                         const int j = k1 + lj;
                         double v = 0.0;
                         if (lj < m && kc < K)
@@ -698,20 +700,20 @@ __device__ void pfaff_one_twostep(const skew_problem &P, double *logabs, int32_t
                         bf[ni] = v;
                     }
 #pragma unroll
-                    for (int mi = 0; mi < 4; ++mi)
+                    for (int mi = 0; mi < FR; ++mi)
 #pragma unroll
-                        for (int ni = 0; ni < 4; ++ni)
+                        for (int ni = 0; ni < FR; ++ni)
                             if (!diag || mi >= ni)   // above the diagonal: nothing stored
                                 dmma884(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
                 }
 #pragma unroll
-                for (int mi = 0; mi < 4; ++mi) {
-                    const int li = bi * 32 + mi * 8 + g;
+                for (int mi = 0; mi < FR; ++mi) {
+                    const int li = bi * WT + mi * 8 + g;
 #pragma unroll
-                    for (int ni = 0; ni < 4; ++ni)
+                    for (int ni = 0; ni < FR; ++ni)
 #pragma unroll
                         for (int cc = 0; cc < 2; ++cc) {
-                            const int lj = bj * 32 + ni * 8 + 2 * tg + cc;
+                            const int lj = bj * WT + ni * 8 + 2 * tg + cc;
                             if (li < m && lj < m && li > lj) {
                                 double *dst = X + (int64_t)(k1 + lj) * ldx + (k1 + li);
                                 *dst = *dst + acc[mi][ni][cc];
@@ -791,10 +793,20 @@ batched_twostep_kernel(int count, const skew_problem *problems, const int32_t *o
         double *la = logabs ? logabs + b : nullptr;
         int32_t *sg = sign ? sign + b : nullptr, *inf = info ? info + b : nullptr;
         const int nm = max_n > 1 ? max_n : 1;
+        const bool wt16 = batched_wt_for(tab, n) == 16;
         switch (batched_nb_for(tab, n)) {
-            case 8: pfaff_one_twostep<8>(P, la, sg, inf, s_blk, nm, sh, fin); break;
-            case 32: pfaff_one_twostep<32>(P, la, sg, inf, s_blk, nm, sh, fin); break;
-            default: pfaff_one_twostep<16>(P, la, sg, inf, s_blk, nm, sh, fin); break;
+            case 8:
+                if (wt16) pfaff_one_twostep<8, 16>(P, la, sg, inf, s_blk, nm, sh, fin);
+                else pfaff_one_twostep<8, 32>(P, la, sg, inf, s_blk, nm, sh, fin);
+                break;
+            case 32:
+                if (wt16) pfaff_one_twostep<32, 16>(P, la, sg, inf, s_blk, nm, sh, fin);
+                else pfaff_one_twostep<32, 32>(P, la, sg, inf, s_blk, nm, sh, fin);
+                break;
+            default:
+                if (wt16) pfaff_one_twostep<16, 16>(P, la, sg, inf, s_blk, nm, sh, fin);
+                else pfaff_one_twostep<16, 32>(P, la, sg, inf, s_blk, nm, sh, fin);
+                break;
         }
     }
 }
@@ -824,10 +836,20 @@ batched_blocked_kernel(int count, const skew_problem *problems, const int32_t *o
         double *la = logabs ? logabs + b : nullptr;
         int32_t *sg = sign ? sign + b : nullptr, *inf = info ? info + b : nullptr;
         const int nm = max_n > 1 ? max_n : 1;
+        const bool wt16 = batched_wt_for(tab, n) == 16;
         switch (batched_nb_for(tab, n)) {
-            case 8: factor_one_blocked<8>(P, la, sg, inf, s_blk, nm, sh, fin); break;
-            case 32: factor_one_blocked<32>(P, la, sg, inf, s_blk, nm, sh, fin); break;
-            default: factor_one_blocked<16>(P, la, sg, inf, s_blk, nm, sh, fin); break;
+            case 8:
+                if (wt16) factor_one_blocked<8, 16>(P, la, sg, inf, s_blk, nm, sh, fin);
+                else factor_one_blocked<8, 32>(P, la, sg, inf, s_blk, nm, sh, fin);
+                break;
+            case 32:
+                if (wt16) factor_one_blocked<32, 16>(P, la, sg, inf, s_blk, nm, sh, fin);
+                else factor_one_blocked<32, 32>(P, la, sg, inf, s_blk, nm, sh, fin);
+                break;
+            default:
+                if (wt16) factor_one_blocked<16, 16>(P, la, sg, inf, s_blk, nm, sh, fin);
+                else factor_one_blocked<16, 32>(P, la, sg, inf, s_blk, nm, sh, fin);
+                break;
         }
     }
 }

@@ -251,17 +251,25 @@ bool twostep_fits(int64_t n, int nb, int sms);
 int launch_finish_twostep(int64_t n, const double *a, const int32_t *piv, const Ctrl *ctrl,
                           double *logabs, int32_t *sign, int32_t *info, cudaStream_t stream);
 
-// Panel width of the CTA-local batched kernels per order bucket: n <= n_upper[i] takes
-// nb[i] (8, 16 or 32; first match), larger orders the last entry; count 0: 16.
+// Panel width and update warp tile of the CTA-local batched kernels per order bucket:
+// n <= n_upper[i] takes nb[i] (8, 16 or 32) and wt[i] (16 or 32: each warp of the
+// trailing update owns a wt x wt tile of the lower triangle; first match), larger
+// orders the last entry; count 0: width 16, warp tile 32.
 struct BatchedNb {
     int count;
     int n_upper[8];
     int nb[8];
+    int wt[8];
 };
 __host__ __device__ inline int batched_nb_for(const BatchedNb &t, int n) {
     for (int i = 0; i < t.count; ++i)
         if (n <= t.n_upper[i]) return t.nb[i];
     return t.count > 0 ? t.nb[t.count - 1] : 16;
+}
+__host__ __device__ inline int batched_wt_for(const BatchedNb &t, int n) {
+    for (int i = 0; i < t.count; ++i)
+        if (n <= t.n_upper[i]) return t.wt[i];
+    return t.count > 0 ? t.wt[t.count - 1] : 32;
 }
 BatchedNb batched_nb_table();     // the table installed by skew_set_batched_nb_table
 

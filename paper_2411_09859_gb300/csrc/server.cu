@@ -2,8 +2,10 @@
 //
 // Requests (a device matrix each) are queued by skew_server_submit.  A worker thread
 //   - admits queued requests in arrival order while their device memory fits in the
-//     budget (the matrix copy, t, piv, optionally L): admission happens as soon as
-//     memory frees up, also while other work is running;
+//     budget: the resident buffers (the matrix copy, t, piv, optionally L), held until
+//     the request is released, and the workspace its launch allocates (its own call's,
+//     or its share of a batched launch), held until its work has finished; admission
+//     happens as soon as memory frees up, also while other work is running;
 //   - launches admitted work on the first free stream: all admitted small requests of
 //     one kind together in one batched launch (skew_ltlt_batched for requests that keep
 //     their factors, skew_pfaffian_batched for Pfaffian-only ones), or one large
@@ -46,11 +48,13 @@ struct Request {
     double *d_logabs = nullptr;
     int32_t *d_sign = nullptr, *d_info = nullptr;
     HostResult *host = nullptr;
-    size_t bytes = 0;
+    size_t bytes = 0;              // resident buffers (matrix, factors, result words)
+    size_t ws_bytes = 0;           // transient workspace of its launch, held until done
+    bool ws_held = false;          // ws_bytes counted in `used`
     int lane = -1;                 // stream its work was enqueued on
     ReqState state = ReqState::Queued;
     int status = SKEW_OK;
-    Clock::time_point t_submit, t_done;
+    Clock::time_point t_submit, t_admit, t_launch, t_done;
 };
 
 struct Lane {                      // one stream and what runs on it
@@ -99,6 +103,27 @@ size_t request_bytes(int64_t n, bool want_L) {
                al(sizeof(double)) + 2 * al(sizeof(int32_t));
     if (want_L) b += al(nn * nn * sizeof(double));
     return b;
+}
+
+// Device memory a request's launch allocates for the duration of its work: the
+// workspace of its own call, or its share of a batched launch (a descriptor, the
+// batch's result words and the batched kernel's counters).
+size_t request_ws_bytes(const skew_server *s, const Request &r) {
+    if (r.n <= batch_limit(s, r)) return 1024 + skew::batched_workspace_bytes(1, (int)r.n);
+    if (r.mode == SKEW_SERVE_FACTORS_L) return skew_workspace_bytes(r.n, 0, 1);
+    if (r.mode == SKEW_SERVE_PFAFFIAN) {
+        const size_t a = skew_workspace_bytes_twostep(r.n, 0, SKEW_PRECISION_FP64);
+        const size_t b = skew_workspace_bytes(r.n, 0, 0);   // fallback of large orders
+        return a > b ? a : b;
+    }
+    return skew_workspace_bytes(r.n, 0, 0);
+}
+
+// The launch of the request has ended (completed or failed): its workspace is back.
+void drop_ws(skew_server *s, Request &r) {
+    if (!r.ws_held) return;
+    s->used -= r.ws_bytes;
+    r.ws_held = false;
 }
 
 HostResult *take_host_slot(skew_server *s) {
@@ -270,26 +295,33 @@ bool launch_next(skew_server *s, int lane_index) {
         }
         if (status == SKEW_OK) status = copy_results_back(r, ln.stream);
     }
+    // The tickets stay Running, also when the launch failed part way, until the lane's
+    // event shows that everything enqueued so far (copies from the caller's matrix,
+    // kernels, copies into the result slots) has finished; the completion pass then
+    // marks them Done, or Failed with the status kept here.
+    const auto launched = Clock::now();
     for (uint64_t tk : ln.tickets) {
         Request &r = s->reqs[tk];
-        r.state = status == SKEW_OK ? ReqState::Running : ReqState::Failed;
+        r.state = ReqState::Running;
         r.status = status;
         r.lane = lane_index;
+        r.t_launch = launched;
     }
-    if (status == SKEW_OK) {
-        cudaError_t e = cudaEventRecord(ln.done, ln.stream);
-        if (e != cudaSuccess) {
-            skew::set_last_error(e);
-            for (uint64_t tk : ln.tickets) {
-                s->reqs[tk].state = ReqState::Failed;
-                s->reqs[tk].status = SKEW_ERR_CUDA;
-            }
-            status = SKEW_ERR_CUDA;
-        }
-    }
-    if (status != SKEW_OK) {
+    cudaError_t e = cudaEventRecord(ln.done, ln.stream);
+    if (e != cudaSuccess) {
+        // no event: wait for the lane's stream here instead
+        skew::set_last_error(e);
+        cudaGetLastError();
+        cudaStreamSynchronize(ln.stream);
+        cudaGetLastError();
         const auto now = Clock::now();
-        for (uint64_t tk : ln.tickets) s->reqs[tk].t_done = now;
+        for (uint64_t tk : ln.tickets) {
+            Request &r = s->reqs[tk];
+            r.state = ReqState::Failed;
+            if (r.status == SKEW_OK) r.status = SKEW_ERR_CUDA;
+            r.t_done = now;
+            drop_ws(s, r);
+        }
         ln.tickets.clear();
         s->cv_done.notify_all();
         return true;
@@ -312,13 +344,16 @@ void worker_main(skew_server *s) {
             for (uint64_t tk : ln.tickets) {
                 Request &r = s->reqs[tk];
                 r.t_done = now;
-                if (q == cudaSuccess) {
+                if (q == cudaSuccess && r.status == SKEW_OK) {
                     r.state = ReqState::Done;
                 } else {
-                    skew::set_last_error(q);
+                    if (q != cudaSuccess) {
+                        skew::set_last_error(q);
+                        r.status = SKEW_ERR_CUDA;
+                    }
                     r.state = ReqState::Failed;
-                    r.status = SKEW_ERR_CUDA;
                 }
+                drop_ws(s, r);
             }
             if (q != cudaSuccess) cudaGetLastError();
             ln.tickets.clear();
@@ -329,8 +364,10 @@ void worker_main(skew_server *s) {
         // 2. admission, in arrival order, while memory fits the budget
         while (!s->queue.empty()) {
             Request &r = s->reqs[s->queue.front()];
-            if (s->used + r.bytes > s->budget) break;
-            s->used += r.bytes;
+            if (s->used + r.bytes + r.ws_bytes > s->budget) break;
+            s->used += r.bytes + r.ws_bytes;
+            r.ws_held = true;
+            r.t_admit = Clock::now();
             r.state = ReqState::Admitted;
             s->admitted.push_back(r.ticket);
             s->queue.pop_front();
@@ -400,14 +437,15 @@ int skew_server_submit(skew_server *s, int64_t n, const double *A, int64_t lda, 
     if (ticket == nullptr) return -6;
     const size_t bytes = request_bytes(n, mode == SKEW_SERVE_FACTORS_L);
     std::lock_guard<std::mutex> lock(s->mu);
-    if (bytes > s->budget) return SKEW_ERR_NOMEM;
     Request r;
-    r.ticket = s->next_ticket++;
     r.n = n;
     r.mode = mode;
+    r.bytes = bytes;
+    r.ws_bytes = request_ws_bytes(s, r);
+    if (bytes + r.ws_bytes > s->budget) return SKEW_ERR_NOMEM;
+    r.ticket = s->next_ticket++;
     r.src = A;
     r.src_ld = lda;
-    r.bytes = bytes;
     r.t_submit = Clock::now();
     r.host = take_host_slot(s);
     if (r.host == nullptr) return SKEW_ERR_NOMEM;
@@ -455,6 +493,24 @@ int skew_server_wait(skew_server *s, uint64_t ticket, double timeout_s, double *
     if (piv) *piv = factors ? r.piv : nullptr;
     if (L) *L = r.L;
     if (latency_s) *latency_s = std::chrono::duration<double>(r.t_done - r.t_submit).count();
+    return SKEW_OK;
+}
+
+int skew_server_timing(skew_server *s, uint64_t ticket, double *queued_s, double *waiting_s,
+                       double *running_s) {
+    if (s == nullptr) return -1;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return -2;
+    const Request &r = it->second;
+    if (r.state != ReqState::Done && r.state != ReqState::Failed) return SKEW_ERR_BUSY;
+    if (r.lane < 0) return SKEW_ERR_BUSY;            // failed before it was launched
+    auto sec = [](Clock::time_point a, Clock::time_point b) {
+        return std::chrono::duration<double>(b - a).count();
+    };
+    if (queued_s) *queued_s = sec(r.t_submit, r.t_admit);
+    if (waiting_s) *waiting_s = sec(r.t_admit, r.t_launch);
+    if (running_s) *running_s = sec(r.t_launch, r.t_done);
     return SKEW_OK;
 }
 

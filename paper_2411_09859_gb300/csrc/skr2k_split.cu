@@ -22,6 +22,10 @@
 // differs from the exact update by at most about 1.1 * 2^-53 * K * (max row entry of
 // U) * (max row entry of V) -- the size of FP64 rounding in an ordinary dot product,
 // but measured against row maxima rather than entry by entry.  K = 2 * pairs <= 64.
+// So that a large sub-diagonal entry of T does not raise the row maxima (w_j carries
+// t_j), each pair of the trailing update is first balanced by exact powers of two,
+// (a_p, w_p) -> (2^e_p a_p, 2^-e_p w_p), which leaves its term a_p w_p^T - w_p a_p^T
+// unchanged (pair_balance_exp).
 //
 // Update kernel: persistent, one CTA per SM, tiles of 128 rows x 32 columns of the
 // lower triangle of C, each CTA taking a contiguous run of tiles (consecutive tiles
@@ -120,10 +124,39 @@ __device__ __forceinline__ unsigned int pack2(int lo, int hi) {
     return bf16_bits(lo) | (bf16_bits(hi) << 16);
 }
 
+// 2^e as a double (|e| <= 1000: a normal number)
+__device__ __forceinline__ double pow2(int e) {
+    return __longlong_as_double((long long)(1023 + e) << 52);
+}
+
+// Balancing exponent e_p of pair p of the Tridiag / Fused kinds.  The pair's term
+// a_p w_p^T - w_p a_p^T is unchanged when a_p is scaled by 2^e_p and w_p by 2^-e_p
+// (exactly, as both are powers of two).  With |a| <= 1 (entries of L) and w_j =
+// t_j a_{j+1} - t_{j-1} a_{j-1} (+ x), |w_p| is about max(|t_{j-1}|, |t_j|) (= T_p), so
+// e_p = ceil(log2(T_p) / 2) brings both columns to about sqrt(T_p): a row then has no
+// column far below its largest entry only because T is large, and the digits keep the
+// precision of the a columns (the bound below is measured against row maxima).
+template <PairKind KIND>
+__device__ __forceinline__ int pair_balance_exp(const PairSource<KIND> &src, int p) {
+    if (KIND == PairKind::Rank2k || src.b < 2) return 0;
+    const int64_t j = 2 * (int64_t)p + 1;
+    double tm;
+    if (j < src.b) {
+        tm = fabs(src.tt[j - 1]);
+        if (j + 1 < src.b) tm = fmax(tm, fabs(src.tt[j]));
+    } else {
+        tm = fabs(src.tt[src.b - 2]);             // b odd: the pair (a_{b-1}, x)
+    }
+    const int ex = exponent_of(tm);
+    if (ex < -1000) return 0;                     // zero (or tiny) coupling
+    const int e = (ex + 1) >> 1;
+    return e > 400 ? 400 : (e < -400 ? -400 : e);
+}
+
 // Pre-pass, four threads per row i (thread g of the row takes pairs 8g .. 8g+7): the
-// exponent E_i of the row's largest pair entry and the digit slices
-// Zu[s][i][0..63] = digits of [a | -w], Zv[s][i][0..63] = digits of [w | a] (pair p in
-// column p of each half, zero past P).
+// pairs balanced by 2^(+-e_p) (pair_balance_exp), the exponent E_i of the row's
+// largest balanced entry, and the digit slices Zu[s][i][0..63] = digits of [a | -w],
+// Zv[s][i][0..63] = digits of [w | a] (pair p in column p of each half, zero past P).
 template <PairKind KIND>
 __global__ void __launch_bounds__(256)
 split_prepare_kernel(int64_t m, PairSource<KIND> src, int P, unsigned short *Zu,
@@ -139,6 +172,11 @@ split_prepare_kernel(int64_t m, PairSource<KIND> src, int P, unsigned short *Zu,
         wv[q] = 0.0;
         if (i < m && p < P) {
             src.get(p, i, av[q], wv[q]);
+            const int e = pair_balance_exp(src, p);
+            if (e != 0) {
+                av[q] *= pow2(e);
+                wv[q] *= pow2(-e);
+            }
             E = max(E, max(exponent_of(av[q]), exponent_of(wv[q])));
         }
     }

@@ -150,7 +150,12 @@ def test_batched_nb_table():
         with pytest.raises(skew.SkewError):
             skew.set_batched_nb_table([(64, 12)])
         skew.set_batched_nb_table([])
-        assert skew.batched_nb(100) == 16
+        assert skew.batched_nb(100) == 16 and skew.batched_warp_tile(100) == 32
+        skew.set_batched_nb_table([(64, 8, 16), (256, 16, 32), (512, 32, 16)])
+        assert [skew.batched_warp_tile(n) for n in (10, 65, 300, 600)] == [16, 32, 16, 16]
+        assert [skew.batched_nb(n) for n in (10, 65, 300)] == [8, 16, 32]
+        with pytest.raises(skew.SkewError):
+            skew.set_batched_nb_table([(64, 8, 24)])
     finally:
         if not autotune.load():
             skew.set_batched_nb_table([])

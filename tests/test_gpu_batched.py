@@ -241,15 +241,16 @@ def test_pfaffian_batched_replays_from_a_cuda_graph():
 
 
 @pytest.mark.parametrize("nb", [8, 16, 32])
-def test_batched_panel_widths_against_oracle(nb):
-    """Every width the batched tuner can choose, forced for all orders, in both
-    batched kernels."""
+@pytest.mark.parametrize("wt", [16, 32])
+def test_batched_panel_widths_against_oracle(nb, wt):
+    """Every (panel width, update warp tile) the batched tuner can choose, forced for
+    all orders, in both batched kernels."""
     from paper_2411_09859_gb300 import autotune
     sizes = [2, 9, 16, 33, 70, 128, 200, 256, 300, 512]
     mats = [inputs.skew_gaussian(n, 7100 + n) for n in sizes]
     try:
-        skew.set_batched_nb_table([(512, nb)])
-        assert skew.batched_nb(100) == nb
+        skew.set_batched_nb_table([(512, nb, wt)])
+        assert skew.batched_nb(100) == nb and skew.batched_warp_tile(100) == wt
         la, sg, info, ts, pivs, Ls = run_batch(mats, want_L=True)
         for b, A in enumerate(mats):
             check_against_oracle(A, la[b], sg[b], info[b], ts[b], pivs[b], Ls[b])

@@ -190,3 +190,24 @@ def test_cancel_and_malformed_requests():
     srv.release(t1)
     assert srv.stats() == {"used_bytes": 0, "queued": 0, "in_flight": 0}
     srv.close()
+
+
+def test_latency_breakdown_sums_to_latency():
+    """Each finished request reports where its latency went (waiting for the budget,
+    for a stream, then running); the three parts are non-negative and add up to the
+    latency skew_server_wait reports."""
+    n = 300
+    A = dev(inputs.skew_gaussian(n, 13))
+    per = 8 * n * n + 8 * n + 4 * n + 4096
+    srv = skew.Server(int(3.5 * per), n_streams=2, small_n_max=128)
+    tickets = [srv.submit(A, pfaffian_only=(i % 2 == 0)) for i in range(8)]
+    queued_any = False
+    for tk in tickets:
+        r = srv.wait(tk, 60.0)
+        parts = (r["queued_s"], r["waiting_s"], r["running_s"])
+        assert all(x >= 0.0 for x in parts)
+        assert abs(sum(parts) - r["latency_s"]) <= 1e-6 + 1e-9 * r["latency_s"]
+        queued_any |= r["queued_s"] > 0.0
+        srv.release(tk)
+    assert queued_any                      # the budget held some requests back
+    srv.close()

@@ -125,3 +125,36 @@ def test_twostep_trivial_sizes():
     assert int(sg.item()) == 1 and float(la.item()) == 0.0
     la, sg, *_ = skew.pfaffian_twostep(torch.zeros((1, 1), dtype=torch.float64, device="cuda"))
     assert int(sg.item()) == 0
+
+
+def test_twostep_from_two_host_threads():
+    """Two host threads call skew_pfaffian_twostep at once, each on its own stream and
+    matrix, with the widest panel (its launch needs the raised shared-memory limit);
+    both results equal the oracle's."""
+    import threading
+    mats = [inputs.skew_gaussian(900 + 2 * i, 5100 + i) for i in range(2)]
+    out = [None, None]
+    err = []
+
+    def work(i):
+        try:
+            s = torch.cuda.Stream()
+            res = []
+            for _ in range(3):
+                la, sg, a, piv, info = skew.pfaffian_twostep(dev(mats[i]), nb=96, stream=s)
+                s.synchronize()
+                res.append((float(la.item()), int(sg.item()), a.cpu().numpy(),
+                            piv.cpu().numpy(), int(info.item())))
+            out[i] = res
+        except Exception as e:                      # reported on the main thread
+            err.append(e)
+
+    th = [threading.Thread(target=work, args=(i,)) for i in range(2)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    assert not err, err
+    for i in range(2):
+        for la, sg, a, piv, info in out[i]:
+            check_against_oracle(mats[i], la, sg, a, piv, info)
