@@ -63,6 +63,8 @@ def parse_args():
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--nb", type=int, default=0)
     ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-plain", action="store_true",
+                    help="skip timing the plain (no look-ahead) path beside the headline")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
@@ -204,19 +206,20 @@ class ClockSampler:
 SIDE_STREAM_KERNELS = ("pivot_rows",)
 
 
-def kernel_table(prof: dict, steps: int, total_ms: float) -> dict:
+def kernel_table(prof: dict, steps: int, total_ms: float, concurrent_panel: bool = False) -> dict:
     """Per-kernel time from the library's event pairs (recorded on each launch's own
     stream).  Kernels on the critical stream get ms per step and their share of the
-    step.  A side-stream kernel (pivot_rows) runs beside the trailing update: its event
-    span includes the time it waits for multiprocessors the update holds, so it is
-    reported as a span only, with no share (its device time per launch is in the ncu
-    launch list)."""
+    step.  A side-stream kernel (pivot_rows; with the look-ahead also the panel) runs
+    beside the trailing update: its event span includes the time it waits for
+    multiprocessors the update holds, so it is reported as a span only, with no share
+    (its device time per launch is in the ncu launch list)."""
     out = {}
+    side = SIDE_STREAM_KERNELS + (("panel",) if concurrent_panel else ())
     for k, v in prof.items():
         if not v["launches"]:
             continue
         row = {"launches_per_step": v["launches"] / steps}
-        if k in SIDE_STREAM_KERNELS:
+        if k in side:
             row.update({"ms_per_step": None, "event_span_ms_per_step": v["ms"] / steps,
                         "share": None,
                         "note": "side stream, overlaps the trailing update; span, not "
@@ -987,7 +990,9 @@ def run_ours(args):
     t = torch.empty(n - 1, dtype=torch.float64, device=dev)
     piv = torch.empty(n, dtype=torch.int32, device=dev)
     info = torch.empty(1, dtype=torch.int32, device=dev)
-    ws = torch.empty(skew.workspace_bytes(n, nb, True), dtype=torch.uint8, device=dev)
+    lookahead = skew.lookahead_used(n, nb)
+    ws = torch.empty(skew.workspace_bytes(n, nb, True, lookahead=True), dtype=torch.uint8,
+                     device=dev)
     torch.cuda.synchronize()
 
     def step(A):
@@ -1035,11 +1040,48 @@ def run_ours(args):
     achieved = sk["flops"] / (sk["ms"] / 1e3) / 1e12 if sk["ms"] > 0 else None
     ratio = recorded_traffic()
     traffic = (ratio * sk["bytes"] / sk["launches"]) if (ratio and sk["launches"]) else None
-    kernels = kernel_table(prof, K, ms)
+    kernels = kernel_table(prof, K, ms, concurrent_panel=lookahead)
     panel = prof["panel"]
     kernels["panel"]["achieved_gbs"] = (panel["bytes"] / (panel["ms"] / 1e3) / 1e9
                                         if panel["ms"] > 0 else None)
     kernels["panel"]["us_per_column_step"] = panel["ms"] / K * 1e3 / max(n - 1, 1)
+    kernels["panel"]["path"] = ("look-ahead: beside the previous block's update, on its own "
+                                "stream (us per column step is its span)" if lookahead else
+                                "plain: between the updates, on the launch stream")
+
+    # ---- the same factorization on the plain path (no look-ahead), for comparison
+    plain = None
+    if lookahead and not args.skip_plain:
+        old_la = skew.set_lookahead(False)
+        try:
+            ws_p = torch.empty(skew.workspace_bytes(n, nb, True), dtype=torch.uint8, device=dev)
+            A_p = skew.fortran_empty(n, n, dev)
+            L_p = skew.fortran_empty(n, n, dev)
+            t_p = torch.empty_like(t)
+            piv_p = torch.empty_like(piv)
+            info_p = torch.empty_like(info)
+            pt = []
+            for i in range(3):
+                A_p.copy_(torch.from_numpy(A_host).to(dev))
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                skew.ltlt(A_p, nb=nb, stream=stream, L=L_p, t=t_p, piv=piv_p, info=info_p,
+                          workspace=ws_p)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if i:
+                    pt.append(e0.elapsed_time(e1))
+            plain_ms = statistics.median(pt)
+            same = bool(np.array_equal(piv_p.cpu().numpy(), piv_host))
+            plain = {"ms_per_step": plain_ms, "value": factorization_flops(n) / (plain_ms / 1e3) / 1e12,
+                     "unit": UNIT, "steps": len(pt), "pivots_equal_lookahead": same,
+                     "speedup_of_lookahead": plain_ms / (ms / K)}
+            del ws_p, A_p, L_p, t_p, piv_p, info_p
+            torch.cuda.empty_cache()
+        finally:
+            skew.set_lookahead(old_la)
 
     # ---- end to end through the host-buffer C-ABI call (pinned host buffers)
     e2e = None
@@ -1138,6 +1180,8 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": sk["bytes"] / max(sk["launches"], 1),
                          "algorithmic_flops_per_launch": sk["flops"] / max(sk["launches"], 1)},
             "kernels": kernels,
+            "lookahead": bool(lookahead),
+            "plain_path": plain,
             "e2e": e2e,
             "precision": precision,
             "pfaffian_only": twostep,

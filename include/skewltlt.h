@@ -161,6 +161,29 @@ int skew_get_batched_warp_tile(int n);
 size_t skew_workspace_bytes(int64_t n, int nb, int with_L);
 
 /*
+ * Workspace for the look-ahead path of skew_ltlt / skew_pfaffian (FP64 update, panel
+ * width 2 .. 64, n - 1 <= 128 x the multiprocessors of the device): the panel of each
+ * block runs on a second stream beside the trailing update of the block before it
+ * (Section 5.2's panel, left-looking over both blocks, with its exchanges deferred to
+ * the next update), which then reads and writes two matrix buffers: A and an n x n
+ * copy in this workspace.  A call given at least this many bytes (or no workspace)
+ * takes the look-ahead path; one given only skew_workspace_bytes takes the plain
+ * path.  Both give the same pivots and factors up to rounding.  Where the look-ahead
+ * does not apply this equals skew_workspace_bytes.  No counterpart in the paper (its
+ * blocked algorithm updates in place, Section 5.2).
+ */
+size_t skew_workspace_bytes_lookahead(int64_t n, int nb, int with_L);
+
+/* Turns the look-ahead path on (the default) or off for later calls of this process;
+ * returns the previous setting.  Off, every call takes the plain path. */
+int skew_set_lookahead(int on);
+
+/* 1 if skew_ltlt / skew_pfaffian_ex at order n, width nb (0 = default) and this
+ * trailing-update precision take the look-ahead path on the current device when given
+ * skew_workspace_bytes_lookahead bytes (or no workspace), else 0. */
+int skew_lookahead_used(int64_t n, int nb, int precision);
+
+/*
  * skew_ltlt -- pivoted blocked right-looking P A P^T = L T L^T
  * (Section 4.2, Variant 1; Section 5.2 pivoted blocked right-looking algorithm).
  *

@@ -43,6 +43,9 @@ SIGNATURES = {
     "skew_set_batched_tiles": ([_i32, _vp, _vp, _vp], _i32),
     "skew_get_batched_warp_tile": ([_i32], _i32),
     "skew_workspace_bytes": ([_i64, _i32, _i32], _sz),
+    "skew_workspace_bytes_lookahead": ([_i64, _i32, _i32], _sz),
+    "skew_set_lookahead": ([_i32], _i32),
+    "skew_lookahead_used": ([_i64, _i32, _i32], _i32),
     "skew_ltlt": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
     "skew_pfaffian": ([_i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
     "skew_pfaffian_from_factors": ([_i64, _vp, _vp, _vp, _vp, _vp], _i32),
@@ -225,8 +228,21 @@ def set_nb_table(table):
                                                          ctypes.cast(nbs, ctypes.c_void_p)))
 
 
-def workspace_bytes(n: int, nb: int = 0, with_L: bool = True) -> int:
-    return int(lib().skew_workspace_bytes(n, nb, 1 if with_L else 0))
+def workspace_bytes(n: int, nb: int = 0, with_L: bool = True, lookahead: bool = False) -> int:
+    """Workspace bytes of ltlt / pfaffian at order n and width nb; with `lookahead`, the
+    size that lets the call take the look-ahead path (see set_lookahead)."""
+    fn = lib().skew_workspace_bytes_lookahead if lookahead else lib().skew_workspace_bytes
+    return int(fn(n, nb, 1 if with_L else 0))
+
+
+def set_lookahead(on: bool) -> bool:
+    """Turn the look-ahead path of ltlt / pfaffian on or off; returns the old setting."""
+    return bool(lib().skew_set_lookahead(1 if on else 0))
+
+
+def lookahead_used(n: int, nb: int = 0, precision: int = 0) -> bool:
+    """Whether a call at order n, width nb takes the look-ahead path on this device."""
+    return bool(lib().skew_lookahead_used(n, nb, precision))
 
 
 def trim_memory():

@@ -211,12 +211,21 @@ def main():
     if os.path.exists(TABLE_PATH):
         with open(TABLE_PATH) as f:
             res = json.load(f)
+    for stale in ("batched_note", "command"):
+        res.pop(stale, None)
     if not args.batched_only:
         res.update(tune([int(x) for x in args.sizes.split(",")],
                         [int(x) for x in args.candidates.split(",")], args.reps))
         nat.set_nb_table(res["table"])
+        res["lookahead"] = {str(n): nat.lookahead_used(int(n), int(nb)) for n, nb in res["table"]}
     res.update(tune_batched(reps=args.reps))
     nat.set_batched_nb_table(res["batched_table"])
+    res["command"] = ("python -m paper_2411_09859_gb300.autotune "
+                      + ("--batched-only " if args.batched_only else
+                         f"--sizes {args.sizes} --candidates {args.candidates} ")
+                      + f"--reps {args.reps} (the smallest width within {TIE * 100:.1f} % "
+                      "of the fastest is kept; batched: widths over the mix's buckets with "
+                      "warp tile 32, then warp tiles with those widths)")
     if not args.no_save:
         save(res)
     print(json.dumps(res))

@@ -150,6 +150,42 @@ void side_release(int dev, const SideStream &s) {
     g_side_pool[dev].push_back(s);
 }
 
+// Streams of the look-ahead factorization: the panels on a stream of the highest
+// priority (so that their CTAs are placed as soon as the running trailing update leaves
+// room on a multiprocessor) and pivot_rows on another, with the events that order
+// them.  Pooled per device like the side streams.
+struct LaStreams {
+    cudaStream_t panel, rows;
+    cudaEvent_t fork, panel_done, upd_done[2], pjoin, rjoin;
+};
+std::vector<LaStreams> g_la_pool[kMaxDevices];
+
+int la_acquire(int dev, LaStreams *out) {
+    {
+        std::lock_guard<std::mutex> lock(g_dev_mutex);
+        if (!g_la_pool[dev].empty()) {
+            *out = g_la_pool[dev].back();
+            g_la_pool[dev].pop_back();
+            return SKEW_OK;
+        }
+    }
+    int lo = 0, hi = 0;
+    SKEW_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    SKEW_TRY(cudaStreamCreateWithPriority(&out->panel, cudaStreamNonBlocking, hi));
+    SKEW_TRY(cudaStreamCreateWithFlags(&out->rows, cudaStreamNonBlocking));
+    cudaEvent_t *evs[] = {&out->fork, &out->panel_done, &out->upd_done[0], &out->upd_done[1],
+                          &out->pjoin, &out->rjoin};
+    for (cudaEvent_t *e : evs) SKEW_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    return SKEW_OK;
+}
+
+void la_release(int dev, const LaStreams &s) {
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    g_la_pool[dev].push_back(s);
+}
+
+std::atomic<int> g_lookahead{1};
+
 // Library-private stream-ordered pool: freed blocks stay reserved for reuse (release
 // threshold = max), so repeated calls do not map and unmap device memory.
 int device_pool(int dev, cudaMemPool_t *out) {
@@ -238,8 +274,236 @@ WsLayout workspace_layout(int64_t n, int nb, bool with_L, int precision) {
     return w;
 }
 
+LaLayout workspace_layout_la(int64_t n, int nb, bool with_L) {
+    LaLayout l;
+    l.base = workspace_layout(n, nb, with_L, SKEW_PRECISION_FP64);
+    const size_t nn = (size_t)(n > 1 ? n : 1);
+    size_t off = l.base.total;
+    l.mat2 = off;
+    off += align256(nn * nn * sizeof(double));
+    l.maps = off;
+    off += 2 * align256(nn * sizeof(int32_t));
+    l.xs = off;
+    off += 2 * align256(nn * sizeof(double));
+    l.lbuf2 = off;
+    if (!with_L) off += align256(nn * (size_t)nb * sizeof(double));
+    l.total = off;
+    return l;
+}
+
+bool lookahead_applies(int64_t n, int nb, int precision, int sms) {
+    return g_lookahead.load() != 0 && precision == SKEW_PRECISION_FP64 && nb >= 2 &&
+           nb <= kLaMaxCols / 2 && n - 1 > nb && panel_la_fits(n, 0, sms);
+}
+
 // ------------------------------------------------------------------ the factorization
 namespace {
+
+// The blocked factorization with look-ahead: the panel of block j+1 runs on its own
+// stream beside the trailing update of block j.  It reads the state S_{j-1} before
+// that update (left-looking over blocks j and j+1, exchanges deferred, see
+// panel_la.cu); the update of block j reads S_{j-1} through block j's exchanges and
+// writes S_j into the other of two buffers (A and a workspace copy), so neither
+// writes what the other reads.  Order:
+//   panel j+1  after panel j (its stream) and update j-1 (S_{j-1} complete);
+//   update j   after update j-1 (the caller's stream) and panel j;
+//   pivot_rows of panel j (on L columns 1 .. k0_j)  after panel j and update j-1,
+//              which reads the L columns of block j-1.
+int factor_la(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
+              int32_t *piv, int32_t *info, double *logabs, int32_t *sign, int nb, char *base,
+              const LaLayout &lay, cudaStream_t st, bool with_L, const DeviceInfo &di) {
+    Ctrl *ctrl = reinterpret_cast<Ctrl *>(base + lay.base.ctrl);
+    ArgmaxPartial *part = reinterpret_cast<ArgmaxPartial *>(base + lay.base.partials);
+    if (t == nullptr) t = reinterpret_cast<double *>(base + lay.base.tbuf);
+    if (piv == nullptr) piv = reinterpret_cast<int32_t *>(base + lay.base.pivbuf);
+    double *B = reinterpret_cast<double *>(base + lay.mat2);
+    const size_t nn = (size_t)n;
+    int32_t *maps[2] = {reinterpret_cast<int32_t *>(base + lay.maps),
+                        reinterpret_cast<int32_t *>(base + lay.maps + align256(nn * sizeof(int32_t)))};
+    double *xs[2] = {reinterpret_cast<double *>(base + lay.xs),
+                     reinterpret_cast<double *>(base + lay.xs + align256(nn * sizeof(double)))};
+    double *lbuf[2] = {reinterpret_cast<double *>(base + lay.base.lbuf),
+                       reinterpret_cast<double *>(base + lay.lbuf2)};
+    // S_j lives in B for even j and in A for odd j; S_{-1} is A
+    auto sbuf = [&](int64_t j) -> double * { return (j >= 0 && (j & 1) == 0) ? B : A; };
+    auto sld = [&](int64_t j) -> int64_t { return (j >= 0 && (j & 1) == 0) ? (int64_t)n : lda; };
+    // L columns of the block starting at k0 (block index j)
+    auto lblock = [&](int64_t k0, int64_t j) -> double * {
+        return with_L ? L + (k0 + 1) * ldl : lbuf[j & 1];
+    };
+    const int64_t lld = with_L ? ldl : (int64_t)n;
+
+    LaStreams ls{};
+    SKEW_TRY_STATUS(la_acquire(di.device, &ls));
+    int status = SKEW_OK;
+    bool p_used = false, r_used = false;
+    do {
+        cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(part, 0, sizeof(ArgmaxPartial) * 2 * kMaxPanelGrid, st);
+        if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+        {
+            ProfScope ps(kProfPrologue, st, 0.0,
+                         8.0 * (double)n * (double)(n - 1) / 2.0 +
+                             (with_L ? 8.0 * (double)n * (double)n : 0.0));
+            status = launch_prologue(n, A, lda, with_L ? L : nullptr, ldl, piv, ctrl, st);
+        }
+        if (status != SKEW_OK) break;
+        e = cudaEventRecord(ls.fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ls.panel, ls.fork, 0);
+        if (e == cudaSuccess && with_L) e = cudaStreamWaitEvent(ls.rows, ls.fork, 0);
+        if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+        p_used = true;
+        r_used = with_L;
+
+        auto panel_prof = [&](int64_t kb, int64_t k0, int64_t kend, bool with_x, double &pf,
+                              double &pb) {
+            pf = 0.0;
+            pb = 0.0;
+            for (int64_t k = k0; k <= kend; ++k) {
+                if (k == kend && !with_x) break;
+                const double rows = (double)(n - k - 1);
+                pf += 2.0 * rows * (double)(k - kb);
+                pb += 8.0 * rows * 2.0;
+            }
+        };
+        // panel 0: the first block, from A itself
+        int64_t k0 = 0, kend = (nb < n - 1) ? nb : n - 1;
+        {
+            PanelLAArgs pa;
+            pa.S = A;
+            pa.lds = lda;
+            pa.map_prev = nullptr;
+            pa.xprev = nullptr;
+            pa.Lprev = nullptr;
+            pa.ldlp = lld;
+            pa.Lp = lblock(0, 0);
+            pa.ldl = lld;
+            pa.t = t;
+            pa.piv = piv;
+            pa.map_out = maps[0];
+            pa.xout = xs[0];
+            pa.ctrl = ctrl;
+            pa.part = part;
+            pa.n = (int)n;
+            pa.kb = 0;
+            pa.k0 = 0;
+            pa.kend = (int)kend;
+            pa.with_x = kend < n - 1 ? 1 : 0;
+            double pf, pb;
+            panel_prof(0, 0, kend, pa.with_x != 0, pf, pb);
+            ProfScope ps(kProfPanel, ls.panel, pf, pb);
+            status = launch_panel_la(pa, di.sms, ls.panel);
+        }
+        if (status != SKEW_OK) break;
+        e = cudaEventRecord(ls.panel_done, ls.panel);
+        if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+
+        for (int64_t j = 0;; ++j) {
+            const int64_t s = kend;                  // this block: k0 .. kend-1
+            const bool has_update = s < n - 1;
+            if (has_update) {
+                // ---- update j: S_j = (S_{j-1} through block j's exchanges) + pairs
+                e = cudaStreamWaitEvent(st, ls.panel_done, 0);
+                if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+                Skr2kArgs sa;
+                sa.m = n - s - 1;
+                double *dst = sbuf(j);
+                const int64_t ldd = sld(j);
+                sa.C = dst + (s + 1) + (s + 1) * ldd;
+                sa.ldc = ldd;
+                sa.Cin = sbuf(j - 1);
+                sa.ldcin = sld(j - 1);
+                sa.map = maps[j & 1] + (s + 1);
+                sa.alpha = 1.0;
+                sa.beta = 1.0;
+                sa.P = lblock(k0, j) + (s + 1);
+                sa.ldp = lld;
+                sa.Q = nullptr;
+                sa.ldq = 0;
+                sa.tt = t + k0 + 1;
+                sa.x = xs[j & 1] + (s + 1);
+                sa.b = kend - k0;
+                {
+                    ProfScope ps(kProfSkr2k, st, skr2k_flops(sa.m, sa.b / 2 + (sa.b & 1)),
+                                 skr2k_bytes(sa.m));
+                    status = launch_skr2k(PairKind::Fused, sa, st);
+                }
+                if (status != SKEW_OK) break;
+                e = cudaEventRecord(ls.upd_done[j & 1], st);
+                if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+            }
+            // ---- pivot_rows of panel j on L columns 1 .. k0
+            if (with_L && k0 >= 1) {
+                e = cudaStreamWaitEvent(ls.rows, ls.panel_done, 0);
+                if (e == cudaSuccess && j >= 1)
+                    e = cudaStreamWaitEvent(ls.rows, ls.upd_done[(j - 1) & 1], 0);
+                if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+                ProfScope ps(kProfPivotRows, ls.rows, 0.0,
+                             4.0 * 8.0 * (double)k0 * (double)(kend - k0));
+                status = launch_pivot_rows(n, L, ldl, piv, (int)k0, (int)kend, ls.rows);
+                if (status != SKEW_OK) break;
+            }
+            if (!has_update) break;
+            // ---- panel j+1, beside update j: reads S_{j-1}
+            const int64_t k0n = kend, kendn = (kend + nb < n - 1) ? kend + nb : n - 1;
+            if (j >= 1) {
+                e = cudaStreamWaitEvent(ls.panel, ls.upd_done[(j - 1) & 1], 0);
+                if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+            }
+            PanelLAArgs pa;
+            pa.S = sbuf(j - 1);
+            pa.lds = sld(j - 1);
+            pa.map_prev = maps[j & 1];
+            pa.xprev = xs[j & 1];
+            pa.Lprev = lblock(k0, j);
+            pa.ldlp = lld;
+            pa.Lp = lblock(k0n, j + 1);
+            pa.ldl = lld;
+            pa.t = t;
+            pa.piv = piv;
+            pa.map_out = maps[(j + 1) & 1];
+            pa.xout = xs[(j + 1) & 1];
+            pa.ctrl = ctrl;
+            pa.part = part;
+            pa.n = (int)n;
+            pa.kb = (int)k0;
+            pa.k0 = (int)k0n;
+            pa.kend = (int)kendn;
+            pa.with_x = kendn < n - 1 ? 1 : 0;
+            {
+                double pf, pb;
+                panel_prof(k0, k0n, kendn, pa.with_x != 0, pf, pb);
+                ProfScope ps(kProfPanel, ls.panel, pf, pb);
+                status = launch_panel_la(pa, di.sms, ls.panel);
+            }
+            if (status != SKEW_OK) break;
+            e = cudaEventRecord(ls.panel_done, ls.panel);
+            if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+            k0 = k0n;
+            kend = kendn;
+        }
+        if (status != SKEW_OK) break;
+    } while (0);
+
+    // join: the caller's stream waits for the last panel and the last pivot_rows
+    if (p_used) {
+        cudaError_t e = cudaEventRecord(ls.pjoin, ls.panel);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ls.pjoin, 0);
+        if (e != cudaSuccess && status == SKEW_OK) { set_last_error(e); status = SKEW_ERR_CUDA; }
+    }
+    if (r_used) {
+        cudaError_t e = cudaEventRecord(ls.rjoin, ls.rows);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ls.rjoin, 0);
+        if (e != cudaSuccess && status == SKEW_OK) { set_last_error(e); status = SKEW_ERR_CUDA; }
+    }
+    if (status == SKEW_OK) {
+        ProfScope ps(kProfFinish, st, 0.0, 12.0 * (double)n);
+        status = launch_finish(n, t, piv, ctrl, logabs, sign, info, st);
+    }
+    la_release(di.device, ls);
+    return status;
+}
 
 int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
            int32_t *piv, int32_t *info, double *logabs, int32_t *sign, int nb,
@@ -248,6 +512,28 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
     DeviceInfo di;
     SKEW_TRY_STATUS(current_device_info(&di));
     if (nb == 0) nb = skew_default_nb(n);
+    if (lookahead_applies(n, nb, precision, di.sms)) {
+        const LaLayout llay = workspace_layout_la(n, nb, with_L);
+        char *lb = static_cast<char *>(workspace);
+        if (lb == nullptr || workspace_bytes >= llay.total) {
+            bool lown = false;
+            if (lb == nullptr) {
+                SKEW_TRY_STATUS(pool_alloc(reinterpret_cast<void **>(&lb), llay.total, st));
+                lown = true;
+            }
+            int rc = factor_la(n, A, lda, L, ldl, t, piv, info, logabs, sign, nb, lb, llay, st,
+                               with_L, di);
+            if (lown) {
+                cudaError_t e = cudaFreeAsync(lb, st);
+                if (e != cudaSuccess && rc == SKEW_OK) {
+                    set_last_error(e);
+                    rc = SKEW_ERR_CUDA;
+                }
+            }
+            return rc;
+        }
+        // a caller's workspace sized for the plain path: factor without look-ahead
+    }
     const WsLayout lay = workspace_layout(n, nb, with_L, precision);
     char *base = static_cast<char *>(workspace);
     bool own = false;
@@ -626,6 +912,27 @@ size_t skew_workspace_bytes(int64_t n, int nb, int with_L) {
     if (nb <= 0) nb = skew_default_nb(n);
     if (nb > kMaxNb) nb = kMaxNb;
     return workspace_layout(n, nb, with_L != 0).total;
+}
+
+size_t skew_workspace_bytes_lookahead(int64_t n, int nb, int with_L) {
+    if (n < 0) return 0;
+    if (nb <= 0) nb = skew_default_nb(n);
+    if (nb > kMaxNb) nb = kMaxNb;
+    if (nb > kLaMaxCols / 2 || n >= 65535) return workspace_layout(n, nb, with_L != 0).total;
+    return workspace_layout_la(n, nb, with_L != 0).total;
+}
+
+int skew_lookahead_used(int64_t n, int nb, int precision) {
+    DeviceInfo di;
+    if (current_device_info(&di) != SKEW_OK) return 0;
+    if (nb <= 0) nb = skew_default_nb(n);
+    return lookahead_applies(n, nb, precision, di.sms) ? 1 : 0;
+}
+
+int skew_set_lookahead(int on) {
+    const int old = g_lookahead.load();
+    g_lookahead.store(on != 0 ? 1 : 0);
+    return old;
 }
 
 int skew_profile_enable(int on) {

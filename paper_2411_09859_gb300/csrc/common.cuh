@@ -55,6 +55,8 @@ struct Ctrl {
     double vtop[2];           // panel: v[k+1] of step k (slot k & 1), before the exchange
     double pad1[4];
     double rowp[2][kMaxNb];   // panel: L[k+1, k0+1..k] of step k (slot k & 1)
+    int physp[2][4];          // look-ahead panel: source index and panel-start position
+                              // of row k+1 of step k (slot k & 1)
     double vnext[2];          // two-step panel: v[k+2] of pair step j (slot j & 1)
     double rowq[2][kMaxNb];   // two-step panel: stored row k+2 of pair step j (slot j & 1)
 };
@@ -66,6 +68,7 @@ struct __align__(16) ArgmaxPartial {
     int idx;                  // that row (INT32_MAX if none)
     unsigned int tag;         // shared-memory panels: step tag; val, idx, tag are written
                               // and read together as one 128-bit access
+    int aux[4];               // look-ahead panel: aux[0] = panel-start position of idx
     double row[kMaxNb];       // L[idx, k0+1 .. k]
 };
 constexpr int64_t kMaxOrder = int64_t(1) << 22;   // keeps every tile count below 2^31
@@ -75,6 +78,16 @@ struct WsLayout {
     size_t ctrl, partials, tbuf, pivbuf, lbuf, split, total;
 };
 WsLayout workspace_layout(int64_t n, int nb, bool with_L, int precision = 0);
+// The look-ahead factorization's workspace: the plain layout, then a second n x n
+// matrix (ld n), two position maps (n int32 each), two updated columns (n doubles
+// each) and, without L, a second panel buffer (n x nb).
+struct LaLayout {
+    WsLayout base;
+    size_t mat2, maps, xs, lbuf2, total;
+};
+LaLayout workspace_layout_la(int64_t n, int nb, bool with_L);
+// Whether skew_ltlt / skew_pfaffian take the look-ahead path for this order and width.
+bool lookahead_applies(int64_t n, int nb, int precision, int sms);
 
 // ------------------------------------------------------------------ device helpers
 __device__ __forceinline__ uint64_t global_ns() {
@@ -200,6 +213,41 @@ inline int64_t panel_grid(int64_t rows, int sms) {
 }
 int panel_max_blocks_per_sm(int *out);
 
+// Look-ahead panel (panel_la.cu): the same steps k = k0 .. kend-1 as launch_panel, but
+// run beside the trailing update of the previous panel.  It reads the unfactored block
+// from S, the state BEFORE that update (left-looking over the previous panel's L
+// columns kb+1 .. k0 as well as its own), never writes S, and defers its exchanges:
+// position i of the current order is row/column idx(i) of S, where idx starts as
+// map_prev (the previous panel's exchanges; nullptr: identity) and follows this
+// panel's exchanges.  Outputs: L columns k0+1 .. kend (rows by position), t, piv,
+// map_out[i] (i > k0: the position at this panel's start of what is now at i), and,
+// with `with_x`, the updated column kend in xout (positions kend+1 .. n-1).
+struct PanelLAArgs {
+    const double *S;          // source state, lds x n, strictly lower triangle read
+    int64_t lds;
+    const int32_t *map_prev;  // n entries or nullptr
+    const double *xprev;      // updated column k0 by position (k0+1 .. n-1), or nullptr:
+                              // column k0 is read from S
+    const double *Lprev;      // L columns kb+1 .. k0 (k0 - kb <= 64 of them), by position
+    int64_t ldlp;
+    double *Lp;               // L columns k0+1 .. kend
+    int64_t ldl;
+    double *t;
+    int32_t *piv;
+    int32_t *map_out;
+    double *xout;
+    Ctrl *ctrl;
+    ArgmaxPartial *part;
+    int n, kb, k0, kend, with_x;
+};
+constexpr int kLaThreads = 128;   // one row per thread
+constexpr int kLaMaxCols = 128;   // (k0 - kb) + (kend - k0) L columns in shared memory
+// Whether the rows of a look-ahead panel at k0 fit one per thread on `sms` CTAs.
+inline bool panel_la_fits(int64_t n, int64_t k0, int sms) {
+    return n - k0 - 1 <= (int64_t)sms * kLaThreads && n < 65535;
+}
+int launch_panel_la(const PanelLAArgs &a, int sms, cudaStream_t stream);
+
 // Row exchanges piv[k+1] <-> k+1, k = k0 .. kend-1 in order, on L columns 1 .. k0.
 int launch_pivot_rows(int64_t n, double *L, int64_t ldl, const int32_t *piv, int k0,
                       int kend, cudaStream_t stream);
@@ -210,6 +258,12 @@ struct Skr2kArgs {
     int64_t m;             // order of the updated skew block C
     double *C;
     int64_t ldc;
+    // Out of place (Cin != nullptr): the old C is read from the skew matrix Cin
+    // (ldcin), entry (i, j) of C being entry (map[i], map[j]) of Cin (lower storage,
+    // negated when map[i] < map[j]); C is only written.
+    const double *Cin = nullptr;
+    int64_t ldcin = 0;
+    const int32_t *map = nullptr;
     double alpha, beta;    // C := beta C + alpha * sum_p (a_p w_p^T - w_p a_p^T)
     const double *P;       // Rank2k: the a columns; Tridiag/Fused: the A columns
     int64_t ldp;

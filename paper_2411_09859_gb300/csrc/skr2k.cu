@@ -20,6 +20,10 @@
 //             Tridiag with x added to w_{b-1} when b is even (l = a_{b-1} is then
 //             already a pair), or the extra pair (a_{b-1}, x) when b is odd.
 //
+// Out of place (Cin != nullptr, the look-ahead factorization): the old C is read from
+// another buffer through a map of rows/columns (the panel's deferred exchanges) and C
+// is only written; the update is otherwise the same.
+//
 // W is never stored: each CTA forms the pair columns of its row block while it
 // stages them into shared memory (the GPU counterpart of forming T A^T while
 // packing, Section 4.3).  FP64 throughput on this part is what bounds the kernel
@@ -58,7 +62,7 @@ __device__ __forceinline__ void tri_tile(int64_t idx, int64_t &bi, int64_t &bj) 
 template <PairKind KIND>
 __global__ void __launch_bounds__(kThreads, 2)
 skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
-             PairSource<KIND> src) {
+             PairSource<KIND> src, const double *Cin, int64_t ldcin, const int32_t *map) {
     __shared__ double Us[BM][LDS];
     __shared__ double Vs[BM][LDS];
 
@@ -115,18 +119,38 @@ skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
     }
 
     // ---- epilogue: strictly lower entries inside the block.  All C loads of a row
-    // block are issued before its stores, so their latencies overlap.
+    // block are issued before its stores, so their latencies overlap.  Out of place,
+    // the old entry (gi, gj) is entry (map[gi], map[gj]) of the skew matrix Cin.
+    int cmap[4][2];
+    if (Cin != nullptr) {
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int64_t gj = J0 + wn * 32 + ni * 8 + 2 * tg + c;
+                cmap[ni][c] = gj < m ? __ldg(map + gj) : 0;
+            }
+    }
 #pragma unroll
     for (int mi = 0; mi < 4; ++mi) {
         const int64_t gi = I0 + wm * 32 + mi * 8 + g;
         double cv[4][2];
+        const int rmap = (Cin != nullptr && gi < m) ? __ldg(map + gi) : 0;
 #pragma unroll
         for (int ni = 0; ni < 4; ++ni)
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 const int64_t gj = J0 + wn * 32 + ni * 8 + 2 * tg + c;
                 const bool in = gi < m && gj < m && gi > gj && beta != 0.0;
-                cv[ni][c] = in ? C[gi + gj * ldc] : 0.0;
+                if (!in) {
+                    cv[ni][c] = 0.0;
+                } else if (Cin == nullptr) {
+                    cv[ni][c] = C[gi + gj * ldc];
+                } else {
+                    const int a = rmap, b = cmap[ni][c];
+                    cv[ni][c] = a > b ? __ldg(Cin + a + (int64_t)b * ldcin)
+                                      : -__ldg(Cin + b + (int64_t)a * ldcin);
+                }
             }
 #pragma unroll
         for (int ni = 0; ni < 4; ++ni) {
@@ -151,7 +175,8 @@ int launch_kind(const Skr2kArgs &a, cudaStream_t stream) {
     if (tiles > INT_MAX) return SKEW_ERR_CUDA;      // unreachable: orders are capped
     PairSource<KIND> src{a.P, a.ldp, a.Q, a.ldq, a.tt, a.x, a.b};
     skr2k_kernel<KIND><<<(unsigned)tiles, kThreads, 0, stream>>>(a.m, a.C, a.ldc, a.alpha,
-                                                                  a.beta, src);
+                                                                  a.beta, src, a.Cin, a.ldcin,
+                                                                  a.map);
     note_launches(1);
     return check_launch();
 }

@@ -299,6 +299,121 @@ def ltlt_blocked_delayed(A: np.ndarray, nb: int):
     return L, t, piv
 
 
+def ltlt_lookahead(A: np.ndarray, nb: int):
+    """The data flow of the look-ahead factorization, restated in numpy: the panel of
+    block j+1 is formed from S_{j-1}, the state BEFORE block j's trailing update,
+    left-looking over the L columns of blocks j and j+1 (h = T L[k, :]^T over columns
+    kb+1 .. k with kb = block j's first column); it never writes S: its exchanges only
+    update a map from positions to rows/columns of S (starting from block j's map), and
+    the trailing update of block j+1 reads S_j through that map and writes S_{j+1} to
+    another buffer.  Block j's L rows are exchanged in the panel's working copy only;
+    pivot_rows applies each panel's exchanges to the earlier L columns after the update
+    that reads them.  Returns ``(L, t, piv)``; must equal the oracle's factorization."""
+    n = A.shape[0]
+    src0 = full_skew_from_lower(np.asarray(A, dtype=np.float64))
+    L = np.eye(n)
+    t = np.zeros(max(n - 1, 0))
+    piv = np.arange(n)
+    if n < 2:
+        return L, t, piv
+
+    def panel(S, map_prev, xprev, kb, k0, kend, with_x):
+        rows = np.arange(k0 + 1, n)
+        phs = np.array(map_prev[k0 + 1:], copy=True)          # source index by position
+        pho = np.arange(k0 + 1, n)                            # panel-start position
+        # working copy of L columns kb+1 .. kend for rows k0+1 .. n-1 (by position)
+        W = np.zeros((n, kend - kb))
+        W[k0 + 1:, :k0 - kb] = L[k0 + 1:, kb + 1:k0 + 1]
+        v = np.zeros(n)
+        if xprev is not None:
+            v[k0 + 1:] = xprev[k0 + 1:]
+        else:
+            v[k0 + 1:] = S[phs, map_prev[k0]]
+        xout = None
+        for k in range(k0, kend):
+            p = k + 1
+            r = p + int(np.argmax(np.abs(v[p:])))
+            tau = v[r]
+            t[k] = tau
+            piv[p] = r
+            if r != p:
+                for arr in (v,):
+                    arr[[p, r]] = arr[[r, p]]
+                W[[p, r], :] = W[[r, p], :]
+                a, b = p - (k0 + 1), r - (k0 + 1)
+                phs[[a, b]] = phs[[b, a]]
+                pho[[a, b]] = pho[[b, a]]
+                L[[p, r], k0 + 1:k + 1] = L[[r, p], k0 + 1:k + 1]
+            c = k + 1 - kb - 1                                # W column of L column k+1
+            W[p, c] = 1.0
+            W[p + 1:, c] = v[p + 1:] / tau if tau != 0.0 else 0.0
+            L[p:, k + 1] = W[p:, c]
+            if k + 1 < kend or with_x:
+                h = np.zeros(k + 1 - kb)
+                for q in range(kb + 1, k + 2):
+                    val = 0.0
+                    if q - 1 >= kb + 1:
+                        tq1 = t[q - 1]
+                        val += tq1 * W[p, q - 1 - kb - 1]
+                    if q + 1 <= k + 1:
+                        lq1 = 1.0 if q + 1 == k + 1 else W[p, q + 1 - kb - 1]
+                        val -= t[q] * lq1
+                    h[q - kb - 1] = val
+                idx = phs[p + 1 - (k0 + 1):]
+                xnew = S[idx, phs[p - (k0 + 1)]]
+                vn = xnew - W[p + 1:, :k + 1 - kb] @ h
+                v[:] = 0.0
+                v[p + 1:] = vn
+                if k + 1 == kend:
+                    xout = np.zeros(n)
+                    xout[p + 1:] = vn
+        map_out = np.arange(n)
+        map_out[k0 + 1:] = pho
+        return map_out, xout
+
+    def update(S_in, map_j, k0, kend, x):
+        s = kend
+        S_out = np.zeros_like(S_in)
+        idx = map_j[s + 1:]
+        C = S_in[np.ix_(idx, idx)]
+        Ap = L[s + 1:, k0 + 1:kend + 1]
+        Tp = tridiag_from_t(t[k0 + 1:kend], Ap.shape[1])
+        l = L[s + 1:, kend]
+        xv = x[s + 1:]
+        C = C - Ap @ Tp @ Ap.T + (np.outer(l, xv) - np.outer(xv, l))
+        S_out[s + 1:, s + 1:] = C
+        return S_out
+
+    def pivot_rows(k0, kend):
+        for k in range(k0, kend):
+            r = piv[k + 1]
+            if r != k + 1:
+                L[[k + 1, r], 1:k0 + 1] = L[[r, k + 1], 1:k0 + 1]
+
+    ident = np.arange(n)
+    k0, kend = 0, min(nb, n - 1)
+    maps, xs = {}, {}
+    maps[0], xs[0] = panel(src0, ident, None, 0, 0, kend, kend < n - 1)
+    states = {-1: src0}
+    blocks = {0: (0, kend)}
+    j = 0
+    while True:
+        k0, kend = blocks[j]
+        s = kend
+        if j >= 1:
+            pivot_rows(k0, kend)          # after panel j and update j-1
+        if s >= n - 1:
+            break
+        k0n, kendn = kend, min(kend + nb, n - 1)
+        blocks[j + 1] = (k0n, kendn)
+        # panel j+1 beside update j: both read S_{j-1}
+        maps[j + 1], xs[j + 1] = panel(states[j - 1], maps[j][np.arange(n)] if j >= 0 else ident,
+                                       xs[j], k0, k0n, kendn, kendn < n - 1)
+        states[j] = update(states[j - 1], maps[j], k0, kend, xs[j])
+        j += 1
+    return L, t, piv
+
+
 def twostep_blocked(A, nb):
     """Blocked left-looking restatement of the two-step (Pfaffian-only) elimination,
     in the order the GPU path takes it.  Returns ``(a, piv)``.

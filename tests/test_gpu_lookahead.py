@@ -1,0 +1,141 @@
+"""The look-ahead path of skew_ltlt / skew_pfaffian against the oracle and against the
+plain path.
+
+With the look-ahead (the default where it applies: FP64 update, panel width 2 .. 64,
+n - 1 <= 128 x the multiprocessors), the panel of each block runs beside the trailing
+update of the block before it, reading the state before that update and deferring its
+exchanges to the next (out-of-place) update.  Both paths factor the same matrix to the
+oracle's factorization: pivots identical, factors within the parity bars of
+test_gpu_parity.  Off (skew_set_lookahead(0)) or with a workspace of only
+skew_workspace_bytes, the plain path runs.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import oracle  # noqa: E402
+import paper_2411_09859_gb300 as skew  # noqa: E402
+from paper_2411_09859_gb300 import inputs  # noqa: E402
+from skewcheck import EPS, backward_error, check_structure  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL_C = 2000.0
+
+
+def dev(A):
+    return torch.from_numpy(np.asfortranarray(A, dtype=np.float64)).cuda()
+
+
+def factor(A, nb, lookahead, workspace=None, with_L=True):
+    old = skew.set_lookahead(lookahead)
+    try:
+        if with_L:
+            L, t, piv, info = skew.ltlt(dev(A), nb=nb, workspace=workspace)
+            torch.cuda.synchronize()
+            return L.cpu().numpy(), t.cpu().numpy(), piv.cpu().numpy(), int(info.item())
+        la, sg, t, piv, info = skew.pfaffian(dev(A), nb=nb, workspace=workspace)
+        torch.cuda.synchronize()
+        return (float(la.item()), int(sg.item())), t.cpu().numpy(), piv.cpu().numpy(), \
+            int(info.item())
+    finally:
+        skew.set_lookahead(old)
+
+
+def check(A, L, t, piv, info):
+    n = A.shape[0]
+    L0, t0, p0, i0 = oracle.ltlt(A)
+    assert np.array_equal(piv, p0), np.nonzero(piv != p0)[0][:5]
+    assert info == i0
+    tol = TOL_C * n * EPS
+    if n > 1:
+        assert np.max(np.abs(t - t0)) <= tol * max(1.0, np.max(np.abs(t0)))
+        if L is not None:
+            assert np.max(np.abs(L - L0)) <= tol
+    if L is not None:
+        check_structure(L, t, piv, n)
+        if n <= 1500:
+            assert backward_error(A, L, t, piv) <= 10
+
+
+@pytest.mark.parametrize("n,nb", [(4, 2), (9, 3), (33, 8), (100, 16), (129, 64), (300, 7),
+                                  (513, 32), (1000, 64), (1031, 48), (2050, 64)])
+def test_lookahead_and_plain_match_the_oracle(n, nb):
+    A = inputs.skew_gaussian(n, 12000 + n)
+    for lookahead in (True, False):
+        check(A, *factor(A, nb, lookahead))
+
+
+@pytest.mark.parametrize("n,nb", [(300, 32), (1001, 64)])
+def test_lookahead_pfaffian_only(n, nb):
+    """skew_pfaffian (no L: two panel buffers in the workspace) takes the look-ahead
+    too; its pivots, t and log|Pf| equal the oracle's."""
+    A = inputs.skew_gaussian(n, 12500 + n)
+    (la, sg), t, piv, info = factor(A, nb, True, with_L=False)
+    check(A, None, t, piv, info)
+    L0, t0, p0, _ = oracle.ltlt(A)
+    la0, sg0 = oracle.pfaffian_from_factors(n, t0, p0)
+    assert sg == sg0 and abs(la - la0) <= 1e-10 * max(1.0, abs(la0))
+
+
+def test_workspace_size_selects_the_path():
+    """A caller's workspace of skew_workspace_bytes takes the plain path, one of
+    skew_workspace_bytes_lookahead the look-ahead; both reach the oracle."""
+    n, nb = 700, 32
+    A = inputs.skew_gaussian(n, 12701)
+    plain = skew.workspace_bytes(n, nb, True)
+    la = skew.workspace_bytes(n, nb, True, lookahead=True)
+    assert la >= plain + 8 * n * n
+    for size in (plain, la):
+        ws = torch.empty(size, dtype=torch.uint8, device="cuda")
+        check(A, *factor(A, nb, True, workspace=ws))
+
+
+def test_lookahead_block_diagonal_zero_pivots_and_ties():
+    """Zero pivot columns (t = 0 at odd steps) and exact ties in the pivot search take
+    the same path through the deferred exchanges as through the plain ones."""
+    s = np.arange(1.0, 41.0)
+    D = inputs.block_diag_skew(s)
+    P = np.random.default_rng(3).permutation(80)
+    A = np.asfortranarray(D[np.ix_(P, P)])
+    for nb in (2, 8, 16):
+        L, t, piv, info = factor(A, nb, True)
+        check(A, L, t, piv, info)
+    B = np.asfortranarray(np.tril(np.ones((90, 90)), -1) - np.triu(np.ones((90, 90)), 1))
+    for nb in (4, 32):
+        check(B, *factor(B, nb, True))
+
+
+def test_lookahead_graph_capture_replays_equal():
+    """A whole look-ahead factorization (its two extra streams forked from and joined
+    to the capturing stream) captured in a CUDA graph and replayed gives the direct
+    call's results bitwise."""
+    n, nb = 600, 32
+    A = inputs.skew_gaussian(n, 12801)
+    Ad = dev(A)
+    work = skew.fortran_empty(n, n, "cuda")
+    L = skew.fortran_empty(n, n, "cuda")
+    t = torch.empty(n - 1, dtype=torch.float64, device="cuda")
+    piv = torch.empty(n, dtype=torch.int32, device="cuda")
+    info = torch.empty(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(skew.workspace_bytes(n, nb, True, lookahead=True), dtype=torch.uint8,
+                     device="cuda")
+    s = torch.cuda.Stream()
+    work.copy_(Ad)
+    torch.cuda.synchronize()
+    skew.ltlt(work, nb=nb, stream=s, L=L, t=t, piv=piv, info=info, workspace=ws)
+    torch.cuda.synchronize()
+    ref = (L.clone(), t.clone(), piv.clone())
+    g = torch.cuda.CUDAGraph()
+    work.copy_(Ad)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        skew.ltlt(work, nb=nb, stream=s, L=L, t=t, piv=piv, info=info, workspace=ws)
+    for _ in range(2):
+        work.copy_(Ad)
+        L.zero_()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(L, ref[0]) and torch.equal(t, ref[1]) and torch.equal(piv, ref[2])
+    check(A, ref[0].cpu().numpy(), ref[1].cpu().numpy(), ref[2].cpu().numpy(), int(info.item()))

@@ -13,13 +13,13 @@ split-precision path (bf16 digit slices on the tensor cores for the trailing upd
   - pivots identical (integer work, bit-exact);
   - log|Pf| within 1e-10 * max(1, |log|Pf||) and the same sign;
   - t and L element by element within TOL_C * n * eps (|L| <= 1; t relative to max|t|),
-    the bar of the smaller parity tests, for every case but one: the split path on the
-    precision workload.  There the digit slices of a row are aligned to the row's
-    largest entry, so an entry 1e6 below it keeps about 20 fewer bits than in FP64, and
-    the L entries of this condition-1e6 matrix differ from the oracle's by more than
-    that bar; the split path is held there to the backward error instead;
+    the bar of the smaller parity tests;
   - the backward error ||P A P^T - L T L^T||_F / (n eps ||A||_F) <= 10 (host BLAS,
-    by column blocks) for the split path and for the precision workload.
+    by column blocks) for the split path and for the precision workload.  (The split
+    path's digit slices are aligned to each row's largest entry; its pairs are first
+    balanced by powers of two so that the large T entries of this condition-1e6 matrix
+    do not raise those maxima: without that step its L entries differed from the
+    oracle's by 4e-5 and its backward error was 33.)
 The measured differences are printed (pytest -s) so that the error of each result
 against the oracle is on record.
 """
@@ -160,7 +160,6 @@ def test_precision_workload_n16384_oracle_and_closed_form():
     # per factor, far inside 1e-7 relative
     assert abs(la0 - closed) <= 1e-7 * closed
     for precision in (skew.PRECISION_FP64, SPLIT):
-        la1, sg1 = compare_with_oracle("qdq16384", precision,
-                                       elementwise=(precision != SPLIT), backward=True)
+        la1, sg1 = compare_with_oracle("qdq16384", precision, backward=True)
         assert sg1 == 1
         assert abs(la1 - closed) <= 1e-7 * closed

@@ -141,8 +141,12 @@ def test_twostep_from_two_host_threads():
             s = torch.cuda.Stream()
             res = []
             for _ in range(3):
-                la, sg, a, piv, info = skew.pfaffian_twostep(dev(mats[i]), nb=96, stream=s)
+                # the input stays referenced until the stream is done with it: torch's
+                # caching allocator would otherwise hand its memory to the other thread
+                Ad = dev(mats[i])
+                la, sg, a, piv, info = skew.pfaffian_twostep(Ad, nb=96, stream=s)
                 s.synchronize()
+                del Ad
                 res.append((float(la.item()), int(sg.item()), a.cpu().numpy(),
                             piv.cpu().numpy(), int(info.item())))
             out[i] = res

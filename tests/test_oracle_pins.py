@@ -338,3 +338,23 @@ def test_oracle_in_pieces_and_batched_equal_single_calls(orc):
         assert i1 == i0 and s1 == s0
         assert np.array_equal(t1, t0) and np.array_equal(p1, p0)
         assert l1 == l0 or (math.isinf(l1) and math.isinf(l0))
+
+
+@pytest.mark.parametrize("n,nb", [(5, 2), (17, 4), (40, 8), (100, 16), (131, 32), (64, 64),
+                                  (200, 10), (97, 3)])
+def test_lookahead_data_flow_reaches_the_oracle(orc, n, nb):
+    """The look-ahead factorization's data flow (panel of block j+1 formed from the
+    state before block j's update, left-looking over both blocks, its exchanges kept
+    as a map and applied by the next out-of-place update), restated in numpy, reaches
+    the oracle's factorization: identical pivots, factors equal up to rounding."""
+    from skewcheck import ltlt_lookahead
+    A = inputs.skew_gaussian(n, 300 + n)
+    L0, t0, p0, _ = orc.ltlt(A)
+    L, t, p = ltlt_lookahead(A, nb)
+    assert np.array_equal(p, p0)
+    assert np.max(np.abs(L - L0)) <= 1e-12
+    assert np.max(np.abs(t - t0)) <= 1e-12 * np.max(np.abs(t0))
+    D = inputs.block_diag_skew([2.0, 3.0, 5.0, 7.0])       # zero pivots at odd steps
+    L1, t1, p1 = ltlt_lookahead(D, 2)
+    L2, t2, p2, _ = orc.ltlt(D)
+    assert np.array_equal(p1, p2) and np.array_equal(t1, t2)
