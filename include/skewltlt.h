@@ -130,6 +130,12 @@ int skew_default_nb(int64_t n);
  * Section 5.2); here it only chooses the default of `nb = 0`.  Thread safe.
  * Returns 0, or -1 / -2 / -3 for a bad count / n_upper / nb. */
 int skew_set_nb_table(int count, const int64_t *n_upper, const int32_t *nb);
+/* The same with, per entry, lookahead[i] = 1 / 0 / -1: that order range takes the
+ * look-ahead path / the plain path / the built-in choice (see skew_set_lookahead);
+ * lookahead may be NULL (all -1).  Returns as skew_set_nb_table, or -4 for a bad
+ * lookahead entry. */
+int skew_set_nb_table_ex(int count, const int64_t *n_upper, const int32_t *nb,
+                         const int32_t *lookahead);
 
 /* Panel width (8, 16 or 32) of the CTA-local batched kernels (skew_ltlt_batched for
  * orders <= 512, skew_pfaffian_batched) per order bucket: a matrix of order
@@ -174,9 +180,14 @@ size_t skew_workspace_bytes(int64_t n, int nb, int with_L);
  */
 size_t skew_workspace_bytes_lookahead(int64_t n, int nb, int with_L);
 
-/* Turns the look-ahead path on (the default) or off for later calls of this process;
- * returns the previous setting.  Off, every call takes the plain path. */
-int skew_set_lookahead(int on);
+/* Chooses the path of later calls of this process; returns the previous setting.
+ *   0  plain path always;
+ *   1  (the default) the look-ahead where the panel-width table says so for the order
+ *      (skew_set_nb_table_ex), else for 3072 <= n <= 10240;
+ *   2  the look-ahead wherever it applies;
+ *   32, 64  as 2, with that many rows per CTA in the look-ahead panel instead of 128
+ *      (a tuning knob). */
+int skew_set_lookahead(int mode);
 
 /* 1 if skew_ltlt / skew_pfaffian_ex at order n, width nb (0 = default) and this
  * trailing-update precision take the look-ahead path on the current device when given

@@ -45,6 +45,7 @@ SIGNATURES = {
     "skew_workspace_bytes": ([_i64, _i32, _i32], _sz),
     "skew_workspace_bytes_lookahead": ([_i64, _i32, _i32], _sz),
     "skew_set_lookahead": ([_i32], _i32),
+    "skew_set_nb_table_ex": ([_i32, _vp, _vp, _vp], _i32),
     "skew_lookahead_used": ([_i64, _i32, _i32], _i32),
     "skew_ltlt": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
     "skew_pfaffian": ([_i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
@@ -120,9 +121,11 @@ def _install_saved_nb_table(L):
     with open(path) as f:
         saved = json.load(f)
     table = saved.get("table", [])
-    nu = (ctypes.c_int64 * max(len(table), 1))(*[int(a) for a, _ in table])
-    nbs = (ctypes.c_int32 * max(len(table), 1))(*[int(b) for _, b in table])
-    L.skew_set_nb_table(len(table), ctypes.cast(nu, ctypes.c_void_p), ctypes.cast(nbs, ctypes.c_void_p))
+    nu = (ctypes.c_int64 * max(len(table), 1))(*[int(e[0]) for e in table])
+    nbs = (ctypes.c_int32 * max(len(table), 1))(*[int(e[1]) for e in table])
+    las = (ctypes.c_int32 * max(len(table), 1))(*[int(e[2]) if len(e) > 2 else -1 for e in table])
+    L.skew_set_nb_table_ex(len(table), ctypes.cast(nu, ctypes.c_void_p), ctypes.cast(nbs, ctypes.c_void_p),
+                           ctypes.cast(las, ctypes.c_void_p))
     bt = saved.get("batched_table", [])
     bu = (ctypes.c_int32 * max(len(bt), 1))(*[int(e[0]) for e in bt])
     bn = (ctypes.c_int32 * max(len(bt), 1))(*[int(e[1]) for e in bt])
@@ -219,13 +222,17 @@ def batched_warp_tile(n: int) -> int:
 
 
 def set_nb_table(table):
-    """Install ``[(n_upper, nb), ...]`` (increasing n_upper) as the default panel widths;
-    an empty list restores the built-in rule."""
+    """Install ``[(n_upper, nb), ...]`` or ``[(n_upper, nb, lookahead), ...]`` (increasing
+    n_upper; lookahead 1 / 0 / -1 = look-ahead / plain / built-in choice, default -1) as
+    the default panel widths and paths; an empty list restores the built-in rules."""
     count = len(table)
-    nu = (ctypes.c_int64 * max(count, 1))(*[int(a) for a, _ in table])
-    nbs = (ctypes.c_int32 * max(count, 1))(*[int(b) for _, b in table])
-    _check("skew_set_nb_table", lib().skew_set_nb_table(count, ctypes.cast(nu, ctypes.c_void_p),
-                                                         ctypes.cast(nbs, ctypes.c_void_p)))
+    nu = (ctypes.c_int64 * max(count, 1))(*[int(e[0]) for e in table])
+    nbs = (ctypes.c_int32 * max(count, 1))(*[int(e[1]) for e in table])
+    las = (ctypes.c_int32 * max(count, 1))(*[int(e[2]) if len(e) > 2 else -1 for e in table])
+    _check("skew_set_nb_table_ex",
+           lib().skew_set_nb_table_ex(count, ctypes.cast(nu, ctypes.c_void_p),
+                                      ctypes.cast(nbs, ctypes.c_void_p),
+                                      ctypes.cast(las, ctypes.c_void_p)))
 
 
 def workspace_bytes(n: int, nb: int = 0, with_L: bool = True, lookahead: bool = False) -> int:
@@ -235,9 +242,13 @@ def workspace_bytes(n: int, nb: int = 0, with_L: bool = True, lookahead: bool = 
     return int(fn(n, nb, 1 if with_L else 0))
 
 
-def set_lookahead(on: bool) -> bool:
-    """Turn the look-ahead path of ltlt / pfaffian on or off; returns the old setting."""
-    return bool(lib().skew_set_lookahead(1 if on else 0))
+def set_lookahead(mode) -> int:
+    """Path of later ltlt / pfaffian calls (skew_set_lookahead): False / 0 plain, True / 1
+    the look-ahead where the panel-width table (or the built-in rule) picks it for the
+    order, 2 wherever it applies, 32 / 64 as 2 with that many rows per panel CTA.
+    Returns the old setting."""
+    m = int(mode) if not isinstance(mode, bool) else (1 if mode else 0)
+    return int(lib().skew_set_lookahead(m))
 
 
 def lookahead_used(n: int, nb: int = 0, precision: int = 0) -> bool:

@@ -24,8 +24,21 @@ import statistics
 TABLE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "nb_table.json")
 
 
-def measure(n: int, nb: int, reps: int, seed: int = 17) -> float:
-    """Median milliseconds of skew_ltlt (FP64 update, with L) at order n, width nb."""
+def measure(n: int, nb: int, reps: int, seed: int = 17, lookahead: bool = False) -> float:
+    """Median milliseconds of skew_ltlt (FP64 update, with L) at order n, width nb, on
+    the look-ahead path or the plain one."""
+    import torch
+
+    from . import _native as nat
+    from . import inputs
+    old = nat.set_lookahead(2 if lookahead else 0)
+    try:
+        return _measure(n, nb, reps, seed)
+    finally:
+        nat.set_lookahead(old)
+
+
+def _measure(n: int, nb: int, reps: int, seed: int) -> float:
     import torch
 
     from . import _native as nat
@@ -60,18 +73,48 @@ def pick(ms_by_nb: dict) -> int:
     return min(int(nb) for nb, v in ms_by_nb.items() if v <= best * (1.0 + TIE))
 
 
+def pick_path(ms_by_key: dict):
+    """(nb, lookahead) from timings keyed "nb" (plain path) and "nb+la" (look-ahead):
+    among the choices within TIE of the fastest, the plain path first (it needs less
+    workspace), then the smallest width."""
+    best = min(ms_by_key.values())
+    close = [k for k, v in ms_by_key.items() if v <= best * (1.0 + TIE)]
+    key = min(close, key=lambda k: (k.endswith("+la"), int(str(k).split("+")[0])))
+    return int(str(key).split("+")[0]), 1 if str(key).endswith("+la") else 0
+
+
 def table_from_ms(ms: dict):
-    """[(n, pick(ms[n])) ...] in increasing n: the range (previous n, n] takes the width
-    picked at n."""
-    return [(int(n), pick(d)) for n, d in sorted(ms.items(), key=lambda e: int(e[0]))]
+    """[(n, nb, lookahead) ...] in increasing n: the range (previous n, n] takes the
+    width and path picked at n."""
+    out = []
+    for n, d in sorted(ms.items(), key=lambda e: int(e[0])):
+        nb, la = pick_path({str(k): v for k, v in d.items()})
+        out.append((int(n), nb, la))
+    return out
 
 
 def tune(sizes=(512, 2048, 4096, 8192, 16384), candidates=(32, 48, 64, 96, 128), reps: int = 2):
-    """Returns ``{"table": [(n_upper, nb), ...], "ms": {n: {nb: ms}}}``."""
+    """Returns ``{"table": [(n_upper, nb, lookahead), ...], "ms": {n: {key: ms}}}`` with
+    key "nb" for the plain path and "nb+la" for the look-ahead (widths up to 64)."""
+    from . import _native as nat
     sizes = sorted(int(s) for s in sizes)
-    ms = {n: {nb: measure(n, nb, reps) for nb in candidates if nb < n} for n in sizes}
+    ms = {}
+    for n in sizes:
+        d = {}
+        for nb in candidates:
+            if nb >= n:
+                continue
+            d[str(nb)] = measure(n, nb, reps)
+            old = nat.set_lookahead(2)
+            try:
+                la_ok = nat.lookahead_used(n, nb)
+            finally:
+                nat.set_lookahead(old)
+            if la_ok:
+                d[f"{nb}+la"] = measure(n, nb, reps, lookahead=True)
+        ms[n] = d
     return {"table": table_from_ms(ms), "tie": TIE,
-            "ms": {str(n): {str(b): v for b, v in d.items()} for n, d in ms.items()}}
+            "ms": {str(n): d for n, d in ms.items()}}
 
 
 BUCKETS = (64, 128, 256, 512)      # order buckets of the batched kernels
@@ -217,7 +260,6 @@ def main():
         res.update(tune([int(x) for x in args.sizes.split(",")],
                         [int(x) for x in args.candidates.split(",")], args.reps))
         nat.set_nb_table(res["table"])
-        res["lookahead"] = {str(n): nat.lookahead_used(int(n), int(nb)) for n, nb in res["table"]}
     res.update(tune_batched(reps=args.reps))
     nat.set_batched_nb_table(res["batched_table"])
     res["command"] = ("python -m paper_2411_09859_gb300.autotune "

@@ -292,8 +292,11 @@ LaLayout workspace_layout_la(int64_t n, int nb, bool with_L) {
 }
 
 bool lookahead_applies(int64_t n, int nb, int precision, int sms) {
-    return g_lookahead.load() != 0 && precision == SKEW_PRECISION_FP64 && nb >= 2 &&
-           nb <= kLaMaxCols / 2 && n - 1 > nb && panel_la_fits(n, 0, sms);
+    const int mode = g_lookahead.load();          // 0 off, 1 by order, 2 always, 32..128
+    if (mode == 0 || precision != SKEW_PRECISION_FP64 || nb < 2 || nb > kLaMaxCols / 2 ||
+        n - 1 <= nb || !panel_la_fits(n, 0, sms))
+        return false;
+    return mode != 1 || lookahead_wanted(n);
 }
 
 // ------------------------------------------------------------------ the factorization
@@ -390,6 +393,7 @@ int factor_la(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double 
             pa.k0 = 0;
             pa.kend = (int)kend;
             pa.with_x = kend < n - 1 ? 1 : 0;
+            pa.rows_per_cta = g_lookahead.load() > 2 ? g_lookahead.load() : 0;
             double pf, pb;
             panel_prof(0, 0, kend, pa.with_x != 0, pf, pb);
             ProfScope ps(kProfPanel, ls.panel, pf, pb);
@@ -415,6 +419,7 @@ int factor_la(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double 
                 sa.Cin = sbuf(j - 1);
                 sa.ldcin = sld(j - 1);
                 sa.map = maps[j & 1] + (s + 1);
+                sa.nin = n;
                 sa.alpha = 1.0;
                 sa.beta = 1.0;
                 sa.P = lblock(k0, j) + (s + 1);
@@ -471,6 +476,7 @@ int factor_la(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double 
             pa.k0 = (int)k0n;
             pa.kend = (int)kendn;
             pa.with_x = kendn < n - 1 ? 1 : 0;
+            pa.rows_per_cta = g_lookahead.load() > 2 ? g_lookahead.load() : 0;
             {
                 double pf, pb;
                 panel_prof(k0, k0n, kendn, pa.with_x != 0, pf, pb);
@@ -840,25 +846,62 @@ const char *skew_last_error(void) { return g_last_error; }
 uint64_t skew_kernel_launches(void) { return g_launches.load(); }
 
 // Panel-width table installed by skew_set_nb_table (an autotuner's result), else the
-// built-in rule.  Guarded by a mutex: installs are rare, reads take a snapshot.
+// built-in rule; each entry also says whether that order range takes the look-ahead
+// (-1: the built-in rule).  Guarded by a mutex: installs are rare, reads take a
+// snapshot.
 namespace {
+struct NbEntry {
+    int64_t n_upper;
+    int nb;
+    int lookahead;
+};
 std::mutex g_nb_mutex;
-std::vector<std::pair<int64_t, int>> g_nb_table;
+std::vector<NbEntry> g_nb_table;
 }  // namespace
 
-int skew_set_nb_table(int count, const int64_t *n_upper, const int32_t *nb) {
+}  // extern "C"
+
+namespace skew {
+// Whether order n takes the look-ahead: the table's choice, else on for
+// 3072 <= n <= 10240 (measured on GB300: at n = 4096 / 8192 the look-ahead saves 10 % /
+// 5 %; at 2048 and from 12288 up the panel's extra FP64 work and its share of the
+// multiprocessors cost as much as the overlap saves).
+bool lookahead_wanted(int64_t n) {
+    {
+        std::lock_guard<std::mutex> lock(g_nb_mutex);
+        if (!g_nb_table.empty()) {
+            int la = g_nb_table.back().lookahead;
+            for (const auto &e : g_nb_table)
+                if (n <= e.n_upper) { la = e.lookahead; break; }
+            if (la >= 0) return la != 0;
+        }
+    }
+    return n >= 3072 && n <= 10240;
+}
+}  // namespace skew
+
+extern "C" {
+
+int skew_set_nb_table_ex(int count, const int64_t *n_upper, const int32_t *nb,
+                         const int32_t *lookahead) {
     if (count < 0) return -1;
     if (count > 0 && (n_upper == nullptr)) return -2;
     if (count > 0 && (nb == nullptr)) return -3;
-    std::vector<std::pair<int64_t, int>> t;
+    std::vector<NbEntry> t;
     for (int i = 0; i < count; ++i) {
         if (nb[i] < 1 || nb[i] > kMaxNb) return -3;
         if (i > 0 && n_upper[i] <= n_upper[i - 1]) return -2;
-        t.emplace_back(n_upper[i], nb[i]);
+        const int la = lookahead ? lookahead[i] : -1;
+        if (la < -1 || la > 1) return -4;
+        t.push_back({n_upper[i], nb[i], la});
     }
     std::lock_guard<std::mutex> lock(g_nb_mutex);
     g_nb_table.swap(t);
     return SKEW_OK;
+}
+
+int skew_set_nb_table(int count, const int64_t *n_upper, const int32_t *nb) {
+    return skew_set_nb_table_ex(count, n_upper, nb, nullptr);
 }
 
 int skew_set_batched_tiles(int count, const int32_t *n_upper, const int32_t *nb,
@@ -898,8 +941,8 @@ int skew_default_nb(int64_t n) {
         std::lock_guard<std::mutex> lock(g_nb_mutex);
         if (!g_nb_table.empty()) {
             for (const auto &e : g_nb_table)
-                if (n <= e.first) return e.second;
-            return g_nb_table.back().second;
+                if (n <= e.n_upper) return e.nb;
+            return g_nb_table.back().nb;
         }
     }
     if (n <= 256) return 16;
@@ -929,9 +972,10 @@ int skew_lookahead_used(int64_t n, int nb, int precision) {
     return lookahead_applies(n, nb, precision, di.sms) ? 1 : 0;
 }
 
-int skew_set_lookahead(int on) {
+int skew_set_lookahead(int mode) {
     const int old = g_lookahead.load();
-    g_lookahead.store(on != 0 ? 1 : 0);
+    g_lookahead.store((mode == 2 || mode == 32 || mode == 64 || mode == 128) ? mode
+                                                                            : (mode != 0 ? 1 : 0));
     return old;
 }
 

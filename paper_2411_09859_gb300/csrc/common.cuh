@@ -88,6 +88,8 @@ struct LaLayout {
 LaLayout workspace_layout_la(int64_t n, int nb, bool with_L);
 // Whether skew_ltlt / skew_pfaffian take the look-ahead path for this order and width.
 bool lookahead_applies(int64_t n, int nb, int precision, int sms);
+// The panel-width table's (or the built-in) choice of the look-ahead for order n.
+bool lookahead_wanted(int64_t n);
 
 // ------------------------------------------------------------------ device helpers
 __device__ __forceinline__ uint64_t global_ns() {
@@ -239,8 +241,9 @@ struct PanelLAArgs {
     Ctrl *ctrl;
     ArgmaxPartial *part;
     int n, kb, k0, kend, with_x;
+    int rows_per_cta;         // 0: the rule of la_rows_per_cta; 32, 64, 128: forced
 };
-constexpr int kLaThreads = 128;   // one row per thread
+constexpr int kLaThreads = 128;   // at most one row per thread, at most 128 per CTA
 constexpr int kLaMaxCols = 128;   // (k0 - kb) + (kend - k0) L columns in shared memory
 // Whether the rows of a look-ahead panel at k0 fit one per thread on `sms` CTAs.
 inline bool panel_la_fits(int64_t n, int64_t k0, int sms) {
@@ -264,6 +267,7 @@ struct Skr2kArgs {
     const double *Cin = nullptr;
     int64_t ldcin = 0;
     const int32_t *map = nullptr;
+    int64_t nin = 0;       // order of Cin: map entries outside [0, nin) read as 0
     double alpha, beta;    // C := beta C + alpha * sum_p (a_p w_p^T - w_p a_p^T)
     const double *P;       // Rank2k: the a columns; Tridiag/Fused: the A columns
     int64_t ldp;

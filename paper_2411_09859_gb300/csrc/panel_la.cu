@@ -64,6 +64,7 @@ panel_la_kernel(PanelLAArgs a) {
     const int n = a.n, kb = a.kb, k0 = a.k0, kend = a.kend;
     const int nbj = k0 - kb;                 // L columns of the previous panel
     const int G = (int)gridDim.x;
+    const int nthr = (int)blockDim.x;        // rows per CTA: 32, 64 or 128
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double *S = a.S;
     const int64_t lds = a.lds, ldl = a.ldl;
@@ -71,7 +72,7 @@ panel_la_kernel(PanelLAArgs a) {
     auto slot = [&](int k, int cta) -> ArgmaxPartial * {
         return a.part + (k & 1) * kMaxPanelGrid + cta;
     };
-    auto sL = [&](int c) -> double & { return s_L[c * kLaThreads + tid]; };
+    auto sL = [&](int c) -> double & { return s_L[c * nthr + tid]; };
 
     // this thread's row: chunk warp * G + cta, lane tid % 32
     const int i = k0 + 1 + ((warp * G + (int)blockIdx.x) << 5) + lane;
@@ -90,9 +91,14 @@ panel_la_kernel(PanelLAArgs a) {
     int phs = 0, pho = i;
     if (own) phs = a.map_prev ? __ldg(a.map_prev + i) : i;
     for (int c = 0; c < nbj; ++c) sL(c) = own ? __ldg(a.Lprev + i + (int64_t)c * a.ldlp) : 0.0;
-    for (int c = tid; c < nbj; c += kLaThreads) s_t[c] = __ldcg(a.t + kb + c);
+    for (int c = tid; c < nbj; c += nthr) s_t[c] = __ldcg(a.t + kb + c);
     __syncthreads();
-    if (s_fail) return;
+    if (s_fail) {
+        // an earlier stage failed: leave a valid map (the identity) for the update that
+        // follows, which reads through it
+        if (own && a.map_out) a.map_out[i] = i;
+        return;
+    }
     const unsigned int base = s_base;
 
     // Publish this CTA's step-k candidate (value, position, source index; its L row
@@ -112,7 +118,7 @@ panel_la_kernel(PanelLAArgs a) {
         __syncthreads();
         if (warp != 0) return;
         Best y = no_candidate();
-        if (lane < kLaThreads / 32) {
+        if (lane < nthr / 32) {
             y.raw = s_wraw[lane];
             y.i = s_wi[lane];
             y.c = (int)s_wc[lane];
@@ -123,13 +129,13 @@ panel_la_kernel(PanelLAArgs a) {
         unsigned int packed = kNoIdx;
         if (y.i != INT_MAX) {
             const int ot = owner_tid(y.i);
-            for (int q = lane; q < nq; q += 32) sp->row[q] = s_L[q * kLaThreads + ot];
+            for (int q = lane; q < nq; q += 32) sp->row[q] = s_L[q * nthr + ot];
             if (lane == 0) sp->aux[0] = (int)((unsigned int)y.c & 0xffffu);
             packed = ((unsigned int)y.c & 0xffff0000u) | (unsigned int)y.i;
         }
         if (k + 1 < n && owner_cta(k + 1) == (int)blockIdx.x) {
             const int ot = owner_tid(k + 1);
-            for (int q = lane; q < nq; q += 32) ctrl->rowp[k & 1][q] = s_L[q * kLaThreads + ot];
+            for (int q = lane; q < nq; q += 32) ctrl->rowp[k & 1][q] = s_L[q * nthr + ot];
         }
         __syncwarp();
         if (lane == 0) record_release(sp, y.raw, (int)packed, base + (unsigned int)(k - k0) + 1u);
@@ -233,7 +239,7 @@ panel_la_kernel(PanelLAArgs a) {
             }
         }
         __syncthreads();
-        if (s_fail) return;
+        if (s_fail) break;           // the map written below stays a valid permutation
         const int r = s_r, p = k + 1, nq = k - kb;
         const int win = s_win;
         // source index of the new column p (old row r); with no candidate (all NaN) the
@@ -241,7 +247,7 @@ panel_la_kernel(PanelLAArgs a) {
         // ---------------- one round of loads: exchanged L rows, positions, v[k+1],
         // and this thread's entry of the new column p
         if (win >= 0) {
-            for (int q = tid; q < nq; q += kLaThreads) {
+            for (int q = tid; q < nq; q += nthr) {
                 s_w[q] = __ldcg(&slot(k, win)->row[q]);
                 s_rp[q] = __ldcg(&ctrl->rowp[k & 1][q]);
             }
@@ -278,15 +284,15 @@ panel_la_kernel(PanelLAArgs a) {
         if (r != p && win >= 0) {
             if (owner_cta(p) == (int)blockIdx.x) {
                 const int ot = owner_tid(p);
-                for (int q = tid; q < nq; q += kLaThreads) {
-                    s_L[q * kLaThreads + ot] = s_w[q];
+                for (int q = tid; q < nq; q += nthr) {
+                    s_L[q * nthr + ot] = s_w[q];
                     if (q >= nbj) Lcol(kb + 1 + q)[p] = s_w[q];
                 }
             }
             if (owner_cta(r) == (int)blockIdx.x) {
                 const int ot = owner_tid(r);
-                for (int q = tid; q < nq; q += kLaThreads) {
-                    s_L[q * kLaThreads + ot] = s_rp[q];
+                for (int q = tid; q < nq; q += nthr) {
+                    s_L[q * nthr + ot] = s_rp[q];
                     if (q >= nbj) Lcol(kb + 1 + q)[r] = s_rp[q];
                 }
             }
@@ -297,7 +303,7 @@ panel_la_kernel(PanelLAArgs a) {
             // h for step k+1 from the new row p: L[p, c] = s_w[c - kb - 1] for c <= k,
             // L[p, k+1] = 1; t[c] = s_t[c - kb] for c < k, t[k] = tau
             auto tq = [&](int q) -> double { return q == k ? tau : s_t[q - kb]; };
-            for (int q = kb + 1 + tid; q <= k + 1; q += kLaThreads) {
+            for (int q = kb + 1 + tid; q <= k + 1; q += nthr) {
                 double hq = 0.0;
                 if (q - 1 >= kb + 1) hq = tq(q - 1) * s_w[q - 2 - kb];
                 if (q + 1 <= k + 1) {
@@ -358,13 +364,26 @@ panel_la_kernel(PanelLAArgs a) {
 
 }  // namespace
 
+// Rows per CTA of the look-ahead panel (one per thread): 128, so that a CTA's FP64
+// gemv runs on all four schedulers of its multiprocessor.  Measured on GB300 (look-ahead
+// factorization, ms): 32 rows per CTA up to 4096 rows and 64 up to 8192 gave 61.8 ms at
+// n = 4096 and 257 ms at n = 8192, against 45.5 and 228 with 128: more CTAs in the
+// grid-wide exchange cost more than the shorter gemv saves.  `force` (32 or 64)
+// overrides, for such measurements.
+int la_rows_per_cta(int64_t rows, int force) {
+    if ((force == 32 || force == 64) && rows <= (int64_t)force * kMaxPanelGrid) return force;
+    return 128;
+}
+
 int launch_panel_la(const PanelLAArgs &a, int sms, cudaStream_t stream) {
     const int64_t rows = (int64_t)a.n - a.k0 - 1;
     const int cols = (a.k0 - a.kb) + (a.kend - a.k0);
     if (rows < 1 || cols > kLaMaxCols || !panel_la_fits(a.n, a.k0, sms)) return SKEW_ERR_CUDA;
-    int64_t g = (rows + kLaThreads - 1) / kLaThreads;
+    const int nthr = la_rows_per_cta(rows, a.rows_per_cta);
+    int64_t g = (rows + nthr - 1) / nthr;
     if (g < 1) g = 1;
-    const size_t smem = (size_t)(cols > 0 ? cols : 1) * kLaThreads * sizeof(double);
+    if (g > kMaxPanelGrid) return SKEW_ERR_CUDA;        // unreachable: rows <= 128 x sms
+    const size_t smem = (size_t)(cols > 0 ? cols : 1) * nthr * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute((const void *)panel_la_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kLaMaxCols * kLaThreads * sizeof(double)));
@@ -375,7 +394,7 @@ int launch_panel_la(const PanelLAArgs &a, int sms, cudaStream_t stream) {
     PanelLAArgs args = a;
     void *params[] = {&args};
     e = cudaLaunchCooperativeKernel((const void *)panel_la_kernel, dim3((unsigned)g),
-                                    dim3(kLaThreads), params, smem, stream);
+                                    dim3((unsigned)nthr), params, smem, stream);
     if (e != cudaSuccess) {
         set_last_error(e);
         return SKEW_ERR_CUDA;

@@ -62,7 +62,8 @@ __device__ __forceinline__ void tri_tile(int64_t idx, int64_t &bi, int64_t &bj) 
 template <PairKind KIND>
 __global__ void __launch_bounds__(kThreads, 2)
 skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
-             PairSource<KIND> src, const double *Cin, int64_t ldcin, const int32_t *map) {
+             PairSource<KIND> src, const double *Cin, int64_t ldcin, const int32_t *map,
+             int64_t nin) {
     __shared__ double Us[BM][LDS];
     __shared__ double Vs[BM][LDS];
 
@@ -147,9 +148,13 @@ skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
                 } else if (Cin == nullptr) {
                     cv[ni][c] = C[gi + gj * ldc];
                 } else {
+                    // a map left by a failed panel is still read inside Cin
                     const int a = rmap, b = cmap[ni][c];
-                    cv[ni][c] = a > b ? __ldg(Cin + a + (int64_t)b * ldcin)
-                                      : -__ldg(Cin + b + (int64_t)a * ldcin);
+                    if ((uint64_t)a >= (uint64_t)nin || (uint64_t)b >= (uint64_t)nin || a == b)
+                        cv[ni][c] = 0.0;
+                    else
+                        cv[ni][c] = a > b ? __ldg(Cin + a + (int64_t)b * ldcin)
+                                          : -__ldg(Cin + b + (int64_t)a * ldcin);
                 }
             }
 #pragma unroll
@@ -176,7 +181,7 @@ int launch_kind(const Skr2kArgs &a, cudaStream_t stream) {
     PairSource<KIND> src{a.P, a.ldp, a.Q, a.ldq, a.tt, a.x, a.b};
     skr2k_kernel<KIND><<<(unsigned)tiles, kThreads, 0, stream>>>(a.m, a.C, a.ldc, a.alpha,
                                                                   a.beta, src, a.Cin, a.ldcin,
-                                                                  a.map);
+                                                                  a.map, a.nin);
     note_launches(1);
     return check_launch();
 }

@@ -125,6 +125,11 @@ def test_nb_table_install_and_reset():
             skew.set_nb_table([(1000, 0)])                   # bad width
         skew.set_nb_table([])
         assert [skew.default_nb(n) for n in (100, 1000, 5000)] == [16, 32, 64]
+        skew.set_nb_table([(1000, 24, 0), (8000, 48, 1), (16384, 64, -1)])
+        assert [skew.default_nb(n) for n in (100, 5000, 9000)] == [24, 48, 64]
+        with pytest.raises(skew.SkewError):
+            skew.set_nb_table([(1000, 24, 2)])                # bad path choice
+        skew.set_nb_table([])
     finally:
         from paper_2411_09859_gb300 import autotune
         if not autotune.load():
@@ -138,7 +143,11 @@ def test_autotune_pick_rule():
     assert autotune.pick({"32": 10.0, "64": 9.99, "96": 9.98}) == 32      # all within 0.5 %
     assert autotune.pick({"32": 10.0, "64": 9.0, "96": 8.99}) == 64
     assert autotune.table_from_ms({"4096": {"32": 1.0, "64": 2.0}, "512": {"16": 3.0, "32": 1.0}}) == \
-        [(512, 32), (4096, 32)]
+        [(512, 32, 0), (4096, 32, 0)]
+    # the look-ahead is taken only when it is faster by more than the tie margin
+    assert autotune.pick_path({"32": 10.0, "32+la": 9.99, "64": 10.2}) == (32, 0)
+    assert autotune.pick_path({"32": 10.0, "32+la": 9.0, "64+la": 8.99, "64": 9.5}) == (32, 1)
+    assert autotune.pick_path({"32": 10.0, "64+la": 8.0, "64": 9.5}) == (64, 1)
 
 
 def test_batched_nb_table():

@@ -1,8 +1,9 @@
 """The look-ahead path of skew_ltlt / skew_pfaffian against the oracle and against the
 plain path.
 
-With the look-ahead (the default where it applies: FP64 update, panel width 2 .. 64,
-n - 1 <= 128 x the multiprocessors), the panel of each block runs beside the trailing
+With the look-ahead (where it applies: FP64 update, panel width 2 .. 64, n - 1 <= 128 x
+the multiprocessors; taken by default for the orders where it is faster, and here
+forced with skew_set_lookahead(2)), the panel of each block runs beside the trailing
 update of the block before it, reading the state before that update and deferring its
 exchanges to the next (out-of-place) update.  Both paths factor the same matrix to the
 oracle's factorization: pivots identical, factors within the parity bars of
@@ -27,7 +28,8 @@ def dev(A):
 
 
 def factor(A, nb, lookahead, workspace=None, with_L=True):
-    old = skew.set_lookahead(lookahead)
+    # 2: the look-ahead wherever it applies (the default, 1, takes it by order only)
+    old = skew.set_lookahead(2 if lookahead else 0)
     try:
         if with_L:
             L, t, piv, info = skew.ltlt(dev(A), nb=nb, workspace=workspace)
@@ -74,7 +76,29 @@ def test_lookahead_pfaffian_only(n, nb):
     check(A, None, t, piv, info)
     L0, t0, p0, _ = oracle.ltlt(A)
     la0, sg0 = oracle.pfaffian_from_factors(n, t0, p0)
-    assert sg == sg0 and abs(la - la0) <= 1e-10 * max(1.0, abs(la0))
+    assert sg == sg0
+    if sg0 != 0:                              # odd n: Pf = 0, log|Pf| = -inf on both
+        assert abs(la - la0) <= 1e-10 * max(1.0, abs(la0))
+
+
+def test_default_path_choice():
+    """Mode 1 (the default) takes the look-ahead by order: the built-in rule for
+    3072 <= n <= 10240, or the panel-width table's choice; mode 0 never."""
+    old = skew.set_lookahead(1)
+    try:
+        skew.set_nb_table([])
+        assert not skew.lookahead_used(2000, 32) and skew.lookahead_used(4096, 64)
+        assert not skew.lookahead_used(16384, 64)
+        skew.set_nb_table([(3000, 32, 1), (20000, 64, 0)])
+        assert skew.lookahead_used(2000) and not skew.lookahead_used(4096)
+        assert not skew.lookahead_used(4096, 128)             # wider than 64: plain
+        skew.set_lookahead(0)
+        assert not skew.lookahead_used(2000)
+    finally:
+        skew.set_lookahead(old)
+        from paper_2411_09859_gb300 import autotune
+        if not autotune.load():
+            skew.set_nb_table([])
 
 
 def test_workspace_size_selects_the_path():
@@ -120,6 +144,15 @@ def test_lookahead_graph_capture_replays_equal():
     ws = torch.empty(skew.workspace_bytes(n, nb, True, lookahead=True), dtype=torch.uint8,
                      device="cuda")
     s = torch.cuda.Stream()
+    old = skew.set_lookahead(2)
+    try:
+        run_graph_case(A, Ad, work, L, t, piv, info, ws, s, n, nb)
+    finally:
+        skew.set_lookahead(old)
+
+
+def run_graph_case(A, Ad, work, L, t, piv, info, ws, s, n, nb):
+    assert skew.lookahead_used(n, nb)
     work.copy_(Ad)
     torch.cuda.synchronize()
     skew.ltlt(work, nb=nb, stream=s, L=L, t=t, piv=piv, info=info, workspace=ws)
