@@ -63,6 +63,9 @@ def parse_args():
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--nb", type=int, default=0)
     ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--path", choices=["auto", "plain", "lookahead"], default="auto",
+                    help="factorization path of the timed steps (auto: the library's choice "
+                         "for the order)")
     ap.add_argument("--skip-plain", action="store_true",
                     help="skip timing the other path (plain / look-ahead) beside the headline")
     ap.add_argument("--skip-e2e", action="store_true")
@@ -110,9 +113,9 @@ def table_nb(n: int) -> int:
             table = json.load(f).get("table", [])
     except (OSError, ValueError):
         table = []
-    for hi, nb in table:
-        if n <= hi:
-            return int(nb)
+    for entry in table:                       # (n_upper, nb[, look-ahead])
+        if n <= entry[0]:
+            return int(entry[1])
     if table:
         return int(table[-1][1])
     return 16 if n <= 256 else (32 if n <= 2048 else 64)
@@ -990,6 +993,8 @@ def run_ours(args):
     t = torch.empty(n - 1, dtype=torch.float64, device=dev)
     piv = torch.empty(n, dtype=torch.int32, device=dev)
     info = torch.empty(1, dtype=torch.int32, device=dev)
+    if args.path != "auto":
+        skew.set_lookahead(2 if args.path == "lookahead" else 0)
     lookahead = skew.lookahead_used(n, nb)
     ws = torch.empty(skew.workspace_bytes(n, nb, True, lookahead=True), dtype=torch.uint8,
                      device=dev)

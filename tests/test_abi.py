@@ -68,7 +68,7 @@ def test_binding_argument_counts_match_the_header():
 
 def test_host_only_queries(lib):
     assert lib.skew_version() >= 100
-    assert lib.skew_default_nb(16384) in (16, 32, 64, 128)
+    assert lib.skew_default_nb(16384) in (16, 32, 48, 64, 96, 128)
     ws = lib.skew_workspace_bytes(16384, 64, 0)
     assert ws >= 16384 * 64 * 8
     assert lib.skew_workspace_bytes(16384, 64, 1) < ws

@@ -23,7 +23,8 @@ def test_parse_cpulist():
 def test_table_nb_matches_the_saved_table_and_the_builtin_rule():
     with open(os.path.join(ROOT, "paper_2411_09859_gb300", "nb_table.json")) as f:
         table = json.load(f)["table"]
-    for hi, nb in table:
+    for entry in table:                            # (n_upper, nb[, look-ahead])
+        hi, nb = entry[0], entry[1]
         assert bench.table_nb(hi) == nb            # the range's upper end
     assert bench.table_nb(table[-1][0] * 2) == table[-1][1]   # beyond: the last entry
     # orders of the at-scale configuration take the width the bench reports
