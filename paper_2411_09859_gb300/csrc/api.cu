@@ -649,6 +649,7 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
                 sa.b = kend - k0;
                 ProfScope ps(kProfSkr2k, st, skr2k_flops(sa.m, sa.b / 2 + (sa.b & 1)),
                              skr2k_bytes(sa.m));
+                sa.balance = 1;
                 if (precision == SKEW_PRECISION_SPLIT_BF16)
                     status = launch_skr2k_split(PairKind::Fused, sa, base + lay.split, &ctrl->err, di.sms, st);
                 else
@@ -760,6 +761,7 @@ int factor_twostep(int64_t n, double *A, int64_t lda, double *a, int32_t *piv, i
                 sa.x = nullptr;
                 sa.b = np;
                 ProfScope ps(kProfSkr2k, st, skr2k_flops(m, np), skr2k_bytes(m));
+                sa.balance = 1;
                 if (precision == SKEW_PRECISION_SPLIT_BF16)
                     status = launch_skr2k_split(PairKind::Rank2k, sa, base + lay.split, &ctrl->err,
                                                 di.sms, st);

@@ -268,6 +268,7 @@ struct Skr2kArgs {
     int64_t ldcin = 0;
     const int32_t *map = nullptr;
     int64_t nin = 0;       // order of Cin: map entries outside [0, nin) read as 0
+    int balance = 0;       // split precision: balance each pair by powers of two first
     double alpha, beta;    // C := beta C + alpha * sum_p (a_p w_p^T - w_p a_p^T)
     const double *P;       // Rank2k: the a columns; Tridiag/Fused: the A columns
     int64_t ldp;

@@ -59,7 +59,7 @@ __device__ __forceinline__ void tri_tile(int64_t idx, int64_t &bi, int64_t &bj) 
     bj = idx - r * (r + 1) / 2;
 }
 
-template <PairKind KIND>
+template <PairKind KIND, bool MAPPED>
 __global__ void __launch_bounds__(kThreads, 2)
 skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
              PairSource<KIND> src, const double *Cin, int64_t ldcin, const int32_t *map,
@@ -123,7 +123,7 @@ skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
     // block are issued before its stores, so their latencies overlap.  Out of place,
     // the old entry (gi, gj) is entry (map[gi], map[gj]) of the skew matrix Cin.
     int cmap[4][2];
-    if (Cin != nullptr) {
+    if (MAPPED) {
 #pragma unroll
         for (int ni = 0; ni < 4; ++ni)
 #pragma unroll
@@ -136,7 +136,7 @@ skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
     for (int mi = 0; mi < 4; ++mi) {
         const int64_t gi = I0 + wm * 32 + mi * 8 + g;
         double cv[4][2];
-        const int rmap = (Cin != nullptr && gi < m) ? __ldg(map + gi) : 0;
+        const int rmap = (MAPPED && gi < m) ? __ldg(map + gi) : 0;
 #pragma unroll
         for (int ni = 0; ni < 4; ++ni)
 #pragma unroll
@@ -145,7 +145,7 @@ skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
                 const bool in = gi < m && gj < m && gi > gj && beta != 0.0;
                 if (!in) {
                     cv[ni][c] = 0.0;
-                } else if (Cin == nullptr) {
+                } else if (!MAPPED) {
                     cv[ni][c] = C[gi + gj * ldc];
                 } else {
                     // a map left by a failed panel is still read inside Cin
@@ -179,9 +179,12 @@ int launch_kind(const Skr2kArgs &a, cudaStream_t stream) {
     const int64_t tiles = nt * (nt + 1) / 2;
     if (tiles > INT_MAX) return SKEW_ERR_CUDA;      // unreachable: orders are capped
     PairSource<KIND> src{a.P, a.ldp, a.Q, a.ldq, a.tt, a.x, a.b};
-    skr2k_kernel<KIND><<<(unsigned)tiles, kThreads, 0, stream>>>(a.m, a.C, a.ldc, a.alpha,
-                                                                  a.beta, src, a.Cin, a.ldcin,
-                                                                  a.map, a.nin);
+    if (a.Cin != nullptr)
+        skr2k_kernel<KIND, true><<<(unsigned)tiles, kThreads, 0, stream>>>(
+            a.m, a.C, a.ldc, a.alpha, a.beta, src, a.Cin, a.ldcin, a.map, a.nin);
+    else
+        skr2k_kernel<KIND, false><<<(unsigned)tiles, kThreads, 0, stream>>>(
+            a.m, a.C, a.ldc, a.alpha, a.beta, src, nullptr, 0, nullptr, 0);
     note_launches(1);
     return check_launch();
 }

@@ -22,10 +22,11 @@
 // differs from the exact update by at most about 1.1 * 2^-53 * K * (max row entry of
 // U) * (max row entry of V) -- the size of FP64 rounding in an ordinary dot product,
 // but measured against row maxima rather than entry by entry.  K = 2 * pairs <= 64.
-// So that a large sub-diagonal entry of T does not raise the row maxima (w_j carries
-// t_j), each pair of the trailing update is first balanced by exact powers of two,
-// (a_p, w_p) -> (2^e_p a_p, 2^-e_p w_p), which leaves its term a_p w_p^T - w_p a_p^T
-// unchanged (pair_balance_exp).
+// So that a large sub-diagonal entry of T (w_j carries t_j), or a large trailing column
+// in the two-step update, does not raise the row maxima, each pair of a factorization's
+// trailing update is first balanced by exact powers of two, (a_p, w_p) -> (2^e_p a_p,
+// 2^-e_p w_p), with e_p from the pair's column maxima; this leaves its term
+// a_p w_p^T - w_p a_p^T unchanged (split_colexp_kernel, balance_exp).
 //
 // Update kernel: persistent, one CTA per SM, tiles of 128 rows x 32 columns of the
 // lower triangle of C, each CTA taking a contiguous run of tiles (consecutive tiles
@@ -129,38 +130,69 @@ __device__ __forceinline__ double pow2(int e) {
     return __longlong_as_double((long long)(1023 + e) << 52);
 }
 
-// Balancing exponent e_p of pair p of the Tridiag / Fused kinds.  The pair's term
+// Balancing of the pairs (trailing updates of the factorizations): the term
 // a_p w_p^T - w_p a_p^T is unchanged when a_p is scaled by 2^e_p and w_p by 2^-e_p
-// (exactly, as both are powers of two).  With |a| <= 1 (entries of L) and w_j =
-// t_j a_{j+1} - t_{j-1} a_{j-1} (+ x), |w_p| is about max(|t_{j-1}|, |t_j|) (= T_p), so
-// e_p = ceil(log2(T_p) / 2) brings both columns to about sqrt(T_p): a row then has no
-// column far below its largest entry only because T is large, and the digits keep the
-// precision of the a columns (the bound below is measured against row maxima).
-template <PairKind KIND>
-__device__ __forceinline__ int pair_balance_exp(const PairSource<KIND> &src, int p) {
-    if (KIND == PairKind::Rank2k || src.b < 2) return 0;
-    const int64_t j = 2 * (int64_t)p + 1;
-    double tm;
-    if (j < src.b) {
-        tm = fabs(src.tt[j - 1]);
-        if (j + 1 < src.b) tm = fmax(tm, fabs(src.tt[j]));
-    } else {
-        tm = fabs(src.tt[src.b - 2]);             // b odd: the pair (a_{b-1}, x)
-    }
-    const int ex = exponent_of(tm);
-    if (ex < -1000) return 0;                     // zero (or tiny) coupling
-    const int e = (ex + 1) >> 1;
+// (exactly, both being powers of two).  With Ea_p and Ew_p the largest exponents in
+// the columns a_p and w_p, e_p = ceil((Ew_p - Ea_p) / 2) brings both columns to the
+// same size, so that no column of a row lies far below the row's largest entry only
+// because the pairs differ in scale (a large T entry in w_j = t_j a_{j+1} - ..., or a
+// large trailing column y in the two-step update); the digits then keep the precision
+// of every column (the bound below is measured against row maxima).
+constexpr int kNoExp = (int)0x80808080;      // the byte pattern the column maxima start from
+
+__device__ __forceinline__ int balance_exp(int ea, int ew) {
+    if (ea < -1100 || ew < -1100) return 0;  // an all-zero column
+    const int e = (ew - ea + 1) >> 1;
     return e > 400 ? 400 : (e < -400 ? -400 : e);
 }
 
+// Column maxima of the exponents of the pairs: colexp[p] for a_p, colexp[32 + p] for
+// w_p (four threads per row as in the pre-pass; reduced per CTA, then atomicMax).
+template <PairKind KIND>
+__global__ void __launch_bounds__(256)
+split_colexp_kernel(int64_t m, PairSource<KIND> src, int P, int *colexp) {
+    __shared__ int s_max[64];
+    const int64_t i = (int64_t)blockIdx.x * 64 + (threadIdx.x >> 2);
+    const int g = threadIdx.x & 3;
+    if (threadIdx.x < 64) s_max[threadIdx.x] = kNoExp;
+    __syncthreads();
+    int ea[8], ew[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int p = 8 * g + q;
+        ea[q] = ew[q] = kNoExp;
+        if (i < m && p < P) {
+            double av, wv;
+            src.get(p, i, av, wv);
+            ea[q] = exponent_of(av) < -1100 ? kNoExp : exponent_of(av);
+            ew[q] = exponent_of(wv) < -1100 ? kNoExp : exponent_of(wv);
+        }
+        // the lanes holding the same pairs differ in lane bits 2, 3, 4
+#pragma unroll
+        for (int off = 4; off < 32; off <<= 1) {
+            ea[q] = max(ea[q], __shfl_xor_sync(0xffffffffu, ea[q], off));
+            ew[q] = max(ew[q], __shfl_xor_sync(0xffffffffu, ew[q], off));
+        }
+    }
+    if ((threadIdx.x & 31) < 4) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            atomicMax(&s_max[8 * g + q], ea[q]);
+            atomicMax(&s_max[32 + 8 * g + q], ew[q]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 64 && s_max[threadIdx.x] != kNoExp) atomicMax(&colexp[threadIdx.x], s_max[threadIdx.x]);
+}
+
 // Pre-pass, four threads per row i (thread g of the row takes pairs 8g .. 8g+7): the
-// pairs balanced by 2^(+-e_p) (pair_balance_exp), the exponent E_i of the row's
+// pairs balanced by 2^(+-e_p) (balance_exp, when colexp is given), the exponent E_i of the row's
 // largest balanced entry, and the digit slices Zu[s][i][0..63] = digits of [a | -w],
 // Zv[s][i][0..63] = digits of [w | a] (pair p in column p of each half, zero past P).
 template <PairKind KIND>
 __global__ void __launch_bounds__(256)
 split_prepare_kernel(int64_t m, PairSource<KIND> src, int P, unsigned short *Zu,
-                     unsigned short *Zv, int *rowexp) {
+                     unsigned short *Zv, int *rowexp, const int *colexp) {
     const int64_t i = (int64_t)blockIdx.x * 64 + (threadIdx.x >> 2);
     const int g = threadIdx.x & 3;
     double av[8], wv[8];
@@ -172,7 +204,7 @@ split_prepare_kernel(int64_t m, PairSource<KIND> src, int P, unsigned short *Zu,
         wv[q] = 0.0;
         if (i < m && p < P) {
             src.get(p, i, av[q], wv[q]);
-            const int e = pair_balance_exp(src, p);
+            const int e = colexp ? balance_exp(__ldg(colexp + p), __ldg(colexp + 32 + p)) : 0;
             if (e != 0) {
                 av[q] *= pow2(e);
                 wv[q] *= pow2(-e);
@@ -589,6 +621,10 @@ int make_slice_map(CUtensorMap *map, const unsigned short *Z, int64_t m, int row
     return r == CUDA_SUCCESS ? SKEW_OK : SKEW_ERR_CUDA;
 }
 
+size_t rowexp_bytes(int64_t m) {
+    return ((size_t)(m > 0 ? m : 1) * sizeof(int) + 255) & ~size_t(255);
+}
+
 size_t slice_bytes(int64_t m) {
     const size_t z = (size_t)kSlices * (size_t)(m > 0 ? m : 1) * kK * sizeof(unsigned short);
     return (z + 1023) & ~size_t(1023);
@@ -610,8 +646,16 @@ int launch_split_kind(const Skr2kArgs &a, void *scratch, int *err, int sms,
     unsigned short *Zu = reinterpret_cast<unsigned short *>(base);
     unsigned short *Zv = reinterpret_cast<unsigned short *>(base + slice_bytes(a.m));
     int *rowexp = reinterpret_cast<int *>(base + 2 * slice_bytes(a.m));
+    int *colexp = reinterpret_cast<int *>(base + 2 * slice_bytes(a.m) + rowexp_bytes(a.m));
     const int pgrid = (int)((a.m + 63) / 64);            // 64 rows per 256-thread CTA
-    split_prepare_kernel<KIND><<<pgrid, 256, 0, stream>>>(a.m, src, P, Zu, Zv, rowexp);
+    if (a.balance) {
+        SKEW_TRY(cudaMemsetAsync(colexp, 0x80, 64 * sizeof(int), stream));
+        split_colexp_kernel<KIND><<<pgrid, 256, 0, stream>>>(a.m, src, P, colexp);
+        note_launches(1);
+        SKEW_TRY_STATUS(check_launch());
+    }
+    split_prepare_kernel<KIND><<<pgrid, 256, 0, stream>>>(a.m, src, P, Zu, Zv, rowexp,
+                                                         a.balance ? colexp : nullptr);
     note_launches(1);
     SKEW_TRY_STATUS(check_launch());
 
@@ -637,7 +681,7 @@ int launch_split_kind(const Skr2kArgs &a, void *scratch, int *err, int sms,
 }  // namespace
 
 size_t split_scratch_bytes(int64_t m) {
-    return 2 * slice_bytes(m) + (((size_t)(m > 0 ? m : 1) * sizeof(int) + 255) & ~size_t(255));
+    return 2 * slice_bytes(m) + rowexp_bytes(m) + 256;      // + the 64 column exponents
 }
 
 int launch_skr2k_split(PairKind kind, const Skr2kArgs &a, void *scratch, int *err, int sms,
