@@ -76,6 +76,13 @@ uint64_t skew_kernel_launches(void);
  * only when no library work is in flight on the current device. */
 int skew_trim_memory(void);
 
+/* Device memory the library's allocations hold on the current device: used_now in
+ * use right now, used_high the most held at once since the last reset (reset_high != 0
+ * resets it after reading).  Counts what the library allocates itself (workspaces,
+ * server buffers, host-call buffers), not the caller's buffers.  No counterpart in the
+ * paper. */
+int skew_pool_usage(size_t *used_now, size_t *used_high, int reset_high);
+
 /*
  * Per-kernel timing.  While enabled, every kernel launch made by skew_ltlt,
  * skew_pfaffian, skew_pfaffian_twostep, the batched calls, skew_rank2k and

@@ -32,6 +32,7 @@ SIGNATURES = {
     "skew_last_error": ([], ctypes.c_char_p),
     "skew_kernel_launches": ([], ctypes.c_uint64),
     "skew_trim_memory": ([], _i32),
+    "skew_pool_usage": ([_vp, _vp, _i32], _i32),
     "skew_selftest_bounded_wait": ([_dbl, _vp], _i32),
     "skew_selftest_mbarrier_wait": ([_dbl, _vp], _i32),
     "skew_profile_enable": ([_i32], _i32),
@@ -254,6 +255,15 @@ def set_lookahead(mode) -> int:
 def lookahead_used(n: int, nb: int = 0, precision: int = 0) -> bool:
     """Whether a call at order n, width nb takes the look-ahead path on this device."""
     return bool(lib().skew_lookahead_used(n, nb, precision))
+
+
+def pool_usage(reset_high: bool = False):
+    """(bytes in use, most bytes in use at once since the last reset) of the library's
+    own device allocations on the current device."""
+    now, high = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    _check("skew_pool_usage", lib().skew_pool_usage(ctypes.byref(now), ctypes.byref(high),
+                                                    1 if reset_high else 0))
+    return int(now.value), int(high.value)
 
 
 def trim_memory():

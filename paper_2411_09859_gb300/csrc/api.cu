@@ -1070,6 +1070,23 @@ int skew_selftest_mbarrier_wait(double timeout_s, int32_t *status) {
     return rc;
 }
 
+int skew_pool_usage(size_t *used_now, size_t *used_high, int reset_high) {
+    int dev;
+    SKEW_TRY(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    SKEW_TRY_STATUS(device_pool(dev, &pool));
+    unsigned long long now = 0, high = 0;   // the attributes are 64-bit values
+    SKEW_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &now));
+    SKEW_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high));
+    if (used_now) *used_now = (size_t)now;
+    if (used_high) *used_high = (size_t)high;
+    if (reset_high) {
+        unsigned long long zero = 0;
+        SKEW_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    }
+    return SKEW_OK;
+}
+
 int skew_trim_memory(void) {
     int dev;
     SKEW_TRY(cudaGetDevice(&dev));

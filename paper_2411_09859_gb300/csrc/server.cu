@@ -109,14 +109,15 @@ size_t request_bytes(int64_t n, bool want_L) {
 // workspace of its own call, or its share of a batched launch (a descriptor, the
 // batch's result words and the batched kernel's counters).
 size_t request_ws_bytes(const skew_server *s, const Request &r) {
+    // (the look-ahead figures cover both paths of skew_ltlt / skew_pfaffian)
     if (r.n <= batch_limit(s, r)) return 1024 + skew::batched_workspace_bytes(1, (int)r.n);
-    if (r.mode == SKEW_SERVE_FACTORS_L) return skew_workspace_bytes(r.n, 0, 1);
+    if (r.mode == SKEW_SERVE_FACTORS_L) return skew_workspace_bytes_lookahead(r.n, 0, 1);
     if (r.mode == SKEW_SERVE_PFAFFIAN) {
         const size_t a = skew_workspace_bytes_twostep(r.n, 0, SKEW_PRECISION_FP64);
-        const size_t b = skew_workspace_bytes(r.n, 0, 0);   // fallback of large orders
+        const size_t b = skew_workspace_bytes_lookahead(r.n, 0, 0);   // fallback of large orders
         return a > b ? a : b;
     }
-    return skew_workspace_bytes(r.n, 0, 0);
+    return skew_workspace_bytes_lookahead(r.n, 0, 0);
 }
 
 // The launch of the request has ended (completed or failed): its workspace is back.

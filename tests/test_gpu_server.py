@@ -111,21 +111,30 @@ def test_pfaffian_only_requests_alone_in_the_mix_and_oracle():
 
 
 def test_admission_follows_budget():
+    """Admission keeps what the server's requests hold within the budget: the resident
+    buffers and the workspaces their launches allocate.  Checked both on the server's
+    own count and on the library's device allocations (their high-water mark over the
+    run, less what was held before the server started)."""
     n = 400
     A = dev(inputs.skew_gaussian(n, 11))
-    per = 8 * n * n + 8 * n + 4 * n + 4096                 # about one request
-    srv = skew.Server(int(2.5 * per), n_streams=4, small_n_max=256)
+    per = 8 * n * n + 8 * n + 4 * n + 4096                 # about one request's buffers
+    budget = int(2.5 * per) + skew.workspace_bytes(n, 0, False, lookahead=True)
+    torch.cuda.synchronize()
+    base, _ = skew.pool_usage(reset_high=True)
+    srv = skew.Server(budget, n_streams=4, small_n_max=256)
     tickets = [srv.submit(A) for _ in range(12)]
     seen_queue = srv.stats()["queued"] > 0
     res = []
     for tk in tickets:                       # results stay resident until released, so
         res.append(srv.wait(tk, 60.0))       # each is released once read to let the
         srv.release(tk)                      # next queued request in
-        assert srv.stats()["used_bytes"] <= int(2.5 * per)
+        assert srv.stats()["used_bytes"] <= budget
     assert seen_queue
     ref = res[0]
     assert all(r["sign"] == ref["sign"] and r["logabs"] == ref["logabs"] for r in res)
     srv.close()
+    _, high = skew.pool_usage()
+    assert high - base <= budget
 
 
 def test_wait_times_out_until_memory_is_released():
@@ -199,7 +208,8 @@ def test_latency_breakdown_sums_to_latency():
     n = 300
     A = dev(inputs.skew_gaussian(n, 13))
     per = 8 * n * n + 8 * n + 4 * n + 4096
-    srv = skew.Server(int(3.5 * per), n_streams=2, small_n_max=128)
+    budget = int(2.5 * per) + skew.workspace_bytes(n, 0, False, lookahead=True)
+    srv = skew.Server(budget, n_streams=2, small_n_max=128)
     tickets = [srv.submit(A, pfaffian_only=(i % 2 == 0)) for i in range(8)]
     queued_any = False
     for tk in tickets:
