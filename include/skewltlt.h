@@ -165,6 +165,13 @@ int skew_set_batched_tiles(int count, const int32_t *n_upper, const int32_t *nb,
                            const int32_t *warp_tile);
 int skew_get_batched_warp_tile(int n);
 
+/* Threads per CTA of the blocked batched kernels (skew_ltlt_batched up to n = 512,
+ * skew_pfaffian_batched): 256 (the default) or 128.  Returns the previous value, or -1
+ * for another value.  With 128, a multiprocessor can hold more matrices at once (when
+ * the panel width keeps shared memory small enough), each factored by fewer warps.
+ * Typically the batched autotuner's choice.  No counterpart in the paper. */
+int skew_set_batched_threads(int threads);
+
 /*
  * Device workspace, in bytes, that skew_ltlt / skew_pfaffian need for order n and
  * panel width nb (0 = default).  `with_L` = 0 gives the figure for skew_pfaffian,

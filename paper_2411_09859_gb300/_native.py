@@ -43,6 +43,7 @@ SIGNATURES = {
     "skew_get_batched_nb": ([_i32], _i32),
     "skew_set_batched_tiles": ([_i32, _vp, _vp, _vp], _i32),
     "skew_get_batched_warp_tile": ([_i32], _i32),
+    "skew_set_batched_threads": ([_i32], _i32),
     "skew_workspace_bytes": ([_i64, _i32, _i32], _sz),
     "skew_workspace_bytes_lookahead": ([_i64, _i32, _i32], _sz),
     "skew_set_lookahead": ([_i32], _i32),
@@ -133,6 +134,7 @@ def _install_saved_nb_table(L):
     bw = (ctypes.c_int32 * max(len(bt), 1))(*[int(e[2]) if len(e) > 2 else 32 for e in bt])
     L.skew_set_batched_tiles(len(bt), ctypes.cast(bu, ctypes.c_void_p), ctypes.cast(bn, ctypes.c_void_p),
                              ctypes.cast(bw, ctypes.c_void_p))
+    L.skew_set_batched_threads(int(saved.get("batched_threads", 256)))
 
 
 def _check(fn: str, status: int):
@@ -220,6 +222,14 @@ def batched_nb(n: int) -> int:
 
 def batched_warp_tile(n: int) -> int:
     return int(lib().skew_get_batched_warp_tile(n))
+
+
+def set_batched_threads(threads: int) -> int:
+    """Threads per CTA of the blocked batched kernels (256 or 128); returns the old value."""
+    old = int(lib().skew_set_batched_threads(int(threads)))
+    if old < 0:
+        raise SkewError("skew_set_batched_threads", old)
+    return old
 
 
 def set_nb_table(table):

@@ -176,14 +176,17 @@ def measure_batched_mix(sizes, table_nb, reps: int = 2, batch=None) -> float:
 
 def tune_batched(sizes=None, buckets=BUCKETS, candidates=BATCHED_NB, tiles=BATCHED_WT,
                  reps: int = 2):
-    """The batched kernels' panel width and update warp tile per order bucket, chosen on
-    a workload mix (default: the batched workload, 4096 orders even in [16, 256]).
-    First every combination of widths over the buckets the mix populates is timed with
-    warp tile 32 (both batched kernels, summed); then, with those widths, every
-    combination of warp tiles.  A bucket the mix does not reach takes the fastest
+    """The batched kernels' panel width and update warp tile per order bucket, and the
+    CTA size of the blocked kernels, chosen on a workload mix (default: the batched
+    workload, 4096 orders even in [16, 256]).  For each CTA size (256, then 128
+    threads): every combination of widths over the buckets the mix populates is timed
+    with warp tile 32 (both batched kernels, summed), then, with those widths, every
+    combination of warp tiles.  The fastest CTA size wins (256 unless 128 is faster by
+    more than the tie margin).  A bucket the mix does not reach takes the fastest
     (width, tile) on a batch of its own orders."""
     import itertools
 
+    from . import _native as nat
     from . import inputs
     if sizes is None:
         sizes = inputs.batched_sizes(4096)
@@ -191,28 +194,43 @@ def tune_batched(sizes=None, buckets=BUCKETS, candidates=BATCHED_NB, tiles=BATCH
     batch = _batch(sizes, 50000)
     lows = [16] + [b + 2 for b in buckets[:-1]]
     used = [hi for lo, hi in zip(lows, buckets) if any(lo <= n <= hi for n in sizes)]
-    mix_ms = {}
-    for combo in itertools.product(candidates, repeat=len(used)):
-        tab = [(hi, nb, 32) for hi, nb in zip(used, combo)]
-        mix_ms[combo] = measure_batched_mix(sizes, tab, reps, batch)
-    best_nb = dict(zip(used, min(mix_ms, key=mix_ms.get)))
-    wt_ms = {}
-    for combo in itertools.product(tiles, repeat=len(used)):
-        tab = [(hi, best_nb[hi], wt) for hi, wt in zip(used, combo)]
-        wt_ms[combo] = measure_batched_mix(sizes, tab, reps, batch)
-    best_wt = dict(zip(used, min(wt_ms, key=wt_ms.get)))
+    per_thr = {}
+    for thr in (256, 128):
+        old_thr = nat.set_batched_threads(thr)
+        try:
+            mix_ms = {}
+            for combo in itertools.product(candidates, repeat=len(used)):
+                tab = [(hi, nb, 32) for hi, nb in zip(used, combo)]
+                mix_ms[combo] = measure_batched_mix(sizes, tab, reps, batch)
+            best_nb = dict(zip(used, min(mix_ms, key=mix_ms.get)))
+            wt_ms = {}
+            for combo in itertools.product(tiles, repeat=len(used)):
+                tab = [(hi, best_nb[hi], wt) for hi, wt in zip(used, combo)]
+                wt_ms[combo] = measure_batched_mix(sizes, tab, reps, batch)
+            best_wt = dict(zip(used, min(wt_ms, key=wt_ms.get)))
+        finally:
+            nat.set_batched_threads(old_thr)
+        per_thr[thr] = (min(wt_ms.values()), best_nb, best_wt, mix_ms, wt_ms)
+    best_thr = 128 if per_thr[128][0] < per_thr[256][0] * (1.0 - TIE) else 256
+    _, best_nb, best_wt, mix_ms, wt_ms = per_thr[best_thr]
     del batch
     extra = {}
-    for lo, hi in zip(lows, buckets):
-        if hi in best_nb:
-            continue
-        own = [lo + 2 * ((hi - lo) // 4)] * 256
-        extra[hi] = {(nb, wt): measure_batched_mix(own, [(hi, nb, wt)], reps)
-                     for nb in candidates for wt in tiles}
-        fastest = min(extra[hi].values())
-        nb, wt = min(k for k, v in extra[hi].items() if v <= fastest * (1.0 + TIE))
-        best_nb[hi], best_wt[hi] = nb, wt
+    old_thr = nat.set_batched_threads(best_thr)
+    try:
+        for lo, hi in zip(lows, buckets):
+            if hi in best_nb:
+                continue
+            own = [lo + 2 * ((hi - lo) // 4)] * 256
+            extra[hi] = {(nb, wt): measure_batched_mix(own, [(hi, nb, wt)], reps)
+                         for nb in candidates for wt in tiles}
+            fastest = min(extra[hi].values())
+            nb, wt = min(k for k, v in extra[hi].items() if v <= fastest * (1.0 + TIE))
+            best_nb[hi], best_wt[hi] = nb, wt
+    finally:
+        nat.set_batched_threads(old_thr)
     return {"batched_table": [(hi, best_nb[hi], best_wt[hi]) for hi in buckets],
+            "batched_threads": best_thr,
+            "batched_threads_best_ms": {str(t): v[0] for t, v in per_thr.items()},
             "batched_mix_ms": {",".join(map(str, k)): v for k, v in mix_ms.items()},
             "batched_mix_warp_tile_ms": {",".join(map(str, k)): v for k, v in wt_ms.items()},
             "batched_mix_buckets": used,
@@ -237,6 +255,7 @@ def load(path: str = TABLE_PATH) -> bool:
     from . import _native as nat
     nat.set_nb_table([tuple(e) for e in saved.get("table", [])])
     nat.set_batched_nb_table([tuple(e) for e in saved.get("batched_table", [])])
+    nat.set_batched_threads(int(saved.get("batched_threads", 256)))
     return True
 
 
@@ -262,12 +281,13 @@ def main():
         nat.set_nb_table(res["table"])
     res.update(tune_batched(reps=args.reps))
     nat.set_batched_nb_table(res["batched_table"])
+    nat.set_batched_threads(res["batched_threads"])
     res["command"] = ("python -m paper_2411_09859_gb300.autotune "
                       + ("--batched-only " if args.batched_only else
                          f"--sizes {args.sizes} --candidates {args.candidates} ")
                       + f"--reps {args.reps} (the smallest width within {TIE * 100:.1f} % "
                       "of the fastest is kept; batched: widths over the mix's buckets with "
-                      "warp tile 32, then warp tiles with those widths)")
+                      "warp tile 32, then warp tiles with those widths, then 256 or 128 threads per CTA)")
     if not args.no_save:
         save(res)
     print(json.dumps(res))

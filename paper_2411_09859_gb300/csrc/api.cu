@@ -790,7 +790,7 @@ int factor_twostep(int64_t n, double *A, int64_t lda, double *a, int32_t *piv, i
 namespace skew {
 namespace {
 std::mutex g_bnb_mutex;
-BatchedNb g_bnb = {0, {0}, {0}, {0}};
+BatchedNb g_bnb = {0, {0}, {0}, {0}, 256};
 }  // namespace
 
 BatchedNb batched_nb_table() {
@@ -911,7 +911,7 @@ int skew_set_batched_tiles(int count, const int32_t *n_upper, const int32_t *nb,
     if (count < 0 || count > 8) return -1;
     if (count > 0 && n_upper == nullptr) return -2;
     if (count > 0 && nb == nullptr) return -3;
-    BatchedNb t = {count, {0}, {0}, {0}};
+    BatchedNb t = {count, {0}, {0}, {0}, 256};
     for (int i = 0; i < count; ++i) {
         if (nb[i] != 8 && nb[i] != 16 && nb[i] != 32) return -3;
         if (n_upper[i] < 1 || (i > 0 && n_upper[i] <= n_upper[i - 1])) return -2;
@@ -922,8 +922,17 @@ int skew_set_batched_tiles(int count, const int32_t *n_upper, const int32_t *nb,
         t.wt[i] = wt;
     }
     std::lock_guard<std::mutex> lock(g_bnb_mutex);
+    t.threads = g_bnb.threads;
     g_bnb = t;
     return SKEW_OK;
+}
+
+int skew_set_batched_threads(int threads) {
+    if (threads != 128 && threads != 256) return -1;
+    std::lock_guard<std::mutex> lock(g_bnb_mutex);
+    const int old = g_bnb.threads;
+    g_bnb.threads = threads;
+    return old;
 }
 
 int skew_set_batched_nb_table(int count, const int32_t *n_upper, const int32_t *nb) {

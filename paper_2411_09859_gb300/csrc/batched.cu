@@ -282,7 +282,7 @@ __device__ Cand blk_cand(Cand x, bool bad, BlkShared &sh, bool &any_bad) {
     y.raw = 0ull;
     y.i = INT_MAX;
     int b = 0;
-    if (lane < kBlkThreads / 32) { y.raw = sh.w_raw[lane]; y.i = sh.w_i[lane]; b = sh.w_bad[lane]; }
+    if (lane < (int)(blockDim.x >> 5)) { y.raw = sh.w_raw[lane]; y.i = sh.w_i[lane]; b = sh.w_bad[lane]; }
     y = warp_cand_all(y);
     any_bad = __any_sync(0xffffffffu, b) != 0;
     return y;
@@ -945,16 +945,17 @@ int launch_batched_twostep(int count, const skew_problem *problems, double *loga
         set_last_error(e);
         return SKEW_ERR_CUDA;
     }
+    const int thr = tab.threads == 128 ? 128 : kBlkThreads;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_twostep_kernel,
-                                                      kBlkThreads, smem);
+                                                      thr, smem);
     if (e != cudaSuccess || per_sm < 1) {
         if (e != cudaSuccess) set_last_error(e);
         return SKEW_ERR_CUDA;
     }
     int grid = sms * per_sm;
     if (grid > count) grid = count;
-    batched_twostep_kernel<<<grid, kBlkThreads, smem, stream>>>(count, problems, order, counter,
+    batched_twostep_kernel<<<grid, thr, smem, stream>>>(count, problems, order, counter,
                                                                 logabs, sign, info, max_n, tab);
     note_launches(1);
     return check_launch();
@@ -990,16 +991,17 @@ int launch_batched(int count, const skew_problem *problems, double *logabs, int3
             set_last_error(e);
             return SKEW_ERR_CUDA;
         }
+        const int thr = tab.threads == 128 ? 128 : kBlkThreads;
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_blocked_kernel,
-                                                          kBlkThreads, bsmem);
+                                                          thr, bsmem);
         if (e != cudaSuccess || per_sm < 1) {
             if (e != cudaSuccess) set_last_error(e);
             return SKEW_ERR_CUDA;
         }
         int grid = sms * per_sm;
         if (grid > count) grid = count;
-        batched_blocked_kernel<<<grid, kBlkThreads, bsmem, stream>>>(
+        batched_blocked_kernel<<<grid, thr, bsmem, stream>>>(
             count, problems, order, counter, logabs, sign, info, max_n, tab);
         note_launches(1);
         return check_launch();

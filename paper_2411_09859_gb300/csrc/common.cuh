@@ -313,12 +313,15 @@ int launch_finish_twostep(int64_t n, const double *a, const int32_t *piv, const 
 // Panel width and update warp tile of the CTA-local batched kernels per order bucket:
 // n <= n_upper[i] takes nb[i] (8, 16 or 32) and wt[i] (16 or 32: each warp of the
 // trailing update owns a wt x wt tile of the lower triangle; first match), larger
-// orders the last entry; count 0: width 16, warp tile 32.
+// orders the last entry; count 0: width 16, warp tile 32.  `threads` (one value for a
+// launch) is the CTA size of the blocked kernels, 256 or 128: with 128 a
+// multiprocessor holds more matrices at once when shared memory allows it.
 struct BatchedNb {
     int count;
     int n_upper[8];
     int nb[8];
     int wt[8];
+    int threads;          // threads per CTA of the blocked batched kernels: 256 or 128
 };
 __host__ __device__ inline int batched_nb_for(const BatchedNb &t, int n) {
     for (int i = 0; i < t.count; ++i)

@@ -242,12 +242,14 @@ def test_pfaffian_batched_replays_from_a_cuda_graph():
 
 @pytest.mark.parametrize("nb", [8, 16, 32])
 @pytest.mark.parametrize("wt", [16, 32])
-def test_batched_panel_widths_against_oracle(nb, wt):
-    """Every (panel width, update warp tile) the batched tuner can choose, forced for
-    all orders, in both batched kernels."""
+@pytest.mark.parametrize("threads", [256, 128])
+def test_batched_panel_widths_against_oracle(nb, wt, threads):
+    """Every (panel width, update warp tile, CTA size) the batched tuner can choose,
+    forced for all orders, in both batched kernels."""
     from paper_2411_09859_gb300 import autotune
     sizes = [2, 9, 16, 33, 70, 128, 200, 256, 300, 512]
     mats = [inputs.skew_gaussian(n, 7100 + n) for n in sizes]
+    old_threads = skew.set_batched_threads(threads)
     try:
         skew.set_batched_nb_table([(512, nb, wt)])
         assert skew.batched_nb(100) == nb and skew.batched_warp_tile(100) == wt
@@ -258,5 +260,6 @@ def test_batched_panel_widths_against_oracle(nb, wt):
         for b, A in enumerate(mats):
             check_twostep(A, la[b], sg[b], info[b], as_[b], pivs[b])
     finally:
+        skew.set_batched_threads(old_threads)
         if not autotune.load():
             skew.set_batched_nb_table([])
