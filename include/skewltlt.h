@@ -140,7 +140,7 @@ int skew_set_nb_table(int count, const int64_t *n_upper, const int32_t *nb);
 /* The same with, per entry, lookahead[i] = 1 / 0 / -1: that order range takes the
  * look-ahead path / the plain path / the built-in choice (see skew_set_lookahead);
  * lookahead may be NULL (all -1).  Returns as skew_set_nb_table, or -4 for a bad
- * lookahead entry. */
+ * lookahead entry.  No counterpart in the paper. */
 int skew_set_nb_table_ex(int count, const int64_t *n_upper, const int32_t *nb,
                          const int32_t *lookahead);
 
@@ -195,6 +195,8 @@ size_t skew_workspace_bytes(int64_t n, int nb, int with_L);
 size_t skew_workspace_bytes_lookahead(int64_t n, int nb, int with_L);
 
 /* Chooses the path of later calls of this process; returns the previous setting.
+ * Both paths compute the factorization of Section 5.2; the look-ahead is a schedule of
+ * this library with no counterpart in the paper.
  *   0  plain path always;
  *   1  (the default) the look-ahead where the panel-width table says so for the order
  *      (skew_set_nb_table_ex), else for 3072 <= n <= 10240;
@@ -205,7 +207,8 @@ int skew_set_lookahead(int mode);
 
 /* 1 if skew_ltlt / skew_pfaffian_ex at order n, width nb (0 = default) and this
  * trailing-update precision take the look-ahead path on the current device when given
- * skew_workspace_bytes_lookahead bytes (or no workspace), else 0. */
+ * skew_workspace_bytes_lookahead bytes (or no workspace), else 0.  No counterpart in
+ * the paper. */
 int skew_lookahead_used(int64_t n, int nb, int precision);
 
 /*
