@@ -172,3 +172,32 @@ def run_graph_case(A, Ad, work, L, t, piv, info, ws, s, n, nb):
         torch.cuda.synchronize()
         assert torch.equal(L, ref[0]) and torch.equal(t, ref[1]) and torch.equal(piv, ref[2])
     check(A, ref[0].cpu().numpy(), ref[1].cpu().numpy(), ref[2].cpu().numpy(), int(info.item()))
+
+
+def test_lookahead_at_its_largest_order_and_beyond():
+    """n - 1 = 128 x (multiprocessors) is the largest order whose panel rows fit one per
+    thread in 128-row CTAs: the look-ahead runs there and gives the plain path's pivots
+    and Pfaffian; one order more falls back to the plain path."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 128 * sms + 1
+    old = skew.set_lookahead(2)
+    try:
+        assert skew.lookahead_used(n, 64)
+        assert not skew.lookahead_used(n + 1, 64)
+    finally:
+        skew.set_lookahead(old)
+    A = inputs.skew_gaussian(n, 12901)
+    res = {}
+    for mode in (2, 0):
+        old = skew.set_lookahead(mode)
+        try:
+            la, sg, t, piv, info = skew.pfaffian(dev(A), nb=64)
+            torch.cuda.synchronize()
+            res[mode] = (float(la.item()), int(sg.item()), t.cpu().numpy(), piv.cpu().numpy(),
+                         int(info.item()))
+        finally:
+            skew.set_lookahead(old)
+    (la2, sg2, t2, p2, i2), (la0, sg0, t0, p0, i0) = res[2], res[0]
+    assert np.array_equal(p2, p0) and i2 == i0 == 0 and sg2 == sg0
+    assert abs(la2 - la0) <= 1e-10 * abs(la0)
+    assert np.max(np.abs(t2 - t0)) <= TOL_C * n * EPS * np.max(np.abs(t0))
