@@ -205,6 +205,14 @@ size_t skew_workspace_bytes_lookahead(int64_t n, int nb, int with_L);
  *      (a tuning knob). */
 int skew_set_lookahead(int mode);
 
+/* Turns the cluster panel on (1, the default) or off (0) for later calls of this
+ * process; returns the previous setting.  On, the plain path factors each panel whose
+ * trailing block has at most 4096 rows (and width <= 96) with one thread-block cluster
+ * of at most 16 CTAs, exchanging each column step's pivot candidates through
+ * distributed shared memory instead of global memory.  Same steps and results as the
+ * grid-wide panel (Section 5.2); the exchange is this library's. */
+int skew_set_cluster_panel(int on);
+
 /* 1 if skew_ltlt / skew_pfaffian_ex at order n, width nb (0 = default) and this
  * trailing-update precision take the look-ahead path on the current device when given
  * skew_workspace_bytes_lookahead bytes (or no workspace), else 0.  No counterpart in

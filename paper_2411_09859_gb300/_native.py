@@ -47,6 +47,7 @@ SIGNATURES = {
     "skew_workspace_bytes": ([_i64, _i32, _i32], _sz),
     "skew_workspace_bytes_lookahead": ([_i64, _i32, _i32], _sz),
     "skew_set_lookahead": ([_i32], _i32),
+    "skew_set_cluster_panel": ([_i32], _i32),
     "skew_set_nb_table_ex": ([_i32, _vp, _vp, _vp], _i32),
     "skew_lookahead_used": ([_i64, _i32, _i32], _i32),
     "skew_ltlt": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
@@ -260,6 +261,12 @@ def set_lookahead(mode) -> int:
     Returns the old setting."""
     m = int(mode) if not isinstance(mode, bool) else (1 if mode else 0)
     return int(lib().skew_set_lookahead(m))
+
+
+def set_cluster_panel(on: bool) -> bool:
+    """Use the cluster panel for narrow trailing blocks on the plain path (default on);
+    returns the old setting."""
+    return bool(lib().skew_set_cluster_panel(1 if on else 0))
 
 
 def lookahead_used(n: int, nb: int = 0, precision: int = 0) -> bool:

@@ -185,6 +185,7 @@ void la_release(int dev, const LaStreams &s) {
 }
 
 std::atomic<int> g_lookahead{1};
+std::atomic<int> g_cluster_panel{1};
 
 // Library-private stream-ordered pool: freed blocks stay reserved for reuse (release
 // threshold = max), so repeated calls do not map and unmap device memory.
@@ -248,6 +249,7 @@ int current_device_info(DeviceInfo *out) {
     di.sms = sms;
     di.panel_grid_max = sms;                       // one panel CTA per SM
     if (di.panel_grid_max > kMaxPanelGrid) di.panel_grid_max = kMaxPanelGrid;
+    SKEW_TRY_STATUS(panel_cluster_supported(&di.cluster_ok));
     std::lock_guard<std::mutex> lock(g_dev_mutex);
     g_dev[dev] = di;
     g_dev_ready[dev] = true;
@@ -290,6 +292,8 @@ LaLayout workspace_layout_la(int64_t n, int nb, bool with_L) {
     l.total = off;
     return l;
 }
+
+bool cluster_panel_enabled() { return g_cluster_panel.load() != 0; }
 
 bool lookahead_applies(int64_t n, int nb, int precision, int sms) {
     const int mode = g_lookahead.load();          // 0 off, 1 by order, 2 always, 32..128
@@ -615,7 +619,11 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
                     pb += 8.0 * (double)(n - s - 1) * 2.0;
                 }
                 ProfScope ps(kProfPanel, st, pf, pb);
-                status = launch_panel(pa, di.panel_grid_max, st);
+                if (di.cluster_ok && cluster_panel_enabled() &&
+                    panel_cluster_fits(n - k0 - 1, (int)(kend - k0)))
+                    status = launch_panel_cluster(pa, st);
+                else
+                    status = launch_panel(pa, di.panel_grid_max, st);
             }
             if (status != SKEW_OK) break;
             if (with_L && k0 >= 1) {
@@ -981,6 +989,10 @@ int skew_lookahead_used(int64_t n, int nb, int precision) {
     if (current_device_info(&di) != SKEW_OK) return 0;
     if (nb <= 0) nb = skew_default_nb(n);
     return lookahead_applies(n, nb, precision, di.sms) ? 1 : 0;
+}
+
+int skew_set_cluster_panel(int on) {
+    return g_cluster_panel.exchange(on != 0 ? 1 : 0);
 }
 
 int skew_set_lookahead(int mode) {

@@ -32,6 +32,7 @@ struct DeviceInfo {
     int device;
     int sms;              // multiprocessors
     int panel_grid_max;   // co-resident CTAs of the panel kernel (cooperative limit)
+    int cluster_ok;       // clusters of 16 panel CTAs can be resident (cluster panel)
 };
 // Properties of the current device; SKEW_ERR_NODEVICE unless it is an sm_103 part.
 int current_device_info(DeviceInfo *out);
@@ -250,6 +251,15 @@ inline bool panel_la_fits(int64_t n, int64_t k0, int sms) {
     return n - k0 - 1 <= (int64_t)sms * kLaThreads && n < 65535;
 }
 int launch_panel_la(const PanelLAArgs &a, int sms, cudaStream_t stream);
+
+// Cluster panel (panel_cluster.cu): the same panel for trailing blocks of at most
+// 16 x 256 rows and width <= 96, run by one thread-block cluster of at most 16 CTAs
+// that exchanges each step's candidates through distributed shared memory.
+bool panel_cluster_fits(int64_t rows, int width);
+int launch_panel_cluster(const PanelArgs &a, cudaStream_t stream);
+int panel_cluster_supported(int *ok);
+// Whether the plain path uses the cluster panel where it fits (skew_set_cluster_panel).
+bool cluster_panel_enabled();
 
 // Row exchanges piv[k+1] <-> k+1, k = k0 .. kend-1 in order, on L columns 1 .. k0.
 int launch_pivot_rows(int64_t n, double *L, int64_t ldl, const int32_t *piv, int k0,

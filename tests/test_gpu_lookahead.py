@@ -179,13 +179,14 @@ def test_lookahead_at_its_largest_order_and_beyond():
     thread in 128-row CTAs: the look-ahead runs there and gives the plain path's pivots
     and Pfaffian; one order more falls back to the plain path."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    n = 128 * sms + 1
     old = skew.set_lookahead(2)
     try:
-        assert skew.lookahead_used(n, 64)
-        assert not skew.lookahead_used(n + 1, 64)
+        assert skew.lookahead_used(128 * sms + 1, 64)
+        assert not skew.lookahead_used(128 * sms + 2, 64)
     finally:
         skew.set_lookahead(old)
+    # an even order (an odd one has Pf = 0) whose first panel needs every multiprocessor
+    n = 128 * sms
     A = inputs.skew_gaussian(n, 12901)
     res = {}
     for mode in (2, 0):

@@ -356,3 +356,42 @@ def test_order_beyond_one_row_per_panel_thread():
     torch.cuda.synchronize()
     assert int(sg1.item()) == int(sg2.item())
     assert abs(float(la1.item()) - float(la2.item())) <= 1e-10 * abs(float(la2.item()))
+
+
+@pytest.mark.parametrize("n,nb", [(2, 1), (40, 8), (257, 32), (1000, 64), (2050, 96), (4097, 64)])
+def test_cluster_panel_on_and_off_match_the_oracle(n, nb):
+    """The plain path's panels of trailing blocks up to 4096 rows run as one thread-block
+    cluster (candidates exchanged through distributed shared memory); with the cluster
+    panel turned off they run as the grid-wide panel.  Both reach the oracle's
+    factorization.  (The look-ahead is off here, so that every panel is a plain one.)"""
+    A = inputs.skew_gaussian(n, 13000 + n)
+    old_la = skew.set_lookahead(0)
+    try:
+        for on in (True, False):
+            old = skew.set_cluster_panel(on)
+            try:
+                assert_parity(A, nb, check_backward=(n <= 1100))
+            finally:
+                skew.set_cluster_panel(old)
+    finally:
+        skew.set_lookahead(old_la)
+
+
+def test_cluster_panel_nonfinite_leaves_together():
+    """A recorded error (here the prologue's flag for a NaN in the input) reaches every
+    CTA of a cluster panel through the first exchange, and they all leave at the same
+    point: the call returns info = -100 and the context stays usable."""
+    A = inputs.skew_gaussian(600, 14)
+    A[500, 300] = np.nan
+    A[300, 500] = np.nan
+    old_la = skew.set_lookahead(0)
+    try:
+        _, _, _, info = gpu_ltlt(A, 32)
+        assert info == -100
+        la, sg, t, piv, info = gpu_pf(A, 32)
+        assert info == -100
+        # the context is still usable
+        B = inputs.skew_gaussian(300, 15)
+        assert_parity(B, 32)
+    finally:
+        skew.set_lookahead(old_la)
