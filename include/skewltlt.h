@@ -199,7 +199,8 @@ size_t skew_workspace_bytes_lookahead(int64_t n, int nb, int with_L);
  * this library with no counterpart in the paper.
  *   0  plain path always;
  *   1  (the default) the look-ahead where the panel-width table says so for the order
- *      (skew_set_nb_table_ex), else for 3072 <= n <= 10240;
+ *      (skew_set_nb_table_ex); without a table entry, only when cluster panels are off
+ *      or cannot be resident (skew_set_cluster_panel) and 3072 <= n <= 10240;
  *   2  the look-ahead wherever it applies;
  *   32, 64  as 2, with that many rows per CTA in the look-ahead panel instead of 128
  *      (a tuning knob). */

@@ -295,12 +295,12 @@ LaLayout workspace_layout_la(int64_t n, int nb, bool with_L) {
 
 bool cluster_panel_enabled() { return g_cluster_panel.load() != 0; }
 
-bool lookahead_applies(int64_t n, int nb, int precision, int sms) {
+bool lookahead_applies(int64_t n, int nb, int precision, const DeviceInfo &di) {
     const int mode = g_lookahead.load();          // 0 off, 1 by order, 2 always, 32..128
     if (mode == 0 || precision != SKEW_PRECISION_FP64 || nb < 2 || nb > kLaMaxCols / 2 ||
-        n - 1 <= nb || !panel_la_fits(n, 0, sms))
+        n - 1 <= nb || !panel_la_fits(n, 0, di.sms))
         return false;
-    return mode != 1 || lookahead_wanted(n);
+    return mode != 1 || lookahead_wanted(n, di.cluster_ok && cluster_panel_enabled());
 }
 
 // ------------------------------------------------------------------ the factorization
@@ -522,7 +522,7 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
     DeviceInfo di;
     SKEW_TRY_STATUS(current_device_info(&di));
     if (nb == 0) nb = skew_default_nb(n);
-    if (lookahead_applies(n, nb, precision, di.sms)) {
+    if (lookahead_applies(n, nb, precision, di)) {
         const LaLayout llay = workspace_layout_la(n, nb, with_L);
         char *lb = static_cast<char *>(workspace);
         if (lb == nullptr || workspace_bytes >= llay.total) {
@@ -876,7 +876,7 @@ namespace skew {
 // 3072 <= n <= 10240 (measured on GB300: at n = 4096 / 8192 the look-ahead saves 10 % /
 // 5 %; at 2048 and from 12288 up the panel's extra FP64 work and its share of the
 // multiprocessors cost as much as the overlap saves).
-bool lookahead_wanted(int64_t n) {
+bool lookahead_wanted(int64_t n, bool cluster_panel) {
     {
         std::lock_guard<std::mutex> lock(g_nb_mutex);
         if (!g_nb_table.empty()) {
@@ -886,7 +886,9 @@ bool lookahead_wanted(int64_t n) {
             if (la >= 0) return la != 0;
         }
     }
-    return n >= 3072 && n <= 10240;
+    // Built-in rule: with cluster panels the plain path is the faster one at every
+    // order; with grid-wide panels the look-ahead wins from about 3072 to 10240.
+    return !cluster_panel && n >= 3072 && n <= 10240;
 }
 }  // namespace skew
 
@@ -988,7 +990,7 @@ int skew_lookahead_used(int64_t n, int nb, int precision) {
     DeviceInfo di;
     if (current_device_info(&di) != SKEW_OK) return 0;
     if (nb <= 0) nb = skew_default_nb(n);
-    return lookahead_applies(n, nb, precision, di.sms) ? 1 : 0;
+    return lookahead_applies(n, nb, precision, di) ? 1 : 0;
 }
 
 int skew_set_cluster_panel(int on) {

@@ -88,9 +88,10 @@ struct LaLayout {
 };
 LaLayout workspace_layout_la(int64_t n, int nb, bool with_L);
 // Whether skew_ltlt / skew_pfaffian take the look-ahead path for this order and width.
-bool lookahead_applies(int64_t n, int nb, int precision, int sms);
-// The panel-width table's (or the built-in) choice of the look-ahead for order n.
-bool lookahead_wanted(int64_t n);
+bool lookahead_applies(int64_t n, int nb, int precision, const DeviceInfo &di);
+// The panel-width table's (or the built-in) choice of the look-ahead for order n;
+// cluster_panel: the plain path's panels run as thread-block clusters.
+bool lookahead_wanted(int64_t n, bool cluster_panel);
 
 // ------------------------------------------------------------------ device helpers
 __device__ __forceinline__ uint64_t global_ns() {

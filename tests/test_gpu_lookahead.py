@@ -82,13 +82,18 @@ def test_lookahead_pfaffian_only(n, nb):
 
 
 def test_default_path_choice():
-    """Mode 1 (the default) takes the look-ahead by order: the built-in rule for
-    3072 <= n <= 10240, or the panel-width table's choice; mode 0 never."""
+    """Mode 1 (the default) takes the look-ahead by order: the panel-width table's
+    choice, else the built-in rule (never with cluster panels, 3072 <= n <= 10240 with
+    grid-wide panels); mode 0 never."""
     old = skew.set_lookahead(1)
+    old_cl = skew.set_cluster_panel(True)
     try:
         skew.set_nb_table([])
+        assert not skew.lookahead_used(4096, 64) and not skew.lookahead_used(2000, 32)
+        skew.set_cluster_panel(False)
         assert not skew.lookahead_used(2000, 32) and skew.lookahead_used(4096, 64)
         assert not skew.lookahead_used(16384, 64)
+        skew.set_cluster_panel(True)
         skew.set_nb_table([(3000, 32, 1), (20000, 64, 0)])
         assert skew.lookahead_used(2000) and not skew.lookahead_used(4096)
         assert not skew.lookahead_used(4096, 128)             # wider than 64: plain
@@ -96,6 +101,7 @@ def test_default_path_choice():
         assert not skew.lookahead_used(2000)
     finally:
         skew.set_lookahead(old)
+        skew.set_cluster_panel(old_cl)
         from paper_2411_09859_gb300 import autotune
         if not autotune.load():
             skew.set_nb_table([])
