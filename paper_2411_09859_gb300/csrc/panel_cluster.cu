@@ -9,10 +9,14 @@
 // v[k+2:] / t[k], Eq. (1)).  What differs is the per-step exchange.  There every CTA
 // publishes its best candidate in global memory with a release-stored step tag and
 // polls all the others' tags.  Here the whole grid is ONE cluster of at most 16 CTAs:
-// each CTA leaves its candidate (and its L row, and row k+1's row and v if it owns row
-// k+1) in its own shared memory, one cluster barrier makes them visible, and every CTA
-// reads them from the other CTAs' shared memory.  The cluster barrier also orders the
-// step's global writes (the exchanged entries of X) for the next step's readers.
+// each WARP leaves its best candidate and that row's L values (and the warp that owns
+// row k+1 that row's L values and v[k+1]) in its CTA's shared memory, one cluster
+// barrier makes them visible, and warp 0 of every CTA reads all the warps' candidates
+// from the other CTAs' shared memory, then the winner's L row, and forms h; one CTA
+// barrier hands the step to the other warps.  A step thus has one cluster barrier and
+// one CTA barrier, and no CTA-wide candidate reduction.  The cluster barrier also
+// orders the step's global writes (the exchanged entries of X) for the next step's
+// readers.
 //
 // Used for trailing blocks of at most 16 x 256 rows (every row of the panel has its own
 // thread), where a grid-wide exchange through L2 dominates a column step.  The
@@ -34,14 +38,20 @@ namespace {
 
 constexpr int kClMaxNb = 96;
 constexpr int kClThreads = 256;     // up to 256 rows per CTA, one per thread
+constexpr int kClWarps = kClThreads / 32;
+
+// One warp's best candidate of a step (16 bytes: read remotely in one load).
+struct __align__(16) ClusterSlot {
+    unsigned long long raw;          // bits of the signed v
+    int idx;                         // its row (INT_MAX: none)
+    int bad;                         // a non-finite v or a recorded error in this warp
+};
 
 // What a CTA shows the cluster for one step (double-buffered by step parity).
 struct ClusterPub {
-    unsigned long long raw;          // the CTA's best candidate: bits of the signed v
-    int idx;                         // its row (INT_MAX: none)
-    int bad;                         // a non-finite v or a recorded error in this CTA
+    ClusterSlot slot[kClWarps];
     double vtop;                     // v[k+1] (written by the CTA that owns row k+1)
-    double row[kClMaxNb];            // L[idx, k0+1 .. k]
+    double row[kClWarps][kClMaxNb];  // L[slot idx, k0+1 .. k] of each warp's candidate
     double rowp[kClMaxNb];           // L[k+1, k0+1 .. k] (the CTA that owns row k+1)
 };
 
@@ -49,20 +59,18 @@ __global__ void __launch_bounds__(kClThreads)
 panel_cluster_kernel(PanelArgs a) {
     extern __shared__ double s_L[];          // [q][threadIdx.x], q < kend - k0
     __shared__ ClusterPub s_pub[2];
-    __shared__ double s_h[kClMaxNb + 1];
-    __shared__ double s_t[kClMaxNb + 1];
-    __shared__ double s_w[kClMaxNb + 1];
-    __shared__ double s_rp[kClMaxNb + 1];
-    __shared__ unsigned long long s_wraw[kClThreads / 32];
-    __shared__ int s_wi[kClThreads / 32];
-    __shared__ int s_wbad[kClThreads / 32];
+    __shared__ double s_t[kClMaxNb + 1];     // t of the panel's steps so far
+    __shared__ double s_h[kClMaxNb + 1];     // h of the current step
+    __shared__ double s_w[kClMaxNb];         // the winner's L row (the new row p)
+    __shared__ double s_rp[kClMaxNb];        // row p's L row (the new row r)
     __shared__ double s_tau, s_vtop;
     __shared__ int s_r, s_win, s_fail;
 
     cg::cluster_group cluster = cg::this_cluster();
     Ctrl *ctrl = a.ctrl;
     const int n = a.n, k0 = a.k0, kend = a.kend;
-    const int G = (int)gridDim.x;                   // = the cluster size
+    const int G = (int)gridDim.x;                   // = the cluster size, a power of two
+    const int lg = __ffs(G) - 1;
     const int me = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double *X = a.X;
@@ -70,57 +78,43 @@ panel_cluster_kernel(PanelArgs a) {
     auto Lcol = [&](int q) -> double * { return a.Lp + (int64_t)(q - k0 - 1) * ldl; };
     auto sL = [&](int q) -> double & { return s_L[q * kClThreads + tid]; };
 
-    // this thread's row: chunk warp * G + cta, lane tid % 32
-    const int64_t i = (int64_t)k0 + 1 + ((int64_t)(warp * G + me) << 5) + lane;
+    // this thread's row: 32-row chunk (warp G + cta), lane tid % 32
+    const int64_t i = (int64_t)k0 + 1 + ((int64_t)((warp << lg) + me) << 5) + lane;
     const bool own = i < n;
-    auto owner_cta = [&](int row) -> int { return ((row - k0 - 1) >> 5) % G; };
+    auto owner_cta = [&](int row) -> int { return ((row - k0 - 1) >> 5) & (G - 1); };
+    auto owner_warp = [&](int row) -> int { return ((row - k0 - 1) >> 5) >> lg; };
     auto owner_tid = [&](int row) -> int {
-        const int j = row - k0 - 1;
-        return (((j >> 5) / G) << 5) + (j & 31);
+        return (owner_warp(row) << 5) | ((row - k0 - 1) & 31);
     };
     // an error recorded before this launch (read by every CTA; the first exchange
     // makes the decision uniform)
     const bool fail0 = ld_volatile_i32(&ctrl->err) != 0;
 
-    // Show this CTA's step-k candidate to the cluster: reduce over the CTA, copy the
-    // candidate's L row (and row k+1's, with v[k+1], if this CTA owns row k+1) into
-    // s_pub[k & 1], then the cluster barrier.
+    // Show this warp's step-k candidate to the cluster: its slot and its L row in
+    // s_pub[k & 1] (and row k+1's L row, if this warp owns row k+1), then the cluster
+    // barrier.  No CTA-wide reduction: the gather reads every warp's slot.
     auto publish = [&](int k, Best best, bool bad, double vtop_mine) {
+        __syncwarp();                        // this warp's s_L writes of the step
         best = warp_best_all(best);
         const int wbad = __any_sync(0xffffffffu, bad);
-        if (lane == 0) {
-            s_wraw[warp] = best.raw;
-            s_wi[warp] = best.i;
-            s_wbad[warp] = wbad;
-        }
         ClusterPub &pb = s_pub[k & 1];
-        if (own && i == k + 1) pb.vtop = vtop_mine;
-        __syncthreads();
-        if (warp == 0) {
-            Best y = no_candidate();
-            int yb = 0;
-            if (lane < kClThreads / 32) {
-                y.raw = s_wraw[lane];
-                y.i = s_wi[lane];
-                yb = s_wbad[lane];
-            }
-            y = warp_best_all(y);
-            yb = __any_sync(0xffffffffu, yb);
-            if (lane == 0) {
-                pb.raw = y.raw;
-                pb.idx = y.i;
-                pb.bad = yb;
-            }
-            const int nq = k - k0;
-            if (y.i != INT_MAX) {
-                const int ot = owner_tid(y.i);
-                for (int q = lane; q < nq; q += 32) pb.row[q] = s_L[q * kClThreads + ot];
-            }
-            if (k + 1 < n && owner_cta(k + 1) == me) {
-                const int ot = owner_tid(k + 1);
-                for (int q = lane; q < nq; q += 32) pb.rowp[q] = s_L[q * kClThreads + ot];
-            }
+        const int nq = k - k0;
+        if (lane == 0) {
+            ClusterSlot sl;
+            sl.raw = best.raw;
+            sl.idx = best.i;
+            sl.bad = wbad;
+            pb.slot[warp] = sl;
         }
+        if (best.i != INT_MAX) {
+            const int ot = owner_tid(best.i);
+            for (int q = lane; q < nq; q += 32) pb.row[warp][q] = s_L[q * kClThreads + ot];
+        }
+        if (k + 1 < n && owner_cta(k + 1) == me && owner_warp(k + 1) == warp) {
+            const int ot = owner_tid(k + 1);
+            for (int q = lane; q < nq; q += 32) pb.rowp[q] = s_L[q * kClThreads + ot];
+        }
+        if (own && i == k + 1) pb.vtop = vtop_mine;
         cluster.sync();
     };
 
@@ -140,25 +134,68 @@ panel_cluster_kernel(PanelArgs a) {
 
     bool failed = false;
     for (int k = k0; k < kend; ++k) {
-        // ---------------- the step-k candidates of the cluster (the barrier was the
-        // last one of publish); warp 0 reads them from every CTA's shared memory
+        const int p = k + 1, nq = k - k0;
+        const bool next = (k + 1 < kend);
+        const bool form_x = (!next && a.with_x);
+        double *colp = X + (int64_t)p * ldx;
+        // column p of this row does not depend on the pivot: its load goes first
+        double x_old = 0.0, xe = 0.0;
+        if (own && i > p) x_old = __ldcg(colp + i);
         if (warp == 0) {
+            // ---------------- the cluster's step-k candidates (the barrier was the last
+            // one of publish): every warp's slot of every CTA, up to four per lane
+            const ClusterPub *pp = cluster.map_shared_rank(&s_pub[k & 1], (unsigned)owner_cta(p));
+            for (int q = lane; q < nq; q += 32) s_rp[q] = pp->rowp[q];   // row p: known already
+            const double vt = pp->vtop;
             Best b = no_candidate();
             int anybad = 0;
-            for (int c = lane; c < G; c += 32) {
-                const ClusterPub *rp = cluster.map_shared_rank(&s_pub[k & 1], (unsigned)c);
-                const unsigned long long pr = rp->raw;
-                const int pi = rp->idx;
-                anybad |= rp->bad;
-                if (better(pr, pi, b.raw, b.i)) { b.raw = pr; b.i = pi; b.c = c; }
+            for (int sidx = lane; sidx < (G << 3); sidx += 32) {
+                const ClusterPub *rp = cluster.map_shared_rank(&s_pub[k & 1], (unsigned)(sidx >> 3));
+                const ClusterSlot sl = rp->slot[sidx & 7];
+                anybad |= sl.bad;
+                if (better(sl.raw, sl.idx, b.raw, b.i)) {
+                    b.raw = sl.raw;
+                    b.i = sl.idx;
+                    b.c = sidx;
+                }
             }
             anybad = __any_sync(0xffffffffu, anybad);
             b = warp_best_all(b);
+            const int r = (b.i == INT_MAX) ? p : b.i;       // all NaN: keep the diagonal
+            const int win = (b.i == INT_MAX) ? -1 : b.c;
+            const double tau = (win < 0) ? vt : as_double(b.raw);
+            if (!anybad) {
+                // the winner's L row, then h = T L[p, :]^T over columns k0+1 .. k+1
+                if (win >= 0) {
+                    const ClusterPub *wp =
+                        cluster.map_shared_rank(&s_pub[k & 1], (unsigned)(win >> 3));
+                    for (int q = lane; q < nq; q += 32) s_w[q] = wp->row[win & 7][q];
+                }
+                __syncwarp();
+                if (next || form_x) {
+                    auto tq = [&](int q) -> double { return q == k ? tau : s_t[q - k0]; };
+                    for (int q = k0 + 1 + lane; q <= k + 1; q += 32) {
+                        double hq = 0.0;
+                        if (q - 1 >= k0 + 1) hq = tq(q - 1) * s_w[q - 2 - k0];
+                        if (q + 1 <= k + 1) {
+                            const double lq1 = (q + 1 == k + 1) ? 1.0 : s_w[q - k0];
+                            hq -= tq(q) * lq1;
+                        }
+                        s_h[q - k0 - 1] = hq;
+                    }
+                }
+            }
             if (lane == 0) {
                 s_fail = anybad;
-                s_r = (b.i == INT_MAX) ? k + 1 : b.i;    // all NaN: keep the diagonal
-                s_tau = as_double(b.raw);
-                s_win = (b.i == INT_MAX) ? -1 : b.c;
+                s_r = r;
+                s_tau = tau;
+                s_vtop = vt;
+                s_win = win;
+                s_t[nq] = tau;
+                if (me == 0 && !anybad) {
+                    a.t[k] = tau;
+                    a.piv[p] = r;
+                }
             }
         }
         __syncthreads();
@@ -166,72 +203,30 @@ panel_cluster_kernel(PanelArgs a) {
             failed = true;
             break;
         }
-        const int r = s_r, p = k + 1, nq = k - k0;
-        // ---------------- the winner's row, row k+1's row and v[k+1], from the CTAs
-        // that hold them; and this thread's entries of X for the exchange
-        const int op = owner_cta(p);
-        if (s_win >= 0) {
-            const ClusterPub *wp = cluster.map_shared_rank(&s_pub[k & 1], (unsigned)s_win);
-            const ClusterPub *pp = cluster.map_shared_rank(&s_pub[k & 1], (unsigned)op);
-            for (int q = tid; q < nq; q += kClThreads) {
-                s_w[q] = wp->row[q];
-                s_rp[q] = pp->rowp[q];
-            }
-        }
-        if (tid == 0) {
-            const ClusterPub *pp = cluster.map_shared_rank(&s_pub[k & 1], (unsigned)op);
-            const double vt = pp->vtop;
-            s_vtop = vt;
-            if (s_win < 0) s_tau = vt;
-        }
-        double *colp = X + (int64_t)p * ldx;
-        double x_old = 0.0, xe = 0.0;
-        if (own && i > p) {
-            x_old = __ldcg(colp + i);
-            if (r != p) {
-                if (i < r) xe = __ldcg(X + i * ldx + r);                 // X[r, i]
-                else if (i > r) xe = __ldcg(X + (int64_t)r * ldx + i);   // X[i, r]
-            }
-        }
-        __syncthreads();
+        const int r = s_r, win = s_win;
         const double tau = s_tau, vtop = s_vtop;
-        if (tid == 0) s_t[k - k0] = tau;
-        if (me == 0 && tid == 0) {
-            a.t[k] = tau;
-            a.piv[p] = r;
+        if (own && i > p && r != p) {
+            if (i < r) xe = __ldcg(X + i * ldx + r);                 // X[r, i]
+            else if (i > r) xe = __ldcg(X + (int64_t)r * ldx + i);   // X[i, r]
         }
-        // exchanged rows of the panel's L columns k0+1..k
-        if (r != p && s_win >= 0) {
-            if (owner_cta(p) == me) {
+        // exchanged rows of the panel's L columns k0+1..k, by the warps that own them
+        if (r != p && win >= 0) {
+            if (owner_cta(p) == me && owner_warp(p) == warp) {
                 const int ot = owner_tid(p);
-                for (int q = tid; q < nq; q += kClThreads) {
+                for (int q = lane; q < nq; q += 32) {
                     s_L[q * kClThreads + ot] = s_w[q];
                     Lcol(k0 + 1 + q)[p] = s_w[q];
                 }
             }
-            if (owner_cta(r) == me) {
+            if (owner_cta(r) == me && owner_warp(r) == warp) {
                 const int ot = owner_tid(r);
-                for (int q = tid; q < nq; q += kClThreads) {
+                for (int q = lane; q < nq; q += 32) {
                     s_L[q * kClThreads + ot] = s_rp[q];
                     Lcol(k0 + 1 + q)[r] = s_rp[q];
                 }
             }
+            __syncwarp();
         }
-        const bool next = (k + 1 < kend);
-        const bool form_x = (!next && a.with_x);
-        if (next || form_x) {
-            auto tq = [&](int q) -> double { return q == k ? tau : s_t[q - k0]; };
-            for (int q = k0 + 1 + tid; q <= k + 1; q += kClThreads) {
-                double hq = 0.0;
-                if (q - 1 >= k0 + 1) hq = tq(q - 1) * s_w[q - 2 - k0];
-                if (q + 1 <= k + 1) {
-                    const double lq1 = (q + 1 == k + 1) ? 1.0 : s_w[q - k0];
-                    hq -= tq(q) * lq1;
-                }
-                s_h[q - k0 - 1] = hq;
-            }
-        }
-        __syncthreads();
 
         Best best = no_candidate();
         bool bad = false;
@@ -301,12 +296,12 @@ bool panel_cluster_fits(int64_t rows, int width) {
     return rows >= 1 && rows <= 16LL * kClThreads && width <= kClMaxNb;
 }
 
-// CTAs of a cluster panel: one per 128 rows, at most 16 (then up to 256 rows each).
+// CTAs of a cluster panel: the power of two that gives at most 128 rows each, at most
+// 16 (then up to 256 rows each).
 int cluster_grid(int64_t rows) {
-    int64_t g = (rows + 127) / 128;
-    if (g > 16) g = 16;
-    if (g < 1) g = 1;
-    return (int)g;
+    int g = 1;
+    while (g < 16 && (int64_t)g * 128 < rows) g <<= 1;
+    return g;
 }
 
 int launch_panel_cluster(const PanelArgs &a, cudaStream_t stream) {
