@@ -255,6 +255,15 @@ split_prepare_kernel(int64_t m, PairSource<KIND> src, int P, unsigned short *Zu,
     }
 }
 
+// An integer-valued FP32 |f| <= 2^22 as an int32 without a conversion instruction:
+// f + 1.5 2^23 is exact and lies in [2^23, 2^24], and its bit pattern minus that of
+// 1.5 2^23 is f.  The group sums P_2 .. P_5 (at most four slice products over 64
+// columns of digits |d| <= 128: |P_d| <= 4 * 64 * 2^14 = 2^22) take this path; it
+// relieves the conversion unit, which the other groups still use.
+__device__ __forceinline__ int small_int_of(float f) {
+    return __float_as_int(__fadd_rn(f, 12582912.0f)) - 0x4B400000;
+}
+
 // v * 2^e2 outside the normal range of the result (rare; kept out of line so that its
 // FP64 operations are not executed speculatively for every entry)
 __device__ __noinline__ double scaled_to_double_slow(long long v, int e2) {
@@ -545,13 +554,15 @@ split_tc_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
                     for (int k = 0; k < kEpiCols; ++k) {
                         const float f0 = __uint_as_float(r[0][k]), f1 = __uint_as_float(r[1][k]);
                         const float f2 = __uint_as_float(r[2][k]), f3 = __uint_as_float(r[3][k]);
-                        const long long Qa =
-                            (long long)(__float2int_rn(f0) * 256 + __float2int_rn(f1));
-                        if (h == 0) {
+                        if (h == 0) {                // P_2 .. P_5: |P_d| <= 2^22
+                            const long long Qa =
+                                (long long)(small_int_of(f0) * 256 + small_int_of(f1));
                             const long long Qb =
-                                (long long)(__float2int_rn(f2) * 256 + __float2int_rn(f3));
+                                (long long)(small_int_of(f2) * 256 + small_int_of(f3));
                             acc[k] = (Qa << 34) + (Qb << 18);
                         } else {
+                            const long long Qa =
+                                (long long)(__float2int_rn(f0) * 256 + __float2int_rn(f1));
                             acc[k] += (Qa << 2) +
                                       (long long)__float2int_rd(fmaf(f2, 256.0f, f3) * 0x1p-14f);
                         }

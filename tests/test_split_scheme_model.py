@@ -73,6 +73,7 @@ def check_rows(a_i, w_i, a_j, w_j):
     for dig in du + dv:
         assert all(-128 <= x <= 127 for x in dig[1:]) and abs(dig[0]) <= 128
     assert all(abs(p) < 2 ** 24 for p in P.values())          # exact FP32 sums
+    assert all(abs(P[d]) <= 2 ** 22 for d in (2, 3, 4, 5))     # the add-based conversion
     Ru = max(abs(x) for x in u)
     Rv = max(abs(x) for x in v)
     bound = Fraction(2.02 * k + 0.5) * Fraction(2) ** -53 * Fraction(Ru) * Fraction(Rv)
@@ -119,3 +120,19 @@ def test_digit_recomposition_and_range():
         d = digits(X)
         assert sum(d[s] * 256 ** (6 - s) for s in range(7)) == X
         assert abs(d[0]) <= 128 and all(-128 <= x <= 127 for x in d[1:])
+
+
+def test_add_based_conversion_of_small_group_sums():
+    """The epilogue turns the group sums P_2 .. P_5 (integers, |P_d| <= 2^22) into int32
+    by one FP32 add of 1.5 2^23 and a subtraction of bit patterns; in IEEE single
+    precision with rounding to nearest that is exact on the whole range, ends included."""
+    magic = np.float32(12582912.0)
+    vals = np.concatenate([np.arange(-2 ** 22, -2 ** 22 + 5000), np.arange(-3000, 3000),
+                           np.arange(2 ** 22 - 5000, 2 ** 22 + 1),
+                           np.random.default_rng(9).integers(-2 ** 22, 2 ** 22 + 1, 20000)])
+    f = vals.astype(np.float32)
+    assert np.array_equal(f.astype(np.int64), vals)                 # exact FP32 integers
+    got = (f + magic).view(np.int32).astype(np.int64) - 0x4B400000
+    assert np.array_equal(got, vals)
+    # just outside the range the trick is no longer exact
+    assert ((np.float32(2 ** 22 + 1) + magic).view(np.int32) - 0x4B400000) != 2 ** 22 + 1
