@@ -39,6 +39,7 @@ namespace {
 constexpr int kClMaxNb = 96;
 constexpr int kClThreads = 256;     // up to 256 rows per CTA, one per thread
 constexpr int kClWarps = kClThreads / 32;
+constexpr int kClLds = kClThreads + 1;  // s_L column stride: a row's entries in distinct banks
 
 // One warp's best candidate of a step (16 bytes: read remotely in one load).
 struct __align__(16) ClusterSlot {
@@ -57,7 +58,7 @@ struct ClusterPub {
 
 __global__ void __launch_bounds__(kClThreads)
 panel_cluster_kernel(PanelArgs a) {
-    extern __shared__ double s_L[];          // [q][threadIdx.x], q < kend - k0
+    extern __shared__ double s_L[];          // [q * kClLds + threadIdx.x], q < kend - k0
     __shared__ ClusterPub s_pub[2];
     __shared__ double s_t[kClMaxNb + 1];     // t of the panel's steps so far
     __shared__ double s_h[kClMaxNb + 1];     // h of the current step
@@ -76,7 +77,7 @@ panel_cluster_kernel(PanelArgs a) {
     double *X = a.X;
     const int64_t ldx = a.ldx, ldl = a.ldl;
     auto Lcol = [&](int q) -> double * { return a.Lp + (int64_t)(q - k0 - 1) * ldl; };
-    auto sL = [&](int q) -> double & { return s_L[q * kClThreads + tid]; };
+    auto sL = [&](int q) -> double & { return s_L[q * kClLds + tid]; };
 
     // this thread's row: 32-row chunk (warp G + cta), lane tid % 32
     const int64_t i = (int64_t)k0 + 1 + ((int64_t)((warp << lg) + me) << 5) + lane;
@@ -108,11 +109,11 @@ panel_cluster_kernel(PanelArgs a) {
         }
         if (best.i != INT_MAX) {
             const int ot = owner_tid(best.i);
-            for (int q = lane; q < nq; q += 32) pb.row[warp][q] = s_L[q * kClThreads + ot];
+            for (int q = lane; q < nq; q += 32) pb.row[warp][q] = s_L[q * kClLds + ot];
         }
         if (k + 1 < n && owner_cta(k + 1) == me && owner_warp(k + 1) == warp) {
             const int ot = owner_tid(k + 1);
-            for (int q = lane; q < nq; q += 32) pb.rowp[q] = s_L[q * kClThreads + ot];
+            for (int q = lane; q < nq; q += 32) pb.rowp[q] = s_L[q * kClLds + ot];
         }
         if (own && i == k + 1) pb.vtop = vtop_mine;
         cluster.sync();
@@ -147,16 +148,30 @@ panel_cluster_kernel(PanelArgs a) {
             const ClusterPub *pp = cluster.map_shared_rank(&s_pub[k & 1], (unsigned)owner_cta(p));
             for (int q = lane; q < nq; q += 32) s_rp[q] = pp->rowp[q];   // row p: known already
             const double vt = pp->vtop;
+            // all remote loads first (G <= 16: at most four slots per lane), then compare
+            ClusterSlot sl[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int sidx = lane + 32 * u;
+                if (sidx < (G << 3)) {
+                    const ClusterPub *rp =
+                        cluster.map_shared_rank(&s_pub[k & 1], (unsigned)(sidx >> 3));
+                    sl[u] = rp->slot[sidx & 7];
+                } else {
+                    sl[u].raw = 0ull;
+                    sl[u].idx = INT_MAX;
+                    sl[u].bad = 0;
+                }
+            }
             Best b = no_candidate();
             int anybad = 0;
-            for (int sidx = lane; sidx < (G << 3); sidx += 32) {
-                const ClusterPub *rp = cluster.map_shared_rank(&s_pub[k & 1], (unsigned)(sidx >> 3));
-                const ClusterSlot sl = rp->slot[sidx & 7];
-                anybad |= sl.bad;
-                if (better(sl.raw, sl.idx, b.raw, b.i)) {
-                    b.raw = sl.raw;
-                    b.i = sl.idx;
-                    b.c = sidx;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                anybad |= sl[u].bad;
+                if (better(sl[u].raw, sl[u].idx, b.raw, b.i)) {
+                    b.raw = sl[u].raw;
+                    b.i = sl[u].idx;
+                    b.c = lane + 32 * u;
                 }
             }
             anybad = __any_sync(0xffffffffu, anybad);
@@ -214,14 +229,14 @@ panel_cluster_kernel(PanelArgs a) {
             if (owner_cta(p) == me && owner_warp(p) == warp) {
                 const int ot = owner_tid(p);
                 for (int q = lane; q < nq; q += 32) {
-                    s_L[q * kClThreads + ot] = s_w[q];
+                    s_L[q * kClLds + ot] = s_w[q];
                     Lcol(k0 + 1 + q)[p] = s_w[q];
                 }
             }
             if (owner_cta(r) == me && owner_warp(r) == warp) {
                 const int ot = owner_tid(r);
                 for (int q = lane; q < nq; q += 32) {
-                    s_L[q * kClThreads + ot] = s_rp[q];
+                    s_L[q * kClLds + ot] = s_rp[q];
                     Lcol(k0 + 1 + q)[r] = s_rp[q];
                 }
             }
@@ -309,10 +324,10 @@ int launch_panel_cluster(const PanelArgs &a, cudaStream_t stream) {
     const int width = a.kend - a.k0;
     if (!panel_cluster_fits(rows, width)) return SKEW_ERR_CUDA;
     const int g = cluster_grid(rows);
-    const size_t smem = (size_t)(width > 0 ? width : 1) * kClThreads * sizeof(double);
+    const size_t smem = (size_t)(width > 0 ? width : 1) * kClLds * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute((const void *)panel_cluster_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kClMaxNb * kClThreads * sizeof(double)));
+                                         (int)(kClMaxNb * kClLds * sizeof(double)));
     if (e == cudaSuccess && g > 8)
         e = cudaFuncSetAttribute((const void *)panel_cluster_kernel,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -348,7 +363,7 @@ int panel_cluster_supported(int *ok) {
     *ok = 0;
     cudaError_t e = cudaFuncSetAttribute((const void *)panel_cluster_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kClMaxNb * kClThreads * sizeof(double)));
+                                         (int)(kClMaxNb * kClLds * sizeof(double)));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute((const void *)panel_cluster_kernel,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -359,7 +374,7 @@ int panel_cluster_supported(int *ok) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16);
     cfg.blockDim = dim3(kClThreads);
-    cfg.dynamicSmemBytes = (size_t)kClMaxNb * kClThreads * sizeof(double);
+    cfg.dynamicSmemBytes = (size_t)kClMaxNb * kClLds * sizeof(double);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 16;
