@@ -239,10 +239,11 @@ panel_global_kernel(PanelArgs a) {
 // CTAs and each warp's accesses to a column are coalesced.
 // ------------------------------------------------------------------------------------
 constexpr int kSmemMaxNb = 96;
+constexpr int kSmemLds = kPanelThreads + 1;   // s_L column stride: a row's entries in distinct banks
 
 __global__ void __launch_bounds__(kPanelThreads)
 panel_smem_kernel(PanelArgs a) {
-    extern __shared__ double s_L[];          // [q][threadIdx.x], q < kend - k0
+    extern __shared__ double s_L[];          // [q * kSmemLds + threadIdx.x], q < kend - k0
     __shared__ double s_h[kSmemMaxNb + 1];   // h of the next step, index q - k0 - 1
     __shared__ double s_t[kSmemMaxNb + 1];   // t[k] of this panel, index k - k0
     __shared__ double s_w[kSmemMaxNb + 1];   // new L row k+1 (old row r), index c - k0 - 1
@@ -263,7 +264,7 @@ panel_smem_kernel(PanelArgs a) {
     auto slot = [&](int k, int cta) -> ArgmaxPartial * {
         return a.part + (k & 1) * kMaxPanelGrid + cta;
     };
-    auto sL = [&](int q) -> double & { return s_L[q * kPanelThreads + tid]; };
+    auto sL = [&](int q) -> double & { return s_L[q * kSmemLds + tid]; };
 
     // this thread's row: chunk (tid / 32) * G + cta, lane tid % 32
     const int64_t i = (int64_t)k0 + 1 + ((int64_t)((tid >> 5) * G + (int)blockIdx.x) << 5) + (tid & 31);
@@ -308,11 +309,11 @@ panel_smem_kernel(PanelArgs a) {
         const int nq = k - k0;
         if (y.i != INT_MAX) {
             const int ot = owner_tid(y.i);
-            for (int q = lane; q < nq; q += 32) sp->row[q] = s_L[q * kPanelThreads + ot];
+            for (int q = lane; q < nq; q += 32) sp->row[q] = s_L[q * kSmemLds + ot];
         }
         if (k + 1 < n && owner_cta(k + 1) == (int)blockIdx.x) {
             const int ot = owner_tid(k + 1);
-            for (int q = lane; q < nq; q += 32) ctrl->rowp[k & 1][q] = s_L[q * kPanelThreads + ot];
+            for (int q = lane; q < nq; q += 32) ctrl->rowp[k & 1][q] = s_L[q * kSmemLds + ot];
         }
         // release: the CTA's writes before the barrier and warp 0's copies (ordered by
         // __syncwarp) become visible to any CTA that sees the tag; candidate and tag
@@ -444,14 +445,14 @@ panel_smem_kernel(PanelArgs a) {
             if (owner_cta(p) == (int)blockIdx.x) {
                 const int ot = owner_tid(p);
                 for (int q = tid; q < nq; q += blockDim.x) {
-                    s_L[q * kPanelThreads + ot] = s_w[q];
+                    s_L[q * kSmemLds + ot] = s_w[q];
                     Lcol(k0 + 1 + q)[p] = s_w[q];
                 }
             }
             if (owner_cta(r) == (int)blockIdx.x) {
                 const int ot = owner_tid(r);
                 for (int q = tid; q < nq; q += blockDim.x) {
-                    s_L[q * kPanelThreads + ot] = s_rp[q];
+                    s_L[q * kSmemLds + ot] = s_rp[q];
                     Lcol(k0 + 1 + q)[r] = s_rp[q];
                 }
             }
@@ -551,7 +552,7 @@ int launch_panel(const PanelArgs &a, int sms, cudaStream_t stream) {
         const int64_t g = panel_grid(rows, sms);
         // (the dynamic shared-memory limit was raised when the device was first used,
         // in panel_max_blocks_per_sm)
-        const size_t smem = (size_t)width * kPanelThreads * sizeof(double);
+        const size_t smem = (size_t)width * kSmemLds * sizeof(double);
         e = cudaLaunchCooperativeKernel((const void *)panel_smem_kernel, dim3((unsigned)g),
                                         dim3(kPanelThreads), params, smem, stream);
     } else {
@@ -573,13 +574,13 @@ int panel_max_blocks_per_sm(int *out) {
     int a = 0, b = 0;
     cudaError_t e = cudaFuncSetAttribute((const void *)panel_smem_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kSmemMaxNb * kPanelThreads * sizeof(double)));
+                                         (int)(kSmemMaxNb * kSmemLds * sizeof(double)));
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, panel_global_kernel,
                                                           kPanelThreads, 0);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &b, panel_smem_kernel, kPanelThreads, kSmemMaxNb * kPanelThreads * sizeof(double));
+            &b, panel_smem_kernel, kPanelThreads, kSmemMaxNb * kSmemLds * sizeof(double));
     if (e != cudaSuccess) {
         set_last_error(e);
         return SKEW_ERR_CUDA;
