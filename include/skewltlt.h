@@ -199,12 +199,21 @@ size_t skew_workspace_bytes_lookahead(int64_t n, int nb, int with_L);
  * this library with no counterpart in the paper.
  *   0  plain path always;
  *   1  (the default) the look-ahead where the panel-width table says so for the order
- *      (skew_set_nb_table_ex); without a table entry, only when cluster panels are off
- *      or cannot be resident (skew_set_cluster_panel) and 3072 <= n <= 10240;
+ *      (skew_set_nb_table_ex); without a table entry, for 3072 <= n <= 5120 with
+ *      cluster panels (skew_set_cluster_panel) and 3072 <= n <= 10240 without;
  *   2  the look-ahead wherever it applies;
  *   32, 64  as 2, with that many rows per CTA in the look-ahead panel instead of 128
  *      (a tuning knob). */
 int skew_set_lookahead(int mode);
+
+/* Sets the trailing order below which a look-ahead factorization goes on without the
+ * look-ahead: once the next trailing update is smaller than `rows`, that update is the
+ * last out-of-place one and the remaining blocks are factored as on the plain path, in
+ * place on its result (the panel of such a block costs more than the update it would
+ * hide).  Returns the previous value; -1 (the default) means 80 x the panel width, 0
+ * keeps the look-ahead to the end.  A schedule of this library, no counterpart in the
+ * paper; results as on the plain path. */
+long long skew_set_lookahead_switch(long long rows);
 
 /* Turns the cluster panel on (1, the default) or off (0) for later calls of this
  * process; returns the previous setting.  On, the plain path factors each panel whose

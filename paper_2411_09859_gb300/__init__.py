@@ -16,13 +16,13 @@ from __future__ import annotations
 from ._native import (SkewError, fortran_empty, kernel_launches, lib, ltlt, ltlt_host,
                       ltlt_host_timing,
                       pfaffian, pfaffian_twostep, pfaffian_from_factors, rank2k, tridiag_rankk,
-                      default_nb, set_nb_table, set_batched_nb_table, batched_nb, batched_warp_tile, set_batched_threads, workspace_bytes, set_lookahead, set_cluster_panel, lookahead_used, trim_memory, pool_usage, STATUS, profile_enable,
+                      default_nb, set_nb_table, set_batched_nb_table, batched_nb, batched_warp_tile, set_batched_threads, workspace_bytes, set_lookahead, set_cluster_panel, set_lookahead_switch, lookahead_used, trim_memory, pool_usage, STATUS, profile_enable,
                       profile_read, ltlt_batched, pfaffian_batched, batched_workspace_bytes, problem_table, BATCH_MAX_N, Server,
                       PRECISION_FP64, PRECISION_SPLIT_BF16)
 
 __all__ = ["SkewError", "fortran_empty", "kernel_launches", "lib", "ltlt", "ltlt_host",
            "ltlt_host_timing",
            "pfaffian", "pfaffian_twostep", "pfaffian_from_factors", "rank2k", "tridiag_rankk", "default_nb", "set_nb_table", "set_batched_nb_table", "batched_nb", "batched_warp_tile", "set_batched_threads",
-           "workspace_bytes", "set_lookahead", "set_cluster_panel", "lookahead_used", "trim_memory", "pool_usage", "STATUS", "profile_enable", "profile_read",
+           "workspace_bytes", "set_lookahead", "set_cluster_panel", "set_lookahead_switch", "lookahead_used", "trim_memory", "pool_usage", "STATUS", "profile_enable", "profile_read",
            "ltlt_batched", "pfaffian_batched", "batched_workspace_bytes", "problem_table", "BATCH_MAX_N", "Server", "PRECISION_FP64",
            "PRECISION_SPLIT_BF16"]

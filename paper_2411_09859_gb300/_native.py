@@ -48,6 +48,7 @@ SIGNATURES = {
     "skew_workspace_bytes_lookahead": ([_i64, _i32, _i32], _sz),
     "skew_set_lookahead": ([_i32], _i32),
     "skew_set_cluster_panel": ([_i32], _i32),
+    "skew_set_lookahead_switch": ([ctypes.c_longlong], ctypes.c_longlong),
     "skew_set_nb_table_ex": ([_i32, _vp, _vp, _vp], _i32),
     "skew_lookahead_used": ([_i64, _i32, _i32], _i32),
     "skew_ltlt": ([_i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
@@ -267,6 +268,13 @@ def set_cluster_panel(on: bool) -> bool:
     """Use the cluster panel for narrow trailing blocks on the plain path (default on);
     returns the old setting."""
     return bool(lib().skew_set_cluster_panel(1 if on else 0))
+
+
+def set_lookahead_switch(rows: int) -> int:
+    """Trailing order below which a look-ahead factorization goes on without the
+    look-ahead (skew_set_lookahead_switch; -1: the default, 80 x the panel width).
+    Returns the old setting."""
+    return int(lib().skew_set_lookahead_switch(int(rows)))
 
 
 def lookahead_used(n: int, nb: int = 0, precision: int = 0) -> bool:

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB_PATH = os.path.join(PKG, "libskewltlt.so")
-SOURCES = ["api.cu", "panel.cu", "panel_la.cu", "panel_cluster.cu", "skr2k.cu", "aux_kernels.cu", "noalloc.cu", "batched.cu", "server.cu", "skr2k_split.cu", "twostep.cu"]
+SOURCES = ["api.cu", "panel.cu", "panel_la.cu", "panel_cluster.cu", "panel_la_cluster.cu", "skr2k.cu", "aux_kernels.cu", "noalloc.cu", "batched.cu", "server.cu", "skr2k_split.cu", "twostep.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

@@ -185,6 +185,8 @@ void la_release(int dev, const LaStreams &s) {
 }
 
 std::atomic<int> g_lookahead{1};
+// Trailing order below which a look-ahead factorization goes on without it (-1: 80 nb)
+std::atomic<long long> g_la_switch{-1};
 std::atomic<int> g_cluster_panel{1};
 
 // Library-private stream-ordered pool: freed blocks stay reserved for reuse (release
@@ -250,6 +252,7 @@ int current_device_info(DeviceInfo *out) {
     di.panel_grid_max = sms;                       // one panel CTA per SM
     if (di.panel_grid_max > kMaxPanelGrid) di.panel_grid_max = kMaxPanelGrid;
     SKEW_TRY_STATUS(panel_cluster_supported(&di.cluster_ok));
+    SKEW_TRY_STATUS(panel_la_cluster_supported(&di.cluster_la_ok));
     std::lock_guard<std::mutex> lock(g_dev_mutex);
     g_dev[dev] = di;
     g_dev_ready[dev] = true;
@@ -305,6 +308,79 @@ bool lookahead_applies(int64_t n, int nb, int precision, const DeviceInfo &di) {
 
 // ------------------------------------------------------------------ the factorization
 namespace {
+
+// The blocks from s on, factored like the plain path (panel, pivot_rows beside the
+// next update, in-place fused update) on the state X = S_j left by the last look-ahead
+// update.  Column s of X is the last look-ahead panel's updated column (kept by
+// position in xlast), which that update does not write.
+int factor_rest_plain(int64_t n, double *X, int64_t ldx, int64_t s, const double *xlast,
+                      int64_t jnext, double *L, int64_t ldl, double *const *lbuf, bool with_L,
+                      double *t, int32_t *piv, Ctrl *ctrl, ArgmaxPartial *part, int nb,
+                      cudaStream_t st, LaStreams &ls, const DeviceInfo &di) {
+    cudaError_t e = cudaMemcpyAsync(X + (s + 1) + s * ldx, xlast + (s + 1),
+                                    sizeof(double) * (size_t)(n - s - 1),
+                                    cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) { set_last_error(e); return SKEW_ERR_CUDA; }
+    int status = SKEW_OK;
+    int64_t jj = jnext;
+    for (int64_t k0 = s; k0 < n - 1 && status == SKEW_OK; ++jj) {
+        const int64_t kend = (k0 + nb < n - 1) ? k0 + nb : n - 1;
+        const bool with_x = kend < n - 1;
+        PanelArgs pa;
+        pa.X = X;
+        pa.ldx = ldx;
+        pa.Lp = with_L ? L + (k0 + 1) * ldl : lbuf[jj & 1];
+        pa.ldl = with_L ? ldl : n;
+        pa.t = t;
+        pa.piv = piv;
+        pa.ctrl = ctrl;
+        pa.part = part;
+        pa.n = (int)n;
+        pa.k0 = (int)k0;
+        pa.kend = (int)kend;
+        pa.with_x = with_x ? 1 : 0;
+        {
+            double pf = 0.0;
+            for (int64_t k = k0; k < kend; ++k) pf += 2.0 * (double)(n - k - 1) * (double)(k - k0);
+            ProfScope ps(kProfPanel, st, pf, 8.0 * 6.0 * (double)(n - k0) * (double)(kend - k0));
+            if (di.cluster_ok && cluster_panel_enabled() &&
+                panel_cluster_fits(n - k0 - 1, (int)(kend - k0)))
+                status = launch_panel_cluster(pa, st);
+            else
+                status = launch_panel(pa, di.panel_grid_max, st);
+        }
+        if (status != SKEW_OK) break;
+        if (with_L && k0 >= 1) {
+            e = cudaEventRecord(ls.fork, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ls.rows, ls.fork, 0);
+            if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+            ProfScope ps(kProfPivotRows, ls.rows, 0.0,
+                         4.0 * 8.0 * (double)k0 * (double)(kend - k0));
+            status = launch_pivot_rows(n, L, ldl, piv, (int)k0, (int)kend, ls.rows);
+            if (status != SKEW_OK) break;
+        }
+        if (with_x) {
+            Skr2kArgs sa;
+            sa.m = n - kend - 1;
+            sa.C = X + (kend + 1) + (kend + 1) * ldx;
+            sa.ldc = ldx;
+            sa.alpha = 1.0;
+            sa.beta = 1.0;
+            sa.P = pa.Lp + (kend + 1);
+            sa.ldp = pa.ldl;
+            sa.Q = nullptr;
+            sa.ldq = 0;
+            sa.tt = t + k0 + 1;
+            sa.x = X + (kend + 1) + kend * ldx;
+            sa.b = kend - k0;
+            ProfScope ps(kProfSkr2k, st, skr2k_flops(sa.m, sa.b / 2 + (sa.b & 1)),
+                         skr2k_bytes(sa.m));
+            status = launch_skr2k(PairKind::Fused, sa, st);
+        }
+        k0 = kend;
+    }
+    return status;
+}
 
 // The blocked factorization with look-ahead: the panel of block j+1 runs on its own
 // stream beside the trailing update of block j.  It reads the state S_{j-1} before
@@ -374,6 +450,15 @@ int factor_la(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double 
                 pb += 8.0 * rows * 2.0;
             }
         };
+        // a look-ahead panel as one cluster where it fits, else grid-wide
+        auto launch_la_panel = [&](const PanelLAArgs &pa) -> int {
+            const int64_t rows = n - (int64_t)pa.k0 - 1;
+            const int cols = (pa.k0 - pa.kb) + (pa.kend - pa.k0);
+            if (di.cluster_la_ok && cluster_panel_enabled() && pa.rows_per_cta == 0 &&
+                panel_la_cluster_fits(rows, cols))
+                return launch_panel_la_cluster(pa, ls.panel);
+            return launch_panel_la(pa, di.sms, ls.panel);
+        };
         // panel 0: the first block, from A itself
         int64_t k0 = 0, kend = (nb < n - 1) ? nb : n - 1;
         {
@@ -401,7 +486,7 @@ int factor_la(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double 
             double pf, pb;
             panel_prof(0, 0, kend, pa.with_x != 0, pf, pb);
             ProfScope ps(kProfPanel, ls.panel, pf, pb);
-            status = launch_panel_la(pa, di.sms, ls.panel);
+            status = launch_la_panel(pa);
         }
         if (status != SKEW_OK) break;
         e = cudaEventRecord(ls.panel_done, ls.panel);
@@ -410,10 +495,71 @@ int factor_la(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double 
         for (int64_t j = 0;; ++j) {
             const int64_t s = kend;                  // this block: k0 .. kend-1
             const bool has_update = s < n - 1;
+            // The waits on panel j come first (they capture its event before panel j+1
+            // records it again); panel j+1 is submitted before update j, so that the
+            // panel (a high-priority stream, possibly one thread-block cluster) is
+            // placed before the update's CTAs fill the multiprocessors.
             if (has_update) {
-                // ---- update j: S_j = (S_{j-1} through block j's exchanges) + pairs
                 e = cudaStreamWaitEvent(st, ls.panel_done, 0);
                 if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+            }
+            // ---- pivot_rows of panel j on L columns 1 .. k0
+            if (with_L && k0 >= 1) {
+                e = cudaStreamWaitEvent(ls.rows, ls.panel_done, 0);
+                if (e == cudaSuccess && j >= 1)
+                    e = cudaStreamWaitEvent(ls.rows, ls.upd_done[(j - 1) & 1], 0);
+                if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+                ProfScope ps(kProfPivotRows, ls.rows, 0.0,
+                             4.0 * 8.0 * (double)k0 * (double)(kend - k0));
+                status = launch_pivot_rows(n, L, ldl, piv, (int)k0, (int)kend, ls.rows);
+                if (status != SKEW_OK) break;
+            }
+            if (!has_update) break;
+            // Below the switch order the panel of a block costs more than the update it
+            // would hide: update j is the last look-ahead update, and the remaining blocks
+            // are factored like the plain path, in place on S_j.
+            const long long sw = g_la_switch.load();
+            const bool la_next = (n - s - 1) > (sw < 0 ? 80LL * nb : sw);
+            // ---- panel j+1, beside update j: reads S_{j-1}
+            const int64_t k0n = kend, kendn = (kend + nb < n - 1) ? kend + nb : n - 1;
+            if (la_next && j >= 1) {
+                e = cudaStreamWaitEvent(ls.panel, ls.upd_done[(j - 1) & 1], 0);
+                if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+            }
+            if (la_next) {
+                PanelLAArgs pa;
+                pa.S = sbuf(j - 1);
+                pa.lds = sld(j - 1);
+                pa.map_prev = maps[j & 1];
+                pa.xprev = xs[j & 1];
+                pa.Lprev = lblock(k0, j);
+                pa.ldlp = lld;
+                pa.Lp = lblock(k0n, j + 1);
+                pa.ldl = lld;
+                pa.t = t;
+                pa.piv = piv;
+                pa.map_out = maps[(j + 1) & 1];
+                pa.xout = xs[(j + 1) & 1];
+                pa.ctrl = ctrl;
+                pa.part = part;
+                pa.n = (int)n;
+                pa.kb = (int)k0;
+                pa.k0 = (int)k0n;
+                pa.kend = (int)kendn;
+                pa.with_x = kendn < n - 1 ? 1 : 0;
+                pa.rows_per_cta = g_lookahead.load() > 2 ? g_lookahead.load() : 0;
+                {
+                    double pf, pb;
+                    panel_prof(k0, k0n, kendn, pa.with_x != 0, pf, pb);
+                    ProfScope ps(kProfPanel, ls.panel, pf, pb);
+                    status = launch_la_panel(pa);
+                }
+                if (status != SKEW_OK) break;
+                e = cudaEventRecord(ls.panel_done, ls.panel);
+                if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
+            }
+            if (has_update) {
+                // ---- update j: S_j = (S_{j-1} through block j's exchanges) + pairs
                 Skr2kArgs sa;
                 sa.m = n - s - 1;
                 double *dst = sbuf(j);
@@ -442,54 +588,11 @@ int factor_la(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double 
                 e = cudaEventRecord(ls.upd_done[j & 1], st);
                 if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
             }
-            // ---- pivot_rows of panel j on L columns 1 .. k0
-            if (with_L && k0 >= 1) {
-                e = cudaStreamWaitEvent(ls.rows, ls.panel_done, 0);
-                if (e == cudaSuccess && j >= 1)
-                    e = cudaStreamWaitEvent(ls.rows, ls.upd_done[(j - 1) & 1], 0);
-                if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
-                ProfScope ps(kProfPivotRows, ls.rows, 0.0,
-                             4.0 * 8.0 * (double)k0 * (double)(kend - k0));
-                status = launch_pivot_rows(n, L, ldl, piv, (int)k0, (int)kend, ls.rows);
-                if (status != SKEW_OK) break;
+            if (!la_next) {
+                status = factor_rest_plain(n, sbuf(j), sld(j), s, xs[j & 1], j + 1, L, ldl,
+                                           lbuf, with_L, t, piv, ctrl, part, nb, st, ls, di);
+                break;
             }
-            if (!has_update) break;
-            // ---- panel j+1, beside update j: reads S_{j-1}
-            const int64_t k0n = kend, kendn = (kend + nb < n - 1) ? kend + nb : n - 1;
-            if (j >= 1) {
-                e = cudaStreamWaitEvent(ls.panel, ls.upd_done[(j - 1) & 1], 0);
-                if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
-            }
-            PanelLAArgs pa;
-            pa.S = sbuf(j - 1);
-            pa.lds = sld(j - 1);
-            pa.map_prev = maps[j & 1];
-            pa.xprev = xs[j & 1];
-            pa.Lprev = lblock(k0, j);
-            pa.ldlp = lld;
-            pa.Lp = lblock(k0n, j + 1);
-            pa.ldl = lld;
-            pa.t = t;
-            pa.piv = piv;
-            pa.map_out = maps[(j + 1) & 1];
-            pa.xout = xs[(j + 1) & 1];
-            pa.ctrl = ctrl;
-            pa.part = part;
-            pa.n = (int)n;
-            pa.kb = (int)k0;
-            pa.k0 = (int)k0n;
-            pa.kend = (int)kendn;
-            pa.with_x = kendn < n - 1 ? 1 : 0;
-            pa.rows_per_cta = g_lookahead.load() > 2 ? g_lookahead.load() : 0;
-            {
-                double pf, pb;
-                panel_prof(k0, k0n, kendn, pa.with_x != 0, pf, pb);
-                ProfScope ps(kProfPanel, ls.panel, pf, pb);
-                status = launch_panel_la(pa, di.sms, ls.panel);
-            }
-            if (status != SKEW_OK) break;
-            e = cudaEventRecord(ls.panel_done, ls.panel);
-            if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
             k0 = k0n;
             kend = kendn;
         }
@@ -886,9 +989,10 @@ bool lookahead_wanted(int64_t n, bool cluster_panel) {
             if (la >= 0) return la != 0;
         }
     }
-    // Built-in rule: with cluster panels the plain path is the faster one at every
-    // order; with grid-wide panels the look-ahead wins from about 3072 to 10240.
-    return !cluster_panel && n >= 3072 && n <= 10240;
+    // Built-in rule (measured on GB300): with cluster panels the look-ahead (its panels
+    // also clusters, up to the switch order) wins around n = 4096 and loses at 2048 and
+    // 8192; with grid-wide panels it wins from about 3072 to 10240.
+    return cluster_panel ? (n >= 3072 && n <= 5120) : (n >= 3072 && n <= 10240);
 }
 }  // namespace skew
 
@@ -995,6 +1099,10 @@ int skew_lookahead_used(int64_t n, int nb, int precision) {
 
 int skew_set_cluster_panel(int on) {
     return g_cluster_panel.exchange(on != 0 ? 1 : 0);
+}
+
+long long skew_set_lookahead_switch(long long rows) {
+    return g_la_switch.exchange(rows < 0 ? -1 : rows);
 }
 
 int skew_set_lookahead(int mode) {

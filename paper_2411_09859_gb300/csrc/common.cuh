@@ -33,6 +33,7 @@ struct DeviceInfo {
     int sms;              // multiprocessors
     int panel_grid_max;   // co-resident CTAs of the panel kernel (cooperative limit)
     int cluster_ok;       // clusters of 16 panel CTAs can be resident (cluster panel)
+    int cluster_la_ok;    // the same for the look-ahead cluster panel
 };
 // Properties of the current device; SKEW_ERR_NODEVICE unless it is an sm_103 part.
 int current_device_info(DeviceInfo *out);
@@ -259,6 +260,11 @@ int launch_panel_la(const PanelLAArgs &a, int sms, cudaStream_t stream);
 bool panel_cluster_fits(int64_t rows, int width);
 int launch_panel_cluster(const PanelArgs &a, cudaStream_t stream);
 int panel_cluster_supported(int *ok);
+// Look-ahead panel as one cluster (panel_la_cluster.cu): trailing blocks of at most
+// 16 x 256 rows and at most 96 L columns over both blocks.
+bool panel_la_cluster_fits(int64_t rows, int cols);
+int launch_panel_la_cluster(const PanelLAArgs &a, cudaStream_t stream);
+int panel_la_cluster_supported(int *ok);
 // Whether the plain path uses the cluster panel where it fits (skew_set_cluster_panel).
 bool cluster_panel_enabled();
 

@@ -27,9 +27,11 @@ def dev(A):
     return torch.from_numpy(np.asfortranarray(A, dtype=np.float64)).cuda()
 
 
-def factor(A, nb, lookahead, workspace=None, with_L=True):
-    # 2: the look-ahead wherever it applies (the default, 1, takes it by order only)
+def factor(A, nb, lookahead, workspace=None, with_L=True, switch=0):
+    # 2: the look-ahead wherever it applies (the default, 1, takes it by order only);
+    # switch 0: the look-ahead to the last block
     old = skew.set_lookahead(2 if lookahead else 0)
+    old_sw = skew.set_lookahead_switch(switch)
     try:
         if with_L:
             L, t, piv, info = skew.ltlt(dev(A), nb=nb, workspace=workspace)
@@ -41,6 +43,7 @@ def factor(A, nb, lookahead, workspace=None, with_L=True):
             int(info.item())
     finally:
         skew.set_lookahead(old)
+        skew.set_lookahead_switch(old_sw)
 
 
 def check(A, L, t, piv, info):
@@ -81,18 +84,45 @@ def test_lookahead_pfaffian_only(n, nb):
         assert abs(la - la0) <= 1e-10 * max(1.0, abs(la0))
 
 
+@pytest.mark.parametrize("n,nb,switch", [(1031, 48, 300), (1031, 48, 700), (1031, 48, -1),
+                                         (2050, 32, 1000), (700, 16, 5000), (513, 32, 490)])
+def test_lookahead_then_plain(n, nb, switch):
+    """Look-ahead blocks until the trailing order falls below the switch order, the
+    remaining blocks on the plain path in place (the last look-ahead panel's updated
+    column copied into the state): the oracle's factorization, with and without L."""
+    A = inputs.skew_gaussian(n, 13000 + n + switch)
+    check(A, *factor(A, nb, True, switch=switch))
+    (la, sg), t, piv, info = factor(A, nb, True, with_L=False, switch=switch)
+    check(A, None, t, piv, info)
+    L0, t0, p0, _ = oracle.ltlt(A)
+    la0, sg0 = oracle.pfaffian_from_factors(n, t0, p0)
+    assert sg == sg0
+    if sg0 != 0:
+        assert abs(la - la0) <= 1e-10 * max(1.0, abs(la0))
+
+
+def test_switch_setting_round_trip():
+    old = skew.set_lookahead_switch(1234)
+    try:
+        assert skew.set_lookahead_switch(-5) == 1234
+        assert skew.set_lookahead_switch(0) == -1      # negative values mean the default
+    finally:
+        skew.set_lookahead_switch(old)
+
+
 def test_default_path_choice():
     """Mode 1 (the default) takes the look-ahead by order: the panel-width table's
-    choice, else the built-in rule (never with cluster panels, 3072 <= n <= 10240 with
-    grid-wide panels); mode 0 never."""
+    choice, else the built-in rule (3072 <= n <= 5120 with cluster panels, 3072 <= n <=
+    10240 with grid-wide panels); mode 0 never."""
     old = skew.set_lookahead(1)
     old_cl = skew.set_cluster_panel(True)
     try:
         skew.set_nb_table([])
-        assert not skew.lookahead_used(4096, 64) and not skew.lookahead_used(2000, 32)
+        assert skew.lookahead_used(4096, 32) and not skew.lookahead_used(2000, 32)
+        assert not skew.lookahead_used(8192, 32)
         skew.set_cluster_panel(False)
         assert not skew.lookahead_used(2000, 32) and skew.lookahead_used(4096, 64)
-        assert not skew.lookahead_used(16384, 64)
+        assert skew.lookahead_used(8192, 32) and not skew.lookahead_used(16384, 64)
         skew.set_cluster_panel(True)
         skew.set_nb_table([(3000, 32, 1), (20000, 64, 0)])
         assert skew.lookahead_used(2000) and not skew.lookahead_used(4096)
@@ -151,10 +181,12 @@ def test_lookahead_graph_capture_replays_equal():
                      device="cuda")
     s = torch.cuda.Stream()
     old = skew.set_lookahead(2)
+    old_sw = skew.set_lookahead_switch(300)      # look-ahead blocks, then plain ones
     try:
         run_graph_case(A, Ad, work, L, t, piv, info, ws, s, n, nb)
     finally:
         skew.set_lookahead(old)
+        skew.set_lookahead_switch(old_sw)
 
 
 def run_graph_case(A, Ad, work, L, t, piv, info, ws, s, n, nb):
@@ -197,6 +229,7 @@ def test_lookahead_at_its_largest_order_and_beyond():
     res = {}
     for mode in (2, 0):
         old = skew.set_lookahead(mode)
+        old_sw = skew.set_lookahead_switch(0)
         try:
             la, sg, t, piv, info = skew.pfaffian(dev(A), nb=64)
             torch.cuda.synchronize()
@@ -204,6 +237,7 @@ def test_lookahead_at_its_largest_order_and_beyond():
                          int(info.item()))
         finally:
             skew.set_lookahead(old)
+            skew.set_lookahead_switch(old_sw)
     (la2, sg2, t2, p2, i2), (la0, sg0, t0, p0, i0) = res[2], res[0]
     assert np.array_equal(p2, p0) and i2 == i0 == 0 and sg2 == sg0
     assert abs(la2 - la0) <= 1e-10 * abs(la0)
