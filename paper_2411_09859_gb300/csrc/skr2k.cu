@@ -29,6 +29,7 @@
 // packing, Section 4.3).  FP64 throughput on this part is what bounds the kernel
 // (about 1 TFLOP/s for the whole GPU), so the tile loop is kept simple: 64 x 64
 // CTA tiles, four warps of 32 x 32, 16 pairs (32 K-columns) staged per round.
+#include <atomic>
 #include <climits>
 #include <cmath>
 
@@ -43,6 +44,7 @@ constexpr int PC = 16;            // pairs per staging round
 constexpr int KC = 2 * PC;        // K columns per staging round
 constexpr int LDS = KC + 4;       // padded smem row (doubles): conflict-free fragments
 constexpr int kThreads = 128;     // four warps
+constexpr int64_t kSplitWaves = 8;  // updates of at most this many waves cut their tail
 
 __device__ __forceinline__ void dmma_8x8x4(double &c0, double &c1, double a, double b) {
     asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
@@ -59,33 +61,32 @@ __device__ __forceinline__ void tri_tile(int64_t idx, int64_t &bi, int64_t &bj) 
     bj = idx - r * (r + 1) / 2;
 }
 
-template <PairKind KIND, bool MAPPED>
-__global__ void __launch_bounds__(kThreads, 2)
-skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
-             PairSource<KIND> src, const double *Cin, int64_t ldcin, const int32_t *map,
-             int64_t nin) {
-    __shared__ double Us[BM][LDS];
-    __shared__ double Vs[BM][LDS];
-
-    int64_t bi, bj;
-    tri_tile(blockIdx.x, bi, bj);
-    const int64_t I0 = bi * BM, J0 = bj * BM;
+// One TS x TS tile of C with rows I0.. and columns J0..: four warps of TS/2 x TS/2,
+// each F x F DMMA fragments of 8 x 8 (F = TS / 16).
+template <PairKind KIND, bool MAPPED, int TS>
+__device__ __forceinline__ void skr2k_tile(int64_t I0, int64_t J0, int64_t m, double *C,
+                                           int64_t ldc, double alpha, double beta,
+                                           const PairSource<KIND> &src, const double *Cin,
+                                           int64_t ldcin, const int32_t *map, int64_t nin,
+                                           double (&Us)[BM][LDS], double (&Vs)[BM][LDS]) {
+    constexpr int F = TS / 16;                     // fragments per warp and dimension
+    constexpr int WT = TS / 2;                     // warp tile
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp & 1, wn = warp >> 1;       // warp quadrant
     const int g = lane >> 2, tg = lane & 3;        // fragment coordinates
 
-    double acc[4][4][2];
+    double acc[F][F][2];
 #pragma unroll
-    for (int mi = 0; mi < 4; ++mi)
+    for (int mi = 0; mi < F; ++mi)
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni) acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
+        for (int ni = 0; ni < F; ++ni) acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
 
     const int64_t np = src.npairs();
     for (int64_t p0 = 0; p0 < np; p0 += PC) {
         const int nv = (int)((np - p0) < PC ? (np - p0) : PC);
         // ---- stage U rows I0.. and V rows J0.. for pairs p0 .. p0+PC-1
-        for (int it = tid; it < BM * PC; it += kThreads) {
-            const int r = it % BM, pp = it / BM;
+        for (int it = tid; it < TS * PC; it += kThreads) {
+            const int r = it % TS, pp = it / TS;
             double ai = 0.0, wi = 0.0, aj = 0.0, wj = 0.0;
             if (pp < nv) {
                 if (I0 + r < m) src.get(p0 + pp, I0 + r, ai, wi);
@@ -104,15 +105,15 @@ skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
 #pragma unroll 1
             for (int ks = 0; ks < ksteps; ++ks) {
                 const int kc = half * PC + ks * 4 + tg;
-                double af[4], bf[4];
+                double af[F], bf[F];
 #pragma unroll
-                for (int mi = 0; mi < 4; ++mi) af[mi] = Us[wm * 32 + mi * 8 + g][kc];
+                for (int mi = 0; mi < F; ++mi) af[mi] = Us[wm * WT + mi * 8 + g][kc];
 #pragma unroll
-                for (int ni = 0; ni < 4; ++ni) bf[ni] = Vs[wn * 32 + ni * 8 + g][kc];
+                for (int ni = 0; ni < F; ++ni) bf[ni] = Vs[wn * WT + ni * 8 + g][kc];
 #pragma unroll
-                for (int mi = 0; mi < 4; ++mi)
+                for (int mi = 0; mi < F; ++mi)
 #pragma unroll
-                    for (int ni = 0; ni < 4; ++ni)
+                    for (int ni = 0; ni < F; ++ni)
                         dmma_8x8x4(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
             }
         }
@@ -122,26 +123,26 @@ skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
     // ---- epilogue: strictly lower entries inside the block.  All C loads of a row
     // block are issued before its stores, so their latencies overlap.  Out of place,
     // the old entry (gi, gj) is entry (map[gi], map[gj]) of the skew matrix Cin.
-    int cmap[4][2];
+    int cmap[F][2];
     if (MAPPED) {
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
+        for (int ni = 0; ni < F; ++ni)
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                const int64_t gj = J0 + wn * 32 + ni * 8 + 2 * tg + c;
+                const int64_t gj = J0 + wn * WT + ni * 8 + 2 * tg + c;
                 cmap[ni][c] = gj < m ? __ldg(map + gj) : 0;
             }
     }
 #pragma unroll
-    for (int mi = 0; mi < 4; ++mi) {
-        const int64_t gi = I0 + wm * 32 + mi * 8 + g;
-        double cv[4][2];
+    for (int mi = 0; mi < F; ++mi) {
+        const int64_t gi = I0 + wm * WT + mi * 8 + g;
+        double cv[F][2];
         const int rmap = (MAPPED && gi < m) ? __ldg(map + gi) : 0;
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
+        for (int ni = 0; ni < F; ++ni)
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                const int64_t gj = J0 + wn * 32 + ni * 8 + 2 * tg + c;
+                const int64_t gj = J0 + wn * WT + ni * 8 + 2 * tg + c;
                 const bool in = gi < m && gj < m && gi > gj && beta != 0.0;
                 if (!in) {
                     cv[ni][c] = 0.0;
@@ -158,10 +159,10 @@ skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
                 }
             }
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni) {
+        for (int ni = 0; ni < F; ++ni) {
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                const int64_t gj = J0 + wn * 32 + ni * 8 + 2 * tg + c;
+                const int64_t gj = J0 + wn * WT + ni * 8 + 2 * tg + c;
                 if (gi < m && gj < m && gi > gj) {
                     double *dst = C + gi + gj * ldc;
                     const double upd = alpha * acc[mi][ni][c];
@@ -172,6 +173,101 @@ skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
     }
 }
 
+
+// Whole 64 x 64 lower tiles, one per block.
+template <PairKind KIND, bool MAPPED>
+__global__ void __launch_bounds__(kThreads, 2)
+skr2k_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
+             PairSource<KIND> src, const double *Cin, int64_t ldcin, const int32_t *map,
+             int64_t nin) {
+    __shared__ double Us[BM][LDS];
+    __shared__ double Vs[BM][LDS];
+    int64_t bi, bj;
+    tri_tile(blockIdx.x, bi, bj);
+    skr2k_tile<KIND, MAPPED, BM>(bi * BM, bj * BM, m, C, ldc, alpha, beta, src, Cin, ldcin,
+                                 map, nin, Us, Vs);
+}
+
+// The lower tiles from `tile0` on, cut into four 32 x 32 quarters, one per block (a
+// quarter entirely above the diagonal does nothing): the partial last wave of an
+// update, a quarter as long as whole tiles would make it.
+template <PairKind KIND, bool MAPPED>
+__global__ void __launch_bounds__(kThreads, 2)
+skr2k_quarter_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
+                     PairSource<KIND> src, const double *Cin, int64_t ldcin,
+                     const int32_t *map, int64_t nin, int64_t tile0) {
+    __shared__ double Us[BM][LDS];
+    __shared__ double Vs[BM][LDS];
+    const int64_t q = blockIdx.x;
+    int64_t bi, bj;
+    tri_tile(tile0 + (q >> 2), bi, bj);
+    const int si = (int)((q >> 1) & 1), sj = (int)(q & 1);
+    if (bi == bj && si < sj) return;               // above the diagonal
+    skr2k_tile<KIND, MAPPED, BM / 2>(bi * BM + si * (BM / 2), bj * BM + sj * (BM / 2), m, C,
+                                     ldc, alpha, beta, src, Cin, ldcin, map, nin, Us, Vs);
+}
+
+// Both in one launch: blocks below `nfull` take whole tiles 0 .. nfull-1, the rest the
+// quarters of the tiles from nfull on.  Used by the look-ahead's out-of-place update,
+// which shares the device with a panel: its quarters then fill the slots as they free
+// up, where a second launch would wait for the whole tiles to drain.  (Holding both tile
+// sizes makes the whole-tile path of this kernel slower than skr2k_kernel's, so the
+// in-place update keeps two launches.)
+template <PairKind KIND, bool MAPPED>
+__global__ void __launch_bounds__(kThreads, 2)
+skr2k_mixed_kernel(int64_t m, double *C, int64_t ldc, double alpha, double beta,
+                   PairSource<KIND> src, const double *Cin, int64_t ldcin, const int32_t *map,
+                   int64_t nin, int64_t nfull) {
+    __shared__ double Us[BM][LDS];
+    __shared__ double Vs[BM][LDS];
+    const int64_t b = blockIdx.x;
+    int64_t bi, bj;
+    if (b < nfull) {
+        tri_tile(b, bi, bj);
+        skr2k_tile<KIND, MAPPED, BM>(bi * BM, bj * BM, m, C, ldc, alpha, beta, src, Cin,
+                                     ldcin, map, nin, Us, Vs);
+    } else {
+        const int64_t q = b - nfull;
+        tri_tile(nfull + (q >> 2), bi, bj);
+        const int si = (int)((q >> 1) & 1), sj = (int)(q & 1);
+        if (bi == bj && si < sj) return;           // above the diagonal
+        skr2k_tile<KIND, MAPPED, BM / 2>(bi * BM + si * (BM / 2), bj * BM + sj * (BM / 2), m,
+                                         C, ldc, alpha, beta, src, Cin, ldcin, map, nin, Us,
+                                         Vs);
+    }
+}
+
+// Blocks of the update kernel resident on the current device at once (one wave), per
+// device and instantiation, looked up once; 0 if the query fails (then every tile
+// stays whole).
+template <PairKind KIND>
+int64_t skr2k_wave(bool mapped) {
+    constexpr int kDevices = 64;
+    static std::atomic<long long> cached[kDevices][2];         // 0: not looked up yet
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) {
+        cudaGetLastError();
+        return 0;
+    }
+    std::atomic<long long> &slot = cached[dev][mapped ? 1 : 0];
+    long long w = slot.load();
+    if (w > 0) return w;
+    int sms = 0, per = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = mapped ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                         &per, skr2k_kernel<KIND, true>, kThreads, 0)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                         &per, skr2k_kernel<KIND, false>, kThreads, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    w = (long long)per * sms;
+    slot.store(w);
+    return w;
+}
+
 template <PairKind KIND>
 int launch_kind(const Skr2kArgs &a, cudaStream_t stream) {
     if (a.m <= 1) return SKEW_OK;
@@ -179,13 +275,35 @@ int launch_kind(const Skr2kArgs &a, cudaStream_t stream) {
     const int64_t tiles = nt * (nt + 1) / 2;
     if (tiles > INT_MAX) return SKEW_ERR_CUDA;      // unreachable: orders are capped
     PairSource<KIND> src{a.P, a.ldp, a.Q, a.ldq, a.tt, a.x, a.b};
-    if (a.Cin != nullptr)
-        skr2k_kernel<KIND, true><<<(unsigned)tiles, kThreads, 0, stream>>>(
-            a.m, a.C, a.ldc, a.alpha, a.beta, src, a.Cin, a.ldcin, a.map, a.nin);
-    else
-        skr2k_kernel<KIND, false><<<(unsigned)tiles, kThreads, 0, stream>>>(
-            a.m, a.C, a.ldc, a.alpha, a.beta, src, nullptr, 0, nullptr, 0);
-    note_launches(1);
+    // whole waves of 64 x 64 tiles, then the rest as quarters in a second launch -- for
+    // updates of at most kSplitWaves waves, where the partial last wave is a large share
+    // of the time
+    const bool mapped = a.Cin != nullptr;
+    const int64_t wave = skr2k_wave<KIND>(mapped);
+    const int64_t nfull =
+        (wave > 0 && tiles <= kSplitWaves * wave) ? (tiles / wave) * wave : tiles;
+    if (mapped && nfull < tiles) {
+        const int64_t blocks = nfull + 4 * (tiles - nfull);
+        skr2k_mixed_kernel<KIND, true><<<(unsigned)blocks, kThreads, 0, stream>>>(
+            a.m, a.C, a.ldc, a.alpha, a.beta, src, a.Cin, a.ldcin, a.map, a.nin, nfull);
+        note_launches(1);
+        return check_launch();
+    }
+    if (nfull > 0) {
+        if (mapped)
+            skr2k_kernel<KIND, true><<<(unsigned)nfull, kThreads, 0, stream>>>(
+                a.m, a.C, a.ldc, a.alpha, a.beta, src, a.Cin, a.ldcin, a.map, a.nin);
+        else
+            skr2k_kernel<KIND, false><<<(unsigned)nfull, kThreads, 0, stream>>>(
+                a.m, a.C, a.ldc, a.alpha, a.beta, src, nullptr, 0, nullptr, 0);
+        note_launches(1);
+    }
+    if (nfull < tiles) {
+        const unsigned nq = (unsigned)(4 * (tiles - nfull));
+        skr2k_quarter_kernel<KIND, false><<<nq, kThreads, 0, stream>>>(
+            a.m, a.C, a.ldc, a.alpha, a.beta, src, nullptr, 0, nullptr, 0, nfull);
+        note_launches(1);
+    }
     return check_launch();
 }
 
