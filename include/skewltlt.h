@@ -210,8 +210,9 @@ int skew_set_lookahead(int mode);
  * look-ahead: once the next trailing update is smaller than `rows`, that update is the
  * last out-of-place one and the remaining blocks are factored as on the plain path, in
  * place on its result (the panel of such a block costs more than the update it would
- * hide).  Returns the previous value; -1 (the default) means 80 x the panel width, 0
- * keeps the look-ahead to the end.  A schedule of this library, no counterpart in the
+ * hide).  Returns the previous value; -1 (the default) means 2560 rows (where an
+ * update stops hiding a look-ahead panel on GB300, whatever the width), 0 keeps the
+ * look-ahead to the end.  A schedule of this library, no counterpart in the
  * paper; results as on the plain path. */
 long long skew_set_lookahead_switch(long long rows);
 

@@ -272,7 +272,7 @@ def set_cluster_panel(on: bool) -> bool:
 
 def set_lookahead_switch(rows: int) -> int:
     """Trailing order below which a look-ahead factorization goes on without the
-    look-ahead (skew_set_lookahead_switch; -1: the default, 80 x the panel width).
+    look-ahead (skew_set_lookahead_switch; -1: the default, 2560 rows).
     Returns the old setting."""
     return int(lib().skew_set_lookahead_switch(int(rows)))
 

@@ -185,8 +185,13 @@ void la_release(int dev, const LaStreams &s) {
 }
 
 std::atomic<int> g_lookahead{1};
-// Trailing order below which a look-ahead factorization goes on without it (-1: 80 nb)
+// Trailing order below which a look-ahead factorization goes on without it (-1: the
+// default, kLaSwitchRows)
 std::atomic<long long> g_la_switch{-1};
+// Where an update of m trailing rows (about m^2 nb flops at 1 TFLOP/s) stops hiding a
+// look-ahead panel (nb column steps of 7-10 us): m^2 ~ 7e6 to 1e7, whatever the width.
+// Measured best: 2560 at n = 4096, width 32; 2048-3072 at n = 8192, width 64.
+constexpr long long kLaSwitchRows = 2560;
 std::atomic<int> g_cluster_panel{1};
 
 // Library-private stream-ordered pool: freed blocks stay reserved for reuse (release
@@ -519,7 +524,7 @@ int factor_la(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double 
             // would hide: update j is the last look-ahead update, and the remaining blocks
             // are factored like the plain path, in place on S_j.
             const long long sw = g_la_switch.load();
-            const bool la_next = (n - s - 1) > (sw < 0 ? 80LL * nb : sw);
+            const bool la_next = (n - s - 1) > (sw < 0 ? kLaSwitchRows : sw);
             // ---- panel j+1, beside update j: reads S_{j-1}
             const int64_t k0n = kend, kendn = (kend + nb < n - 1) ? kend + nb : n - 1;
             if (la_next && j >= 1) {
