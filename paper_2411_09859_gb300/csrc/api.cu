@@ -1605,10 +1605,14 @@ int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
     int32_t h_sign = 0, h_info = 0;
     h.have_ms = false;
     do {
+        // one contiguous copy when the host matrix has no padding, else a pitched one
         cudaError_t e = cudaEventRecord(h.ev[0], st);
         if (e == cudaSuccess && n > 0)
-            e = cudaMemcpy2DAsync(dA, n * sizeof(double), A_host, lda * sizeof(double),
-                                  n * sizeof(double), n, cudaMemcpyHostToDevice, st);
+            e = (lda == n) ? cudaMemcpyAsync(dA, A_host, (size_t)n * n * sizeof(double),
+                                             cudaMemcpyHostToDevice, st)
+                           : cudaMemcpy2DAsync(dA, n * sizeof(double), A_host,
+                                               lda * sizeof(double), n * sizeof(double), n,
+                                               cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaEventRecord(h.ev[1], st);
         if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
         if (L_host) {
@@ -1620,8 +1624,11 @@ int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
         if (status != SKEW_OK) break;
         e = cudaEventRecord(h.ev[2], st);
         if (e == cudaSuccess && L_host && n > 0)
-            e = cudaMemcpy2DAsync(L_host, ldl * sizeof(double), dL, n * sizeof(double),
-                                  n * sizeof(double), n, cudaMemcpyDeviceToHost, st);
+            e = (ldl == n) ? cudaMemcpyAsync(L_host, dL, (size_t)n * n * sizeof(double),
+                                             cudaMemcpyDeviceToHost, st)
+                           : cudaMemcpy2DAsync(L_host, ldl * sizeof(double), dL,
+                                               n * sizeof(double), n * sizeof(double), n,
+                                               cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && t_host && n > 1)
             e = cudaMemcpyAsync(t_host, dt, (n - 1) * sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && piv_host && n > 0)

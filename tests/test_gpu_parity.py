@@ -9,6 +9,7 @@ Bars:
   - reconstruction ||P A P^T - L T L^T||_F / (n eps ||A||_F) <= 10;
   - log|Pf| within 1e-10 * max(1, |log|Pf||) and the same sign.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -196,6 +197,34 @@ def test_host_entry_point_matches_device_path():
     _, t2, p2, la2, sg2, info2 = skew.ltlt_host(A, want_L=False, nb=32)
     assert np.array_equal(p2, p1) and info2 == 0
     assert_pf_close(la2, sg2, la0, sg0)
+
+
+@pytest.mark.parametrize("n", [255, 256, 700])
+def test_host_entry_point_upper_triangles(n):
+    """skew_ltlt_host: NaN in A's upper triangle (and diagonal) changes nothing, and L's
+    upper triangle comes back exactly zero in an output buffer that held NaN."""
+    A = inputs.skew_gaussian(n, 11 + n)
+    Apoison = np.asfortranarray(A.copy())
+    Apoison[np.triu_indices(n)] = np.nan
+    Lout = np.full((n, n), np.nan, order="F")
+    L, t, piv, la, sg, info = skew.ltlt_host(Apoison, want_L=True, nb=32, L_out=Lout)
+    L1, t1, p1, i1 = gpu_ltlt(A, 32)
+    assert info == 0 and np.array_equal(piv, p1) and np.array_equal(t, t1)
+    assert np.array_equal(L, L1)
+    assert np.all(L[np.triu_indices(n, 1)] == 0.0) and np.all(np.diag(L) == 1.0)
+    # padded host matrices (leading dimension n + 3) take the pitched copies
+    Apad = np.full((n + 3, n), np.nan, order="F")
+    Apad[:n, :] = A
+    L2 = np.full((n + 3, n), np.nan, order="F")
+    t2, p2 = np.zeros(n - 1), np.zeros(n, dtype=np.int32)
+    la2, sg2, inf2 = ctypes.c_double(), ctypes.c_int32(), ctypes.c_int32()
+    vp = ctypes.c_void_p
+    st = skew.lib().skew_ltlt_host(n, vp(Apad.ctypes.data), n + 3, vp(L2.ctypes.data), n + 3,
+                                   vp(t2.ctypes.data), vp(p2.ctypes.data), ctypes.byref(la2),
+                                   ctypes.byref(sg2), ctypes.byref(inf2), 32)
+    assert st == 0 and inf2.value == 0
+    assert np.array_equal(L2[:n], L1) and np.array_equal(p2, p1) and np.array_equal(t2, t1)
+    assert np.all(np.isnan(L2[n:]))                  # the padding rows are not written
 
 
 def test_host_entry_point_keeps_buffers_and_reports_phases():
