@@ -593,7 +593,10 @@ int skew_server_destroy(skew_server *server);
  *   9  sign      host int32 or NULL
  *  10  info      host int32 or NULL
  *  11  nb
- * Host buffers may be pageable or page-locked (page-locked copies are faster).
+ * Host buffers may be pageable or page-locked (page-locked copies are faster).  A
+ * page-locked L_host receives each panel's rows of L as soon as they are final (the
+ * panel of their step and its row exchanges done), while later panels are factored,
+ * on the plain path; otherwise L is copied after the factorization.
  */
 int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
                    int64_t ldl, double *t_host, int32_t *piv_host, double *logabs,

@@ -314,6 +314,37 @@ bool lookahead_applies(int64_t n, int nb, int precision, const DeviceInfo &di) {
 // ------------------------------------------------------------------ the factorization
 namespace {
 
+// Rows of L sent to host memory while the factorization runs (skew_ltlt_host with a
+// page-locked L): a row of L is final once the panel of its step and that panel's
+// pivot_rows are done (later exchanges only touch rows below the panel), so each
+// panel's strip of rows, over all n columns, is copied on `copy` after them.
+struct HostRows {
+    double *L_host = nullptr;
+    int64_t ldl_host = 0;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev = nullptr;      // reused: each wait captures the last record
+    bool used = false;
+};
+
+// Copy rows [r0, r1) of the device L (all n columns) to the host after the work
+// already submitted on `after`.
+int host_rows_strip(HostRows *hr, const double *L, int64_t ldl, int64_t n, int64_t r0,
+                    int64_t r1, cudaStream_t after) {
+    if (hr == nullptr || hr->L_host == nullptr || r1 <= r0) return SKEW_OK;
+    cudaError_t e = cudaEventRecord(hr->ev, after);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hr->copy, hr->ev, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(hr->L_host + r0, hr->ldl_host * sizeof(double), L + r0,
+                              ldl * sizeof(double), (size_t)(r1 - r0) * sizeof(double),
+                              (size_t)n, cudaMemcpyDeviceToHost, hr->copy);
+    if (e != cudaSuccess) {
+        set_last_error(e);
+        return SKEW_ERR_CUDA;
+    }
+    hr->used = true;
+    return SKEW_OK;
+}
+
 // The blocks from s on, factored like the plain path (panel, pivot_rows beside the
 // next update, in-place fused update) on the state X = S_j left by the last look-ahead
 // update.  Column s of X is the last look-ahead panel's updated column (kept by
@@ -626,7 +657,7 @@ int factor_la(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double 
 int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
            int32_t *piv, int32_t *info, double *logabs, int32_t *sign, int nb,
            void *workspace, size_t workspace_bytes, cudaStream_t st, bool with_L,
-           int precision) {
+           int precision, HostRows *host_rows = nullptr) {
     DeviceInfo di;
     SKEW_TRY_STATUS(current_device_info(&di));
     if (nb == 0) nb = skew_default_nb(n);
@@ -744,9 +775,18 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
                     ps_stream = side.stream;
                     side_used = true;
                 }
-                ProfScope ps(kProfPivotRows, ps_stream, 0.0,
-                             4.0 * 8.0 * (double)k0 * (double)(kend - k0));
-                status = launch_pivot_rows(n, L, ldl, piv, (int)k0, (int)kend, ps_stream);
+                {
+                    ProfScope ps(kProfPivotRows, ps_stream, 0.0,
+                                 4.0 * 8.0 * (double)k0 * (double)(kend - k0));
+                    status = launch_pivot_rows(n, L, ldl, piv, (int)k0, (int)kend, ps_stream);
+                }
+                if (status != SKEW_OK) break;
+                // rows k0+1 .. kend of L are final
+                status = host_rows_strip(host_rows, L, ldl, n, k0 + 1, kend + 1, ps_stream);
+                if (status != SKEW_OK) break;
+            } else if (with_L && k0 == 0) {
+                // rows 0 .. kend of L are final after the first panel
+                status = host_rows_strip(host_rows, L, ldl, n, 0, kend + 1, st);
                 if (status != SKEW_OK) break;
             }
             if (with_x) {
@@ -925,6 +965,8 @@ struct HostCall {
     std::mutex mu;
     bool ready = false;
     cudaStream_t st = nullptr;
+    cudaStream_t copy = nullptr;   // rows of L to host memory during the factorization
+    cudaEvent_t ev_rows = nullptr, ev_join = nullptr;
     cudaEvent_t ev[4] = {};
     void *buf = nullptr;          // dA | dL | dt | dpiv | dlog | dsign | dinfo
     size_t buf_bytes = 0;
@@ -936,6 +978,9 @@ HostCall g_host[kMaxDevices];
 int host_ready(HostCall &h) {
     if (h.ready) return SKEW_OK;
     SKEW_TRY(cudaStreamCreateWithFlags(&h.st, cudaStreamNonBlocking));
+    SKEW_TRY(cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking));
+    SKEW_TRY(cudaEventCreateWithFlags(&h.ev_rows, cudaEventDisableTiming));
+    SKEW_TRY(cudaEventCreateWithFlags(&h.ev_join, cudaEventDisableTiming));
     for (cudaEvent_t &e : h.ev) SKEW_TRY(cudaEventCreate(&e));
     h.ready = true;
     return SKEW_OK;
@@ -1615,7 +1660,27 @@ int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
                                                cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaEventRecord(h.ev[1], st);
         if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
-        if (L_host) {
+        // a page-locked L receives its final rows while the factorization runs (plain
+        // path); otherwise, and on the look-ahead path, L is copied after it
+        HostRows hr;
+        if (L_host && n > 0) {
+            cudaPointerAttributes pa;
+            if (cudaPointerGetAttributes(&pa, L_host) == cudaSuccess &&
+                pa.type == cudaMemoryTypeHost) {
+                hr.L_host = L_host;
+                hr.ldl_host = ldl;
+                hr.copy = h.copy;
+                hr.ev = h.ev_rows;
+            } else {
+                cudaGetLastError();
+            }
+        }
+        if (L_host && hr.L_host) {
+            status = factor(n, dA, ld_min, dL, ld_min, dt, dpiv, dinfo, nullptr, nullptr,
+                            nb == 0 ? skew_default_nb(n) : nb, nullptr, 0, st, true,
+                            SKEW_PRECISION_FP64, &hr);
+            if (status == SKEW_OK) status = skew_pfaffian_from_factors(n, dt, dpiv, dlog, dsign, st);
+        } else if (L_host) {
             status = skew_ltlt(n, dA, ld_min, dL, ld_min, dt, dpiv, dinfo, nb, nullptr, 0, st);
             if (status == SKEW_OK) status = skew_pfaffian_from_factors(n, dt, dpiv, dlog, dsign, st);
         } else {
@@ -1623,7 +1688,11 @@ int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
         }
         if (status != SKEW_OK) break;
         e = cudaEventRecord(h.ev[2], st);
-        if (e == cudaSuccess && L_host && n > 0)
+        if (e == cudaSuccess && hr.used) {      // the last rows' copies, then the rest
+            e = cudaEventRecord(h.ev_join, h.copy);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h.ev_join, 0);
+        }
+        if (e == cudaSuccess && L_host && n > 0 && !hr.used)
             e = (ldl == n) ? cudaMemcpyAsync(L_host, dL, (size_t)n * n * sizeof(double),
                                              cudaMemcpyDeviceToHost, st)
                            : cudaMemcpy2DAsync(L_host, ldl * sizeof(double), dL,
@@ -1645,6 +1714,12 @@ int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess && status == SKEW_OK) {
         set_last_error(e);
+        status = SKEW_ERR_CUDA;
+    }
+    // on every exit no copy into the caller's L is left in flight
+    cudaError_t ec = cudaStreamSynchronize(h.copy);
+    if (ec != cudaSuccess && status == SKEW_OK) {
+        set_last_error(ec);
         status = SKEW_ERR_CUDA;
     }
     if (status == SKEW_OK) {

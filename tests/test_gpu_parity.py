@@ -227,6 +227,21 @@ def test_host_entry_point_upper_triangles(n):
     assert np.all(np.isnan(L2[n:]))                  # the padding rows are not written
 
 
+@pytest.mark.parametrize("n,nb", [(700, 32), (33, 32), (300, 64), (1, 8), (2, 8)])
+def test_host_entry_point_page_locked_rows_during_factorization(n, nb):
+    """With a page-locked L the final rows of L reach it panel by panel while the
+    factorization runs; the result equals the device path's, rows past n untouched."""
+    A = inputs.skew_gaussian(n, 21 + n)
+    Lpin = torch.empty((n, n), dtype=torch.float64).pin_memory().t()   # Fortran order
+    Lpin.fill_(float("nan"))
+    L, t, piv, la, sg, info = skew.ltlt_host(A, want_L=True, nb=nb, L_out=Lpin.numpy())
+    L1, t1, p1, i1 = gpu_ltlt(A, nb)
+    assert info == 0 and np.array_equal(piv, p1) and np.array_equal(t, t1)
+    assert np.array_equal(L, L1)
+    ph = skew.ltlt_host_timing()
+    assert ph is not None and all(x >= 0 for x in ph)
+
+
 def test_host_entry_point_keeps_buffers_and_reports_phases():
     """Repeated host calls of one order reuse the library's buffers (no change in free
     device memory after the first) and report their three phases."""
