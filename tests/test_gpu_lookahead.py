@@ -242,3 +242,18 @@ def test_lookahead_at_its_largest_order_and_beyond():
     assert np.array_equal(p2, p0) and i2 == i0 == 0 and sg2 == sg0
     assert abs(la2 - la0) <= 1e-10 * abs(la0)
     assert np.max(np.abs(t2 - t0)) <= TOL_C * n * EPS * np.max(np.abs(t0))
+
+
+@pytest.mark.parametrize("switch", [0, 500])
+def test_lookahead_cluster_panel_nonfinite_leaves_together(switch):
+    """A NaN in the input (flagged by the prologue) reaches every CTA of the cluster
+    look-ahead panel through its first exchange; all leave together with a valid map,
+    the call returns info = -100 on both schedules, and the context stays usable."""
+    A = inputs.skew_gaussian(900, 16)
+    A[700, 200] = np.nan
+    A[200, 700] = np.nan
+    for with_L in (True, False):
+        res = factor(A, 32, True, with_L=with_L, switch=switch)
+        assert res[3] == -100
+    B = inputs.skew_gaussian(500, 17)
+    check(B, *factor(B, 32, True, switch=switch))
