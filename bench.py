@@ -1131,12 +1131,15 @@ def run_ours(args):
                    "h2d_ms": float(med[0]) if len(ph) else None,
                    "device_ms": float(med[1]) if len(ph) else None,
                    "d2h_ms": float(med[2]) if len(ph) else None,
-                   "host_side_ms": (float(np.median(step_ms) - np.sum(med)) if len(ph) else None),
+                   "host_side_ms": (float(np.median(np.array(step_ms) - ph.sum(axis=1)))
+                                    if len(ph) == len(step_ms) and len(ph) else None),
                    "h2d_gbs": float(h2d_b / (med[0] / 1e3) / 1e9) if len(ph) else None,
-                   "d2h_gbs": float(d2h_b / (med[2] / 1e3) / 1e9) if len(ph) else None,
                    "what": ("CUDA events on the call's stream around the copy of A, the "
-                            "factorization and the copies back; host_side_ms = median step "
-                            "wall time minus their sum")},
+                            "factorization and the copies back; with a page-locked L the "
+                            "library sends each panel's final rows of L back while later "
+                            "panels run, so d2h_ms is only what remains after the "
+                            "factorization (the last rows, t, piv); host_side_ms = median "
+                            "over steps of the step's wall time minus its three phases")},
                "host_buffers": ("page-locked, allocated while bound to the "
                                 f"{near_cpus} CPUs next to the GPU" if near_cpus else
                                 "page-locked (GPU-local CPUs unknown: not bound)"),
