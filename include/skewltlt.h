@@ -593,7 +593,8 @@ int skew_server_destroy(skew_server *server);
  *   9  sign      host int32 or NULL
  *  10  info      host int32 or NULL
  *  11  nb
- * Host buffers may be pageable or page-locked (page-locked copies are faster).  A
+ * Host buffers may be pageable or page-locked (page-locked copies are faster).  Only
+ * A's lower triangle crosses the host link (in blocks of 256 columns).  A
  * page-locked L_host receives each panel's rows of L as soon as they are final (the
  * panel of their step and its row exchanges done), while later panels are factored,
  * on the plain path; otherwise L is copied after the factorization.

@@ -1604,6 +1604,9 @@ int skew_pfaffian_batched(int count, const skew_problem *problems, double *logab
     return status;
 }
 
+// Columns per host-link copy of A's lower triangle (skew_ltlt_host).
+constexpr int64_t kHostCopyCols = 256;
+
 int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
                    int64_t ldl, double *t_host, int32_t *piv_host, double *logabs,
                    int32_t *sign, int32_t *info, int nb) {
@@ -1650,14 +1653,16 @@ int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
     int32_t h_sign = 0, h_info = 0;
     h.have_ms = false;
     do {
-        // one contiguous copy when the host matrix has no padding, else a pitched one
+        // Only the lower triangle of A is read, so only it crosses the host link: in
+        // blocks of kHostCopyCols columns, rows from the block's first column down (half
+        // the bytes of the whole matrix; the device's upper triangle is never read).
         cudaError_t e = cudaEventRecord(h.ev[0], st);
-        if (e == cudaSuccess && n > 0)
-            e = (lda == n) ? cudaMemcpyAsync(dA, A_host, (size_t)n * n * sizeof(double),
-                                             cudaMemcpyHostToDevice, st)
-                           : cudaMemcpy2DAsync(dA, n * sizeof(double), A_host,
-                                               lda * sizeof(double), n * sizeof(double), n,
-                                               cudaMemcpyHostToDevice, st);
+        for (int64_t c0 = 0; e == cudaSuccess && c0 < n; c0 += kHostCopyCols) {
+            const int64_t w = (n - c0 < kHostCopyCols) ? n - c0 : kHostCopyCols;
+            e = cudaMemcpy2DAsync(dA + c0 + c0 * n, n * sizeof(double), A_host + c0 + c0 * lda,
+                                  lda * sizeof(double), (size_t)(n - c0) * sizeof(double),
+                                  (size_t)w, cudaMemcpyHostToDevice, st);
+        }
         if (e == cudaSuccess) e = cudaEventRecord(h.ev[1], st);
         if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
         // a page-locked L receives its final rows while the factorization runs (plain
