@@ -596,8 +596,8 @@ int skew_server_destroy(skew_server *server);
  * Host buffers may be pageable or page-locked (page-locked copies are faster).  Only
  * A's lower triangle crosses the host link (in blocks of 256 columns).  A
  * page-locked L_host receives each panel's rows of L as soon as they are final (the
- * panel of their step and its row exchanges done), while later panels are factored,
- * on the plain path; otherwise L is copied after the factorization.
+ * panel of their step and its row exchanges done), while later panels are factored;
+ * a pageable L_host receives L after the factorization.
  */
 int skew_ltlt_host(int64_t n, const double *A_host, int64_t lda, double *L_host,
                    int64_t ldl, double *t_host, int32_t *piv_host, double *logabs,

@@ -352,7 +352,8 @@ int host_rows_strip(HostRows *hr, const double *L, int64_t ldl, int64_t n, int64
 int factor_rest_plain(int64_t n, double *X, int64_t ldx, int64_t s, const double *xlast,
                       int64_t jnext, double *L, int64_t ldl, double *const *lbuf, bool with_L,
                       double *t, int32_t *piv, Ctrl *ctrl, ArgmaxPartial *part, int nb,
-                      cudaStream_t st, LaStreams &ls, const DeviceInfo &di) {
+                      cudaStream_t st, LaStreams &ls, const DeviceInfo &di,
+                      HostRows *host_rows) {
     cudaError_t e = cudaMemcpyAsync(X + (s + 1) + s * ldx, xlast + (s + 1),
                                     sizeof(double) * (size_t)(n - s - 1),
                                     cudaMemcpyDeviceToDevice, st);
@@ -390,9 +391,13 @@ int factor_rest_plain(int64_t n, double *X, int64_t ldx, int64_t s, const double
             e = cudaEventRecord(ls.fork, st);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(ls.rows, ls.fork, 0);
             if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
-            ProfScope ps(kProfPivotRows, ls.rows, 0.0,
-                         4.0 * 8.0 * (double)k0 * (double)(kend - k0));
-            status = launch_pivot_rows(n, L, ldl, piv, (int)k0, (int)kend, ls.rows);
+            {
+                ProfScope ps(kProfPivotRows, ls.rows, 0.0,
+                             4.0 * 8.0 * (double)k0 * (double)(kend - k0));
+                status = launch_pivot_rows(n, L, ldl, piv, (int)k0, (int)kend, ls.rows);
+            }
+            if (status != SKEW_OK) break;
+            status = host_rows_strip(host_rows, L, ldl, n, k0 + 1, kend + 1, ls.rows);
             if (status != SKEW_OK) break;
         }
         if (with_x) {
@@ -430,7 +435,8 @@ int factor_rest_plain(int64_t n, double *X, int64_t ldx, int64_t s, const double
 //              which reads the L columns of block j-1.
 int factor_la(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
               int32_t *piv, int32_t *info, double *logabs, int32_t *sign, int nb, char *base,
-              const LaLayout &lay, cudaStream_t st, bool with_L, const DeviceInfo &di) {
+              const LaLayout &lay, cudaStream_t st, bool with_L, const DeviceInfo &di,
+              HostRows *host_rows) {
     Ctrl *ctrl = reinterpret_cast<Ctrl *>(base + lay.base.ctrl);
     ArgmaxPartial *part = reinterpret_cast<ArgmaxPartial *>(base + lay.base.partials);
     if (t == nullptr) t = reinterpret_cast<double *>(base + lay.base.tbuf);
@@ -525,6 +531,9 @@ int factor_la(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double 
             status = launch_la_panel(pa);
         }
         if (status != SKEW_OK) break;
+        // rows 0 .. kend of L are final after the first panel
+        if (with_L) status = host_rows_strip(host_rows, L, ldl, n, 0, kend + 1, ls.panel);
+        if (status != SKEW_OK) break;
         e = cudaEventRecord(ls.panel_done, ls.panel);
         if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
 
@@ -545,9 +554,13 @@ int factor_la(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double 
                 if (e == cudaSuccess && j >= 1)
                     e = cudaStreamWaitEvent(ls.rows, ls.upd_done[(j - 1) & 1], 0);
                 if (e != cudaSuccess) { set_last_error(e); status = SKEW_ERR_CUDA; break; }
-                ProfScope ps(kProfPivotRows, ls.rows, 0.0,
-                             4.0 * 8.0 * (double)k0 * (double)(kend - k0));
-                status = launch_pivot_rows(n, L, ldl, piv, (int)k0, (int)kend, ls.rows);
+                {
+                    ProfScope ps(kProfPivotRows, ls.rows, 0.0,
+                                 4.0 * 8.0 * (double)k0 * (double)(kend - k0));
+                    status = launch_pivot_rows(n, L, ldl, piv, (int)k0, (int)kend, ls.rows);
+                }
+                if (status != SKEW_OK) break;
+                status = host_rows_strip(host_rows, L, ldl, n, k0 + 1, kend + 1, ls.rows);
                 if (status != SKEW_OK) break;
             }
             if (!has_update) break;
@@ -626,7 +639,8 @@ int factor_la(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double 
             }
             if (!la_next) {
                 status = factor_rest_plain(n, sbuf(j), sld(j), s, xs[j & 1], j + 1, L, ldl,
-                                           lbuf, with_L, t, piv, ctrl, part, nb, st, ls, di);
+                                           lbuf, with_L, t, piv, ctrl, part, nb, st, ls, di,
+                                           host_rows);
                 break;
             }
             k0 = k0n;
@@ -671,7 +685,7 @@ int factor(int64_t n, double *A, int64_t lda, double *L, int64_t ldl, double *t,
                 lown = true;
             }
             int rc = factor_la(n, A, lda, L, ldl, t, piv, info, logabs, sign, nb, lb, llay, st,
-                               with_L, di);
+                               with_L, di, host_rows);
             if (lown) {
                 cudaError_t e = cudaFreeAsync(lb, st);
                 if (e != cudaSuccess && rc == SKEW_OK) {

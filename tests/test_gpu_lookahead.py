@@ -257,3 +257,26 @@ def test_lookahead_cluster_panel_nonfinite_leaves_together(switch):
         assert res[3] == -100
     B = inputs.skew_gaussian(500, 17)
     check(B, *factor(B, 32, True, switch=switch))
+
+
+@pytest.mark.parametrize("switch", [0, 500])
+def test_lookahead_host_call_rows_during_factorization(switch):
+    """skew_ltlt_host on the look-ahead path with a page-locked L (its rows sent back
+    while later panels run, through the switch to the plain path): the same factors as
+    the device call on the same path."""
+    n, nb = 1000, 32
+    A = inputs.skew_gaussian(n, 18)
+    old = skew.set_lookahead(2)
+    old_sw = skew.set_lookahead_switch(switch)
+    try:
+        assert skew.lookahead_used(n, nb)
+        Lpin = torch.empty((n, n), dtype=torch.float64).pin_memory().t()
+        Lpin.fill_(float("nan"))
+        L, t, piv, la, sg, info = skew.ltlt_host(A, want_L=True, nb=nb, L_out=Lpin.numpy())
+        L1, t1, p1, i1 = skew.ltlt(dev(A), nb=nb)
+        torch.cuda.synchronize()
+        assert info == 0 and np.array_equal(piv, p1.cpu().numpy())
+        assert np.array_equal(t, t1.cpu().numpy()) and np.array_equal(L, L1.cpu().numpy())
+    finally:
+        skew.set_lookahead(old)
+        skew.set_lookahead_switch(old_sw)
