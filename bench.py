@@ -66,6 +66,9 @@ def parse_args():
     ap.add_argument("--path", choices=["auto", "plain", "lookahead"], default="auto",
                     help="factorization path of the timed steps (auto: the library's choice "
                          "for the order)")
+    ap.add_argument("--la-switch", type=int, default=-1,
+                    help="trailing order below which a look-ahead factorization goes on "
+                         "without it (skew_set_lookahead_switch; -1: the library's default)")
     ap.add_argument("--skip-plain", action="store_true",
                     help="skip timing the other path (plain / look-ahead) beside the headline")
     ap.add_argument("--skip-e2e", action="store_true")
@@ -995,6 +998,7 @@ def run_ours(args):
     info = torch.empty(1, dtype=torch.int32, device=dev)
     if args.path != "auto":
         skew.set_lookahead(2 if args.path == "lookahead" else 0)
+    skew.set_lookahead_switch(args.la_switch)
     lookahead = skew.lookahead_used(n, nb)
     ws = torch.empty(skew.workspace_bytes(n, nb, True, lookahead=True), dtype=torch.uint8,
                      device=dev)
