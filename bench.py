@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--path", choices=["auto", "plain", "lookahead"], default="auto",
                     help="factorization path of the timed steps (auto: the library's choice "
                          "for the order)")
+    ap.add_argument("--grid-panels", action="store_true",
+                    help="grid-wide panels for every trailing block (skew_set_cluster_panel(0))")
     ap.add_argument("--la-switch", type=int, default=-1,
                     help="trailing order below which a look-ahead factorization goes on "
                          "without it (skew_set_lookahead_switch; -1: the library's default)")
@@ -999,6 +1001,7 @@ def run_ours(args):
     if args.path != "auto":
         skew.set_lookahead(2 if args.path == "lookahead" else 0)
     skew.set_lookahead_switch(args.la_switch)
+    skew.set_cluster_panel(not args.grid_panels)
     lookahead = skew.lookahead_used(n, nb)
     ws = torch.empty(skew.workspace_bytes(n, nb, True, lookahead=True), dtype=torch.uint8,
                      device=dev)
